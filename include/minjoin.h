@@ -1,0 +1,157 @@
+/*
+ * minjoin.h — C ABI of the GB300 (sm_103a) MinJoin edit-similarity join.
+ *
+ * The library computes the join of Zhang & Zhang, "MinJoin: Efficient Edit
+ * Similarity Joins via Local Hash Minima" (arXiv 1810.08833):
+ *   given strings s_0..s_{n-1} and a threshold K (Sec. 1, problem statement),
+ *   return the pairs (i, j), i < j, with ED(s_i, s_j) <= K that share a
+ *   partition (Alg. 3), together with their edit distances.
+ *
+ * Conventions shared by every entry point:
+ *  - Strings are a concatenated byte array `bytes` plus `offsets` (int64,
+ *    n+1 entries, non-decreasing, offsets[0] = 0): string i is
+ *    bytes[offsets[i] .. offsets[i+1]).  Positions are 0-based.
+ *  - Pointers named d_* are device pointers on the context's device; h_* are
+ *    host pointers.  Inputs stay owned by the caller and are only read.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is stream-ordered; calls that return a count synchronise
+ *    the stream before returning.
+ *  - Every function returns 0 (MJ_OK) or a negative MJ_ERR_* code; it never
+ *    aborts the process.  mj_strerror() names a code.  After an error the
+ *    context stays usable.
+ *  - Results of the last call are held in memory the context owns, valid
+ *    until the next call of the same family on that context; *_copy entry
+ *    points copy them into caller buffers.
+ *  - A context is not thread-safe; use one per host thread.
+ */
+#ifndef MINJOIN_H
+#define MINJOIN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MJ_OK 0
+#define MJ_ERR_ARG (-1)          /* invalid argument (null pointer, size, parameter) */
+#define MJ_ERR_CUDA (-2)         /* a CUDA runtime call failed */
+#define MJ_ERR_OOM (-3)          /* device allocation failed */
+#define MJ_ERR_DEVICE (-4)       /* a device-side check failed (see mj_stats.device_flags) */
+#define MJ_ERR_UNSUPPORTED (-5)  /* input outside the supported range (e.g. radius too large) */
+#define MJ_ERR_TIMEOUT (-6)      /* a bounded device-side wait ran out */
+#define MJ_ERR_STATE (-7)        /* call order (e.g. copy before compute, no trained band model) */
+
+/* verification modes (mj_params.verify_mode) */
+#define MJ_VERIFY_PLAIN 0        /* one pass with band K */
+#define MJ_VERIFY_LEARNED 1      /* learned first-pass band k' < K, fallback to K */
+
+typedef struct mj_ctx mj_ctx;
+
+/* Parameters of one join.
+ *  K       edit-distance threshold (Sec. 1).
+ *  T       targeted number of partitions per string (Alg. 2); 0 = K.
+ *  q       q-gram length; 0 = the rule of Sec. 2.2, q = ceil(3 log_|Sigma|(N/T)),
+ *          with Sigma the distinct byte values present and N the longest length;
+ *          capped so that q * ceil(log2 |Sigma|) <= 64.
+ *  r_min   lower bound applied to the neighbourhood radius of Alg. 2 line 2
+ *          (default 1; the literal rule gives r <= 0 for short strings).
+ *  seed    seed of the random q-gram function Pi and of the partition key.
+ *  verify_mode  MJ_VERIFY_PLAIN or MJ_VERIFY_LEARNED.
+ *  flags   bit 0: check every group of equal partition keys for byte equality
+ *          (counts mismatches in mj_stats.key_collisions). */
+typedef struct {
+  uint32_t K;
+  uint32_t T;
+  uint32_t q;
+  int32_t r_min;
+  uint64_t seed;
+  uint32_t verify_mode;
+  uint32_t flags;
+} mj_params;
+
+/* Parameters as derived for an input (Sec. 2.2, Alg. 2 line 2). */
+typedef struct {
+  uint32_t sigma;        /* distinct byte values present */
+  uint32_t bits;         /* bits per rank code, max(1, ceil(log2 sigma)) */
+  uint32_t q, T, K;
+  int32_t r_max;         /* radius of the longest string */
+  uint64_t N;            /* longest string length */
+  uint8_t rank[256];     /* rank code of every byte value (ascending byte order) */
+} mj_derived;
+
+/* Counters and timings of the last call (see each field). */
+typedef struct {
+  uint64_t n_strings, n_bytes;
+  uint64_t n_partitions;       /* records of Alg. 1 over all strings */
+  uint64_t n_raw_pairs;        /* pairs passing both filters, before dedup */
+  uint64_t n_candidates;       /* |C| after dedup (Alg. 3 line 20) */
+  uint64_t n_output;           /* pairs with ED <= K */
+  uint64_t key_collisions;     /* groups with equal keys but different bytes (flags bit 0) */
+  uint64_t band_cells;         /* K-band cells of all candidates: sum over pairs of
+                                  #{(i,j): 1<=i<=|a|, 1<=j<=|b|, |i-j| <= K} */
+  uint64_t first_pass_settled; /* learned mode: pairs decided by the first pass */
+  uint64_t fallback_pairs;     /* learned mode: pairs re-run with band K */
+  uint32_t device_flags;       /* bit set by a failed device-side check */
+  float ms_derive, ms_partition, ms_join_filter, ms_verify, ms_total;
+} mj_stats;
+
+void mj_params_default(mj_params* p, uint32_t K);
+const char* mj_strerror(int status);
+
+/* Create a context on CUDA device `device` (the calling thread's current
+ * device is left unchanged after the call). */
+int mj_create(mj_ctx** ctx, int device);
+void mj_destroy(mj_ctx* ctx);
+int mj_get_stats(const mj_ctx* ctx, mj_stats* out);
+
+/* Step a1 (Sec. 2.2, Alg. 2 line 2): Sigma, rank codes, N, q, T, r_max. */
+int mj_derive(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n,
+              const mj_params* p, void* stream, mj_derived* out);
+
+/* Steps a2-a4 (Alg. 1-2): partitions of every string.  *count receives the
+ * number of partitions; mj_partition_copy writes them in string order, each
+ * (sid, pos, len, key) with key the 64-bit partition-substring hash
+ * (Alg. 3 line 2's f).  `d_qgram_table` (nullable) replaces Pi by a table of
+ * 2^(q*bits) 64-bit values indexed by the packed rank code of a q-gram (first
+ * symbol most significant) — the form of Table 2's worked example. */
+int mj_partition(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n,
+                 const mj_params* p, const uint64_t* d_qgram_table, void* stream, uint64_t* count);
+int mj_partition_copy(mj_ctx* ctx, uint32_t* d_sid, uint32_t* d_pos, uint32_t* d_len,
+                      uint64_t* d_key, void* stream);
+
+/* Steps a2-a7 (Alg. 3 lines 4-20): the deduplicated candidate set C.
+ * *count receives |C|; mj_candidates_copy writes the pairs (i < j) sorted. */
+int mj_candidates(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n,
+                  const mj_params* p, const uint64_t* d_qgram_table, void* stream, uint64_t* count);
+int mj_candidates_copy(mj_ctx* ctx, uint32_t* d_i, uint32_t* d_j, void* stream);
+
+/* Step a8 (Sec. 3, verification with Ukkonen's band): for every pair
+ * (d_i[t], d_j[t]), t < m, writes d_ed[t] = ED if ED <= k_t, else k_t + 1,
+ * where k_t = d_k[t] if d_k is non-null, else K.  Any pair of strings is
+ * allowed (equal ids, empty strings).  Stream-ordered; does not synchronise.
+ * Rank codes are derived from the n strings given. */
+int mj_verify(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n,
+              const uint32_t* d_i, const uint32_t* d_j, const uint32_t* d_k, uint64_t m, uint32_t K,
+              void* stream, uint32_t* d_ed);
+
+/* The whole path (Alg. 3): *count receives the number of output pairs;
+ * mj_result_copy writes them sorted by (i, j) with their edit distances.
+ * In MJ_VERIFY_LEARNED mode a band model must have been trained or loaded. */
+int mj_join(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n,
+            const mj_params* p, void* stream, uint64_t* count);
+int mj_result_copy(mj_ctx* ctx, uint32_t* d_i, uint32_t* d_j, uint32_t* d_ed, void* stream);
+
+/* mj_join on HOST buffers: copies bytes and offsets to the device on
+ * `stream`, runs mj_join, and leaves the result for mj_result_copy_host,
+ * which copies it to host buffers of *count entries each (pinned memory
+ * avoids a staging copy). */
+int mj_join_host(mj_ctx* ctx, const uint8_t* h_bytes, const int64_t* h_offsets, uint32_t n,
+                 const mj_params* p, void* stream, uint64_t* count);
+int mj_result_copy_host(mj_ctx* ctx, uint32_t* h_i, uint32_t* h_j, uint32_t* h_ed, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MINJOIN_H */

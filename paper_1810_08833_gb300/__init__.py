@@ -1,0 +1,247 @@
+"""Python binding of the GB300 MinJoin library (include/minjoin.h).
+
+Argument marshalling only: every step of the join runs in the CUDA kernels of
+libminjoin.so.  PyTorch supplies device memory and the current stream.  There
+is no CPU fallback: if the library is missing or no GPU is present, the calls
+raise.
+
+Functions mirror the C entry points:
+    derive      mj_derive       step a1 (Sec. 2.2 parameters)
+    partition   mj_partition    steps a2-a4 (Alg. 1-2)
+    candidates  mj_candidates   steps a2-a7 (Alg. 3 lines 4-20)
+    verify      mj_verify       step a8 (Ukkonen band, Sec. 3)
+    join        mj_join         the whole path (Alg. 3)
+    join_host   mj_join_host    the whole path from/to host memory
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libminjoin.so")
+
+MJ_VERIFY_PLAIN = 0
+MJ_VERIFY_LEARNED = 1
+
+
+class MinJoinError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where} failed with status {status}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_uint32), ("T", ctypes.c_uint32), ("q", ctypes.c_uint32),
+                ("r_min", ctypes.c_int32), ("seed", ctypes.c_uint64), ("verify_mode", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32)]
+
+
+class Derived(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_uint32), ("bits", ctypes.c_uint32), ("q", ctypes.c_uint32),
+                ("T", ctypes.c_uint32), ("K", ctypes.c_uint32), ("r_max", ctypes.c_int32),
+                ("N", ctypes.c_uint64), ("rank", ctypes.c_uint8 * 256)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_strings", ctypes.c_uint64), ("n_bytes", ctypes.c_uint64), ("n_partitions", ctypes.c_uint64),
+                ("n_raw_pairs", ctypes.c_uint64), ("n_candidates", ctypes.c_uint64),
+                ("n_output", ctypes.c_uint64), ("key_collisions", ctypes.c_uint64),
+                ("band_cells", ctypes.c_uint64), ("first_pass_settled", ctypes.c_uint64),
+                ("fallback_pairs", ctypes.c_uint64), ("device_flags", ctypes.c_uint32),
+                ("ms_derive", ctypes.c_float), ("ms_partition", ctypes.c_float),
+                ("ms_join_filter", ctypes.c_float), ("ms_verify", ctypes.c_float), ("ms_total", ctypes.c_float)]
+
+
+VP = ctypes.c_void_p
+U64 = ctypes.c_uint64
+U32 = ctypes.c_uint32
+
+_SIGS = {
+    "mj_params_default": (None, [ctypes.POINTER(Params), U32]),
+    "mj_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "mj_create": (ctypes.c_int, [ctypes.POINTER(VP), ctypes.c_int]),
+    "mj_destroy": (None, [VP]),
+    "mj_get_stats": (ctypes.c_int, [VP, ctypes.POINTER(Stats)]),
+    "mj_derive": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, ctypes.POINTER(Derived)]),
+    "mj_partition": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, VP, ctypes.POINTER(U64)]),
+    "mj_partition_copy": (ctypes.c_int, [VP, VP, VP, VP, VP, VP]),
+    "mj_candidates": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, VP, ctypes.POINTER(U64)]),
+    "mj_candidates_copy": (ctypes.c_int, [VP, VP, VP, VP]),
+    "mj_verify": (ctypes.c_int, [VP, VP, VP, U32, VP, VP, VP, U64, U32, VP, VP]),
+    "mj_join": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, ctypes.POINTER(U64)]),
+    "mj_result_copy": (ctypes.c_int, [VP, VP, VP, VP, VP]),
+    "mj_join_host": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, ctypes.POINTER(U64)]),
+    "mj_result_copy_host": (ctypes.c_int, [VP, VP, VP, VP, VP]),
+}
+
+_lib = None
+
+
+def library(path: str | None = None) -> ctypes.CDLL:
+    """Load libminjoin.so (built by paper_1810_08833_gb300.build.build())."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"MinJoin CUDA library not built: {p} is missing "
+                               "(run paper_1810_08833_gb300.build.build())")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise MinJoinError(status, where, library().mj_strerror(status).decode())
+
+
+def params(K: int, T: int = 0, q: int = 0, r_min: int = 1, seed: int = 0x5EED,
+           verify_mode: int = MJ_VERIFY_PLAIN, flags: int = 0) -> Params:
+    p = Params()
+    library().mj_params_default(ctypes.byref(p), K)
+    p.T, p.q, p.r_min, p.seed, p.verify_mode, p.flags = T, q, r_min, seed, verify_mode, flags
+    return p
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return t.data_ptr() if t.numel() else None
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _check_inputs(data, offsets):
+    import torch
+    if not (data.is_cuda and offsets.is_cuda):
+        raise ValueError("bytes and offsets must be CUDA tensors")
+    if data.dtype != torch.uint8 or offsets.dtype != torch.int64:
+        raise ValueError("bytes must be uint8 and offsets int64")
+    if not (data.is_contiguous() and offsets.is_contiguous()):
+        raise ValueError("bytes and offsets must be contiguous")
+    return offsets.numel() - 1
+
+
+class Context:
+    """One mj_ctx on a CUDA device (not thread-safe)."""
+
+    def __init__(self, device: int = 0):
+        self._lib = library()
+        h = VP()
+        _check(self._lib.mj_create(ctypes.byref(h), device), "mj_create")
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mj_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self._lib.mj_get_stats(self._h, ctypes.byref(s)), "mj_get_stats")
+        return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+    def derive(self, data, offsets, p: Params, stream=None) -> dict:
+        n = _check_inputs(data, offsets)
+        d = Derived()
+        _check(self._lib.mj_derive(self._h, _ptr(data), _ptr(offsets), n, ctypes.byref(p), _stream(stream),
+                                   ctypes.byref(d)), "mj_derive")
+        return {"sigma": d.sigma, "bits": d.bits, "q": d.q, "T": d.T, "K": d.K, "r_max": d.r_max, "N": d.N,
+                "rank": np.frombuffer(bytes(d.rank), dtype=np.uint8).copy()}
+
+    def partition(self, data, offsets, p: Params, table=None, stream=None):
+        import torch
+        n = _check_inputs(data, offsets)
+        cnt = U64()
+        _check(self._lib.mj_partition(self._h, _ptr(data), _ptr(offsets), n, ctypes.byref(p), _ptr(table),
+                                      _stream(stream), ctypes.byref(cnt)), "mj_partition")
+        m = cnt.value
+        dev = data.device
+        sid = torch.empty(m, dtype=torch.int32, device=dev)
+        pos = torch.empty(m, dtype=torch.int32, device=dev)
+        ln = torch.empty(m, dtype=torch.int32, device=dev)
+        key = torch.empty(m, dtype=torch.int64, device=dev)
+        _check(self._lib.mj_partition_copy(self._h, _ptr(sid), _ptr(pos), _ptr(ln), _ptr(key), _stream(stream)),
+               "mj_partition_copy")
+        return sid, pos, ln, key
+
+    def candidates(self, data, offsets, p: Params, table=None, stream=None):
+        import torch
+        n = _check_inputs(data, offsets)
+        cnt = U64()
+        _check(self._lib.mj_candidates(self._h, _ptr(data), _ptr(offsets), n, ctypes.byref(p), _ptr(table),
+                                       _stream(stream), ctypes.byref(cnt)), "mj_candidates")
+        m = cnt.value
+        ci = torch.empty(m, dtype=torch.int32, device=data.device)
+        cj = torch.empty(m, dtype=torch.int32, device=data.device)
+        _check(self._lib.mj_candidates_copy(self._h, _ptr(ci), _ptr(cj), _stream(stream)), "mj_candidates_copy")
+        return ci, cj
+
+    def verify(self, data, offsets, i, j, K: int, k=None, stream=None):
+        import torch
+        n = _check_inputs(data, offsets)
+        m = i.numel()
+        for t in (i, j) + ((k,) if k is not None else ()):
+            if not t.is_cuda or t.dtype != torch.int32 or not t.is_contiguous() or t.numel() != m:
+                raise ValueError("pair index and band tensors must be contiguous int32 CUDA tensors of equal size")
+        ed = torch.empty(m, dtype=torch.int32, device=data.device)
+        _check(self._lib.mj_verify(self._h, _ptr(data), _ptr(offsets), n, _ptr(i), _ptr(j), _ptr(k), m, K,
+                                   _stream(stream), _ptr(ed)), "mj_verify")
+        return ed
+
+    def join(self, data, offsets, p: Params, stream=None):
+        import torch
+        n = _check_inputs(data, offsets)
+        cnt = U64()
+        _check(self._lib.mj_join(self._h, _ptr(data), _ptr(offsets), n, ctypes.byref(p), _stream(stream),
+                                 ctypes.byref(cnt)), "mj_join")
+        m = cnt.value
+        oi = torch.empty(m, dtype=torch.int32, device=data.device)
+        oj = torch.empty(m, dtype=torch.int32, device=data.device)
+        oe = torch.empty(m, dtype=torch.int32, device=data.device)
+        _check(self._lib.mj_result_copy(self._h, _ptr(oi), _ptr(oj), _ptr(oe), _stream(stream)), "mj_result_copy")
+        return oi, oj, oe
+
+    def join_host(self, data: np.ndarray, offsets: np.ndarray, p: Params, stream=None, out=None):
+        """Host buffers in, host arrays out (pinned buffers avoid staging copies)."""
+        n = offsets.shape[0] - 1
+        data = np.ascontiguousarray(data, dtype=np.uint8)
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        cnt = U64()
+        _check(self._lib.mj_join_host(self._h, data.ctypes.data if data.size else None, offsets.ctypes.data, n,
+                                      ctypes.byref(p), _stream(stream), ctypes.byref(cnt)), "mj_join_host")
+        m = cnt.value
+        if out is None:
+            out = tuple(np.empty(m, dtype=np.uint32) for _ in range(3))
+        oi, oj, oe = (o[:m] for o in out)
+        _check(self._lib.mj_result_copy_host(self._h, oi.ctypes.data if m else None, oj.ctypes.data if m else None,
+                                             oe.ctypes.data if m else None, _stream(stream)), "mj_result_copy_host")
+        return oi, oj, oe

@@ -1,0 +1,646 @@
+// C ABI of the MinJoin library: context, workspace and the host-side
+// orchestration of steps a1-a8 (Alg. 1-3 of the MinJoin paper).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "mj_internal.cuh"
+
+namespace mj {
+
+static thread_local char g_cuda_err[512];
+
+void set_last_cuda_error(cudaError_t e, const char* expr, const char* file, int line) {
+  snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s (%s:%d)", cudaGetErrorString(e), expr, file, line);
+}
+
+int Buf::reserve(size_t need, cudaStream_t s) {
+  if (need <= bytes && p) return MJ_OK;
+  if (p) {
+    // the old buffer may still be read by queued work on `s`
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      set_last_cuda_error(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+      return MJ_ERR_CUDA;
+    }
+    cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  size_t alloc = need < 256 ? 256 : need + need / 8;
+  cudaError_t e = cudaMalloc(&p, alloc);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+    return MJ_ERR_OOM;
+  }
+  bytes = alloc;
+  return MJ_OK;
+}
+
+void Buf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+// ---------------------------------------------------------------- parameter rules
+// Sec. 2.2: q = 3 log_|Sigma|(N/T), read as the smallest q >= 1 with
+// |Sigma|^q >= (N/T)^3, decided in integers as |Sigma|^q T^3 >= N^3.
+static uint32_t q_rule(uint64_t N, uint32_t T, uint32_t sigma) {
+  if (sigma <= 1 || T == 0) return 1;
+  const unsigned __int128 lhs_t = (unsigned __int128)T * T * T;
+  const unsigned __int128 rhs = (unsigned __int128)N * N * N;
+  unsigned __int128 pw = 1;
+  uint32_t q = 0;
+  while (pw * lhs_t < rhs && q < 64) {
+    pw *= sigma;
+    ++q;
+  }
+  return q ? q : 1;
+}
+
+// Alg. 2 line 2, floor division, raised to r_min.
+static int32_t radius_rule(int64_t slen, int64_t q, int64_t T, int32_t r_min) {
+  int64_t num = slen - q + 1 - T, den = 2 * T + 2;
+  int64_t r = num >= 0 ? num / den : -((-num + den - 1) / den);
+  return r < r_min ? r_min : (int32_t)r;
+}
+
+static uint64_t splitmix(uint64_t x) {  // host-side seed expansion (Steele, Lea, Flood 2014)
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+static int bits_for(uint64_t v) {  // bits needed to hold 0..v
+  int b = 1;
+  while (b < 64 && (v >> b)) ++b;
+  return b;
+}
+
+}  // namespace mj
+
+using namespace mj;
+
+struct mj_ctx {
+  int device = 0;
+  mj_stats stats{};
+  Derived d;
+  // pinned host staging for small readbacks
+  unsigned long long* h_small = nullptr;
+  // workspace
+  Buf hist, dev_flags, small;
+  Buf bitmap, tile_count, tile_off, scan_tmp;
+  Buf anchor_pos, anchor_sid;
+  Buf rec_sid, rec_pos, rec_len, rec_slen, rec_h61;
+  Buf keys, keys_alt, idx, idx_alt, sort_tmp;
+  Buf s_sid, s_pos, s_slen, s_len, s_h61;
+  Buf pair_count, pair_off, pairs, pairs_alt;
+  Buf uflags, uoffs, cand_i, cand_j;
+  Buf planes, ed, eflags, eoffs;
+  Buf out_i, out_j, out_ed;
+  Buf in_bytes, in_offsets;  // staging for mj_join_host
+  uint64_t n_part = 0, n_cand = 0, n_out = 0;
+  bool have_part = false, have_cand = false, have_out = false;
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
+
+int readback(mj_ctx* c, const void* d_src, size_t bytes, cudaStream_t s) {
+  MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small, d_src, bytes, cudaMemcpyDeviceToHost, s));
+  MJ_CUDA_TRY(cudaStreamSynchronize(s));
+  return MJ_OK;
+}
+
+int check_inputs(const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const mj_params* p) {
+  if (!d_offsets || !p) return MJ_ERR_ARG;
+  if (n > 0 && !d_bytes) {
+    // an all-empty input may pass a null byte pointer; it is checked later
+  }
+  if (p->K > (1u << 20) || p->r_min < 0) return MJ_ERR_ARG;
+  return MJ_OK;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    cudaGetLastError();
+    return 0.f;
+  }
+  return ms;
+}
+
+// a1: alphabet, longest length, q, T, radius bound.
+int derive(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const mj_params* p,
+           cudaStream_t s) {
+  MJ_TRY(c->hist.reserve(256 * sizeof(unsigned long long) + 64, s));
+  unsigned long long* hist = c->hist.as<unsigned long long>();
+  unsigned long long* maxlen = hist + 256;
+  MJ_TRY(readback(c, d_offsets + n, sizeof(int64_t), s));
+  const uint64_t nbytes = c->h_small[0];
+  if (nbytes >= (1ull << 32)) return MJ_ERR_UNSUPPORTED;
+  if (nbytes > 0 && !d_bytes) return MJ_ERR_ARG;
+  MJ_TRY(launch_byte_histogram(d_bytes, nbytes, hist, s));
+  MJ_TRY(launch_max_length(d_offsets, n, maxlen, s));
+  MJ_TRY(readback(c, hist, 257 * sizeof(unsigned long long), s));
+  Derived& d = c->d;
+  d = Derived();
+  uint32_t sigma = 0;
+  for (int b = 0; b < 256; ++b) {
+    if (c->h_small[b]) d.rank[b] = (uint8_t)sigma++;
+  }
+  d.sigma = sigma;
+  d.bits = 1;
+  while ((1u << d.bits) < sigma) ++d.bits;
+  d.N = c->h_small[256];
+  d.K = p->K;
+  d.T = p->T ? p->T : p->K;
+  if (d.T == 0) d.T = 1;
+  d.q = p->q ? p->q : q_rule(d.N, d.T, sigma);
+  d.q = std::max<uint32_t>(1, std::min<uint32_t>(d.q, 64 / d.bits));
+  d.r_min = p->r_min;
+  d.r_max = radius_rule((int64_t)d.N, d.q, d.T, d.r_min);
+  d.seed = p->seed;
+  c->stats.n_strings = n;
+  c->stats.n_bytes = nbytes;
+  return MJ_OK;
+}
+
+uint64_t key_base_for(uint64_t seed) {
+  const uint64_t M61 = (1ull << 61) - 1;
+  return 257 + splitmix(seed ^ 0x6b6579626173650aull) % (M61 - 1024);
+}
+
+// a2-a4 (after derive): records in c->rec_*.
+int partition(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const uint64_t* d_table,
+              cudaStream_t s) {
+  const Derived& d = c->d;
+  const uint64_t nbytes = c->stats.n_bytes;
+  if (d.r_max > 8192) return MJ_ERR_UNSUPPORTED;
+  PartitionArgs a;
+  a.bytes = d_bytes;
+  a.offsets = d_offsets;
+  a.n = n;
+  a.nbytes = nbytes;
+  a.q = d.q;
+  a.bits = d.bits;
+  a.T = d.T;
+  a.r_min = d.r_min;
+  a.r_max = d.r_max;
+  a.seed32 = (uint32_t)d.seed ^ (uint32_t)(d.seed >> 32);
+  a.seed64 = d.seed;
+  a.table = d_table;
+  memcpy(a.rank, d.rank, 256);
+  const uint64_t tiles = partition_num_tiles(nbytes);
+  c->n_part = 0;
+  if (tiles == 0) return MJ_OK;
+  MJ_TRY(c->dev_flags.reserve(64, s));
+  MJ_CUDA_TRY(cudaMemsetAsync(c->dev_flags.p, 0, 64, s));
+  MJ_TRY(c->bitmap.reserve(tiles * (kPartTile / 32) * sizeof(uint32_t), s));
+  MJ_TRY(c->tile_count.reserve(tiles * sizeof(uint32_t), s));
+  MJ_TRY(c->tile_off.reserve(tiles * sizeof(uint32_t) + 16, s));
+  MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(tiles), s));
+  MJ_TRY(launch_anchor_flags(a, c->bitmap.as<uint32_t>(), c->tile_count.as<uint32_t>(),
+                             c->dev_flags.as<uint32_t>(), s));
+  uint32_t* total = c->tile_off.as<uint32_t>() + tiles;
+  MJ_TRY(launch_exclusive_scan_u32(c->tile_count.as<uint32_t>(), c->tile_off.as<uint32_t>(), tiles,
+                                   c->scan_tmp.p, total, s));
+  MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small, total, 4, cudaMemcpyDeviceToHost, s));
+  MJ_CUDA_TRY(cudaMemcpyAsync((char*)c->h_small + 8, c->dev_flags.p, 4, cudaMemcpyDeviceToHost, s));
+  MJ_CUDA_TRY(cudaStreamSynchronize(s));
+  const uint32_t n_anchor = *(uint32_t*)c->h_small;
+  c->stats.device_flags |= *(uint32_t*)((char*)c->h_small + 8);
+  if (c->stats.device_flags) return MJ_ERR_DEVICE;
+  MJ_TRY(c->anchor_pos.reserve((size_t)n_anchor * 4 + 16, s));
+  MJ_TRY(c->anchor_sid.reserve((size_t)n_anchor * 4 + 16, s));
+  MJ_TRY(launch_anchor_emit(a, c->bitmap.as<uint32_t>(), c->tile_off.as<uint32_t>(), c->anchor_pos.as<uint32_t>(),
+                            c->anchor_sid.as<uint32_t>(), s));
+  MJ_TRY(c->rec_sid.reserve((size_t)n_anchor * 4 + 16, s));
+  MJ_TRY(c->rec_pos.reserve((size_t)n_anchor * 4 + 16, s));
+  MJ_TRY(c->rec_len.reserve((size_t)n_anchor * 4 + 16, s));
+  MJ_TRY(c->rec_slen.reserve((size_t)n_anchor * 4 + 16, s));
+  MJ_TRY(c->rec_h61.reserve((size_t)n_anchor * 8 + 16, s));
+  MJ_TRY(launch_partition_records(d_bytes, d_offsets, c->anchor_pos.as<uint32_t>(), c->anchor_sid.as<uint32_t>(),
+                                  n_anchor, key_base_for(d.seed), c->rec_sid.as<uint32_t>(),
+                                  c->rec_pos.as<uint32_t>(), c->rec_len.as<uint32_t>(), c->rec_slen.as<uint32_t>(),
+                                  c->rec_h61.as<uint64_t>(), s));
+  c->n_part = n_anchor;
+  c->stats.n_partitions = n_anchor;
+  return MJ_OK;
+}
+
+// a5-a7 (after partition): candidates in c->cand_i/j (sorted, distinct).
+int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, uint32_t flags,
+               cudaStream_t s) {
+  const Derived& d = c->d;
+  const uint32_t nr = (uint32_t)c->n_part;
+  c->n_cand = 0;
+  c->stats.n_raw_pairs = 0;
+  c->stats.key_collisions = 0;
+  if (nr == 0) return MJ_OK;
+  const int slen_bits = bits_for(d.N);
+  MJ_TRY(c->keys.reserve((size_t)nr * 8, s));
+  MJ_TRY(c->keys_alt.reserve((size_t)nr * 8, s));
+  MJ_TRY(c->idx.reserve((size_t)nr * 4, s));
+  MJ_TRY(c->idx_alt.reserve((size_t)nr * 4, s));
+  MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(nr), s));
+  MJ_TRY(launch_make_group_keys(c->rec_len.as<uint32_t>(), c->rec_slen.as<uint32_t>(), c->rec_h61.as<uint64_t>(), nr,
+                                slen_bits, c->keys.as<uint64_t>(), c->idx.as<uint32_t>(), s));
+  bool alt = false;
+  MJ_TRY(radix_sort_u64(c->keys.as<uint64_t>(), c->keys_alt.as<uint64_t>(), c->idx.as<uint32_t>(),
+                        c->idx_alt.as<uint32_t>(), nr, 0, 32 + slen_bits, c->sort_tmp.p, &alt, s));
+  const uint64_t* skeys = alt ? c->keys_alt.as<uint64_t>() : c->keys.as<uint64_t>();
+  const uint32_t* sidx = alt ? c->idx_alt.as<uint32_t>() : c->idx.as<uint32_t>();
+  MJ_TRY(c->s_sid.reserve((size_t)nr * 4, s));
+  MJ_TRY(c->s_pos.reserve((size_t)nr * 4, s));
+  MJ_TRY(c->s_slen.reserve((size_t)nr * 4, s));
+  MJ_TRY(c->s_len.reserve((size_t)nr * 4, s));
+  MJ_TRY(c->s_h61.reserve((size_t)nr * 8, s));
+  SortedRecs r{c->s_sid.as<uint32_t>(), c->s_pos.as<uint32_t>(), c->s_slen.as<uint32_t>(), c->s_len.as<uint32_t>(),
+               c->s_h61.as<uint64_t>()};
+  MJ_TRY(launch_gather_records(sidx, nr, c->rec_sid.as<uint32_t>(), c->rec_pos.as<uint32_t>(),
+                               c->rec_slen.as<uint32_t>(), c->rec_len.as<uint32_t>(), c->rec_h61.as<uint64_t>(), r,
+                               s));
+  if (flags & 1u) {
+    MJ_TRY(c->small.reserve(64, s));
+    MJ_CUDA_TRY(cudaMemsetAsync(c->small.p, 0, 8, s));
+    MJ_TRY(launch_key_check(skeys, r, d_bytes, d_offsets, nr, slen_bits, c->small.as<unsigned long long>(), s));
+    MJ_TRY(readback(c, c->small.p, 8, s));
+    c->stats.key_collisions = c->h_small[0];
+  }
+  MJ_TRY(c->pair_count.reserve((size_t)nr * 4, s));
+  MJ_TRY(c->pair_off.reserve((size_t)nr * 8 + 16, s));
+  MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(nr), s));
+  MJ_TRY(launch_count_pairs(skeys, r, nr, slen_bits, d.K, c->pair_count.as<uint32_t>(), s));
+  uint64_t* total = c->pair_off.as<uint64_t>() + nr;
+  MJ_TRY(launch_exclusive_scan_u32_to_u64(c->pair_count.as<uint32_t>(), c->pair_off.as<uint64_t>(), nr,
+                                          c->scan_tmp.p, total, s));
+  MJ_TRY(readback(c, total, 8, s));
+  const uint64_t raw = c->h_small[0];
+  c->stats.n_raw_pairs = raw;
+  if (raw == 0) return MJ_OK;
+  if (raw >= (1ull << 32)) return MJ_ERR_UNSUPPORTED;
+  MJ_TRY(c->pairs.reserve(raw * 8, s));
+  MJ_TRY(c->pairs_alt.reserve(raw * 8, s));
+  MJ_TRY(launch_fill_pairs(skeys, r, nr, slen_bits, d.K, c->pair_off.as<uint64_t>(), c->pairs.as<uint64_t>(), s));
+  MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(raw), s));
+  const int nb = bits_for(n ? n - 1 : 0);
+  MJ_TRY(radix_sort_u64(c->pairs.as<uint64_t>(), c->pairs_alt.as<uint64_t>(), nullptr, nullptr, raw, 0, 32 + nb,
+                        c->sort_tmp.p, &alt, s));
+  const uint64_t* sp = alt ? c->pairs_alt.as<uint64_t>() : c->pairs.as<uint64_t>();
+  MJ_TRY(c->uflags.reserve(raw * 4, s));
+  MJ_TRY(c->uoffs.reserve(raw * 4 + 16, s));
+  MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(raw), s));
+  MJ_TRY(launch_unique_flags(sp, raw, c->uflags.as<uint32_t>(), s));
+  uint32_t* utotal = c->uoffs.as<uint32_t>() + raw;
+  MJ_TRY(launch_exclusive_scan_u32(c->uflags.as<uint32_t>(), c->uoffs.as<uint32_t>(), raw, c->scan_tmp.p, utotal, s));
+  MJ_TRY(readback(c, utotal, 4, s));
+  const uint32_t nc = *(uint32_t*)c->h_small;
+  MJ_TRY(c->cand_i.reserve((size_t)nc * 4 + 16, s));
+  MJ_TRY(c->cand_j.reserve((size_t)nc * 4 + 16, s));
+  MJ_TRY(launch_compact_pairs(sp, c->uflags.as<uint32_t>(), c->uoffs.as<uint32_t>(), raw, c->cand_i.as<uint32_t>(),
+                              c->cand_j.as<uint32_t>(), s));
+  c->n_cand = nc;
+  c->stats.n_candidates = nc;
+  return MJ_OK;
+}
+
+// a8 on arbitrary pairs (rank codes from c->d).
+int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const uint32_t* d_i, const uint32_t* d_j,
+           const uint32_t* d_k, uint64_t m, uint32_t K, uint32_t kmax, uint32_t* d_ed, bool count_cells,
+           cudaStream_t s) {
+  const Derived& d = c->d;
+  if (m == 0) return MJ_OK;
+  if (kmax >= (1u << 16)) return MJ_ERR_UNSUPPORTED;
+  const uint64_t nbytes = c->stats.n_bytes;
+  const uint32_t GW = plane_guard_words(kmax);
+  const uint64_t PW = (nbytes + 31) / 32 + 2 * (uint64_t)GW;
+  MJ_TRY(c->planes.reserve(PW * d.bits * 4, s));
+  RankTable rt;
+  memcpy(rt.r, d.rank, 256);
+  MJ_TRY(launch_build_planes(d_bytes, nbytes, rt, d.bits, c->planes.as<uint32_t>(), PW, GW, s));
+  MJ_TRY(c->dev_flags.reserve(64, s));
+  MJ_CUDA_TRY(cudaMemsetAsync(c->dev_flags.p, 0, 64, s));
+  MJ_TRY(c->small.reserve(64, s));
+  MJ_CUDA_TRY(cudaMemsetAsync(c->small.p, 0, 16, s));
+  VerifyArgs a;
+  a.planes = c->planes.as<uint32_t>();
+  a.bits = d.bits;
+  a.bytes = d_bytes;
+  a.offsets = d_offsets;
+  a.n_strings = (uint32_t)c->stats.n_strings;
+  a.pi = d_i;
+  a.pj = d_j;
+  a.pk = d_k;
+  a.K = K;
+  a.m = m;
+  a.ed = d_ed;
+  a.cells = count_cells ? c->small.as<unsigned long long>() : nullptr;
+  a.dev_flags = c->dev_flags.as<uint32_t>();
+  MJ_TRY(launch_verify(a, rt, PW, GW, kmax, s));
+  return MJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mj_params_default(mj_params* p, uint32_t K) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->K = K;
+  p->T = 0;
+  p->q = 0;
+  p->r_min = 1;
+  p->seed = 0x5EED;
+  p->verify_mode = MJ_VERIFY_PLAIN;
+  p->flags = 0;
+}
+
+const char* mj_strerror(int status) {
+  switch (status) {
+    case MJ_OK: return "ok";
+    case MJ_ERR_ARG: return "invalid argument";
+    case MJ_ERR_CUDA: return g_cuda_err[0] ? g_cuda_err : "CUDA runtime error";
+    case MJ_ERR_OOM: return "device allocation failed";
+    case MJ_ERR_DEVICE: return "device-side check failed";
+    case MJ_ERR_UNSUPPORTED: return "input outside the supported range";
+    case MJ_ERR_TIMEOUT: return "bounded device wait timed out";
+    case MJ_ERR_STATE: return "invalid call order";
+    default: return "unknown status";
+  }
+}
+
+int mj_create(mj_ctx** ctx, int device) {
+  if (!ctx) return MJ_ERR_ARG;
+  *ctx = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return MJ_ERR_CUDA;
+  }
+  DeviceGuard g(device);
+  mj_ctx* c = new mj_ctx();
+  c->device = device;
+  if (cudaMallocHost(&c->h_small, 4096) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return MJ_ERR_OOM;
+  }
+  for (auto& e : c->ev) {
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      mj_destroy(c);
+      return MJ_ERR_CUDA;
+    }
+  }
+  *ctx = c;
+  return MJ_OK;
+}
+
+void mj_destroy(mj_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  cudaDeviceSynchronize();
+  Buf* bufs[] = {&c->hist, &c->dev_flags, &c->small, &c->bitmap, &c->tile_count, &c->tile_off, &c->scan_tmp,
+                 &c->anchor_pos, &c->anchor_sid, &c->rec_sid, &c->rec_pos, &c->rec_len, &c->rec_slen,
+                 &c->rec_h61, &c->keys, &c->keys_alt, &c->idx, &c->idx_alt, &c->sort_tmp, &c->s_sid, &c->s_pos,
+                 &c->s_slen, &c->s_len, &c->s_h61, &c->pair_count, &c->pair_off, &c->pairs, &c->pairs_alt,
+                 &c->uflags, &c->uoffs, &c->cand_i, &c->cand_j, &c->planes, &c->ed, &c->eflags, &c->eoffs,
+                 &c->out_i, &c->out_j, &c->out_ed, &c->in_bytes, &c->in_offsets};
+  for (Buf* b : bufs) b->release();
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->h_small) cudaFreeHost(c->h_small);
+  delete c;
+}
+
+int mj_get_stats(const mj_ctx* c, mj_stats* out) {
+  if (!c || !out) return MJ_ERR_ARG;
+  *out = c->stats;
+  return MJ_OK;
+}
+
+int mj_derive(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const mj_params* p,
+              void* stream, mj_derived* out) {
+  if (!c || !out) return MJ_ERR_ARG;
+  MJ_TRY(check_inputs(d_bytes, d_offsets, n, p));
+  DeviceGuard g(c->device);
+  c->stats = mj_stats{};
+  MJ_TRY(derive(c, d_bytes, d_offsets, n, p, S(stream)));
+  const Derived& d = c->d;
+  out->sigma = d.sigma;
+  out->bits = d.bits;
+  out->q = d.q;
+  out->T = d.T;
+  out->K = d.K;
+  out->r_max = d.r_max;
+  out->N = d.N;
+  memcpy(out->rank, d.rank, 256);
+  return MJ_OK;
+}
+
+int mj_partition(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const mj_params* p,
+                 const uint64_t* d_table, void* stream, uint64_t* count) {
+  if (!c || !count) return MJ_ERR_ARG;
+  MJ_TRY(check_inputs(d_bytes, d_offsets, n, p));
+  DeviceGuard g(c->device);
+  cudaStream_t s = S(stream);
+  c->stats = mj_stats{};
+  c->have_part = false;
+  MJ_TRY(derive(c, d_bytes, d_offsets, n, p, s));
+  MJ_TRY(partition(c, d_bytes, d_offsets, n, d_table, s));
+  MJ_CUDA_TRY(cudaStreamSynchronize(s));
+  c->have_part = true;
+  *count = c->n_part;
+  return MJ_OK;
+}
+
+int mj_partition_copy(mj_ctx* c, uint32_t* d_sid, uint32_t* d_pos, uint32_t* d_len, uint64_t* d_key,
+                      void* stream) {
+  if (!c) return MJ_ERR_ARG;
+  if (!c->have_part) return MJ_ERR_STATE;
+  DeviceGuard g(c->device);
+  cudaStream_t s = S(stream);
+  const size_t n = c->n_part;
+  if (!n) return MJ_OK;
+  if (d_sid) MJ_CUDA_TRY(cudaMemcpyAsync(d_sid, c->rec_sid.p, n * 4, cudaMemcpyDeviceToDevice, s));
+  if (d_pos) MJ_CUDA_TRY(cudaMemcpyAsync(d_pos, c->rec_pos.p, n * 4, cudaMemcpyDeviceToDevice, s));
+  if (d_len) MJ_CUDA_TRY(cudaMemcpyAsync(d_len, c->rec_len.p, n * 4, cudaMemcpyDeviceToDevice, s));
+  if (d_key) MJ_CUDA_TRY(cudaMemcpyAsync(d_key, c->rec_h61.p, n * 8, cudaMemcpyDeviceToDevice, s));
+  return MJ_OK;
+}
+
+int mj_candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const mj_params* p,
+                  const uint64_t* d_table, void* stream, uint64_t* count) {
+  if (!c || !count) return MJ_ERR_ARG;
+  MJ_TRY(check_inputs(d_bytes, d_offsets, n, p));
+  DeviceGuard g(c->device);
+  cudaStream_t s = S(stream);
+  c->stats = mj_stats{};
+  c->have_part = c->have_cand = false;
+  MJ_TRY(derive(c, d_bytes, d_offsets, n, p, s));
+  MJ_TRY(partition(c, d_bytes, d_offsets, n, d_table, s));
+  c->have_part = true;
+  MJ_TRY(candidates(c, d_bytes, d_offsets, n, p->flags, s));
+  MJ_CUDA_TRY(cudaStreamSynchronize(s));
+  c->have_cand = true;
+  *count = c->n_cand;
+  return MJ_OK;
+}
+
+int mj_candidates_copy(mj_ctx* c, uint32_t* d_i, uint32_t* d_j, void* stream) {
+  if (!c) return MJ_ERR_ARG;
+  if (!c->have_cand) return MJ_ERR_STATE;
+  DeviceGuard g(c->device);
+  cudaStream_t s = S(stream);
+  const size_t n = c->n_cand;
+  if (!n) return MJ_OK;
+  if (d_i) MJ_CUDA_TRY(cudaMemcpyAsync(d_i, c->cand_i.p, n * 4, cudaMemcpyDeviceToDevice, s));
+  if (d_j) MJ_CUDA_TRY(cudaMemcpyAsync(d_j, c->cand_j.p, n * 4, cudaMemcpyDeviceToDevice, s));
+  return MJ_OK;
+}
+
+int mj_verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const uint32_t* d_i,
+              const uint32_t* d_j, const uint32_t* d_k, uint64_t m, uint32_t K, void* stream, uint32_t* d_ed) {
+  if (!c || !d_offsets) return MJ_ERR_ARG;
+  if (m && (!d_i || !d_j || !d_ed)) return MJ_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = S(stream);
+  mj_params p;
+  mj_params_default(&p, K);
+  c->stats = mj_stats{};
+  MJ_TRY(derive(c, d_bytes, d_offsets, n, &p, s));
+  uint32_t kmax = K;
+  if (d_k) {
+    // the widest per-pair band sizes the kernel
+    std::vector<uint32_t> hk(m);
+    MJ_CUDA_TRY(cudaMemcpyAsync(hk.data(), d_k, m * 4, cudaMemcpyDeviceToHost, s));
+    MJ_CUDA_TRY(cudaStreamSynchronize(s));
+    kmax = 0;
+    for (uint32_t v : hk) kmax = std::max(kmax, v);
+  }
+  return verify(c, d_bytes, d_offsets, d_i, d_j, d_k, m, K, kmax, d_ed, true, s);
+}
+
+int mj_join(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const mj_params* p,
+            void* stream, uint64_t* count) {
+  if (!c || !count) return MJ_ERR_ARG;
+  MJ_TRY(check_inputs(d_bytes, d_offsets, n, p));
+  if (p->verify_mode != MJ_VERIFY_PLAIN) return MJ_ERR_STATE;
+  DeviceGuard g(c->device);
+  cudaStream_t s = S(stream);
+  c->stats = mj_stats{};
+  c->have_part = c->have_cand = c->have_out = false;
+  MJ_CUDA_TRY(cudaEventRecord(c->ev[0], s));
+  MJ_TRY(derive(c, d_bytes, d_offsets, n, p, s));
+  MJ_CUDA_TRY(cudaEventRecord(c->ev[1], s));
+  MJ_TRY(partition(c, d_bytes, d_offsets, n, nullptr, s));
+  c->have_part = true;
+  MJ_CUDA_TRY(cudaEventRecord(c->ev[2], s));
+  MJ_TRY(candidates(c, d_bytes, d_offsets, n, p->flags, s));
+  c->have_cand = true;
+  MJ_CUDA_TRY(cudaEventRecord(c->ev[3], s));
+  const uint64_t m = c->n_cand;
+  c->n_out = 0;
+  if (m) {
+    MJ_TRY(c->ed.reserve(m * 4, s));
+    MJ_TRY(verify(c, d_bytes, d_offsets, c->cand_i.as<uint32_t>(), c->cand_j.as<uint32_t>(), nullptr, m, p->K, p->K,
+                  c->ed.as<uint32_t>(), true, s));
+    MJ_TRY(c->eflags.reserve(m * 4, s));
+    MJ_TRY(c->eoffs.reserve(m * 4 + 16, s));
+    MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(m), s));
+    MJ_TRY(launch_ed_flags(c->ed.as<uint32_t>(), m, p->K, c->eflags.as<uint32_t>(), s));
+    uint32_t* tot = c->eoffs.as<uint32_t>() + m;
+    MJ_TRY(launch_exclusive_scan_u32(c->eflags.as<uint32_t>(), c->eoffs.as<uint32_t>(), m, c->scan_tmp.p, tot, s));
+    MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small, tot, 4, cudaMemcpyDeviceToHost, s));
+    MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small + 1, c->small.p, 8, cudaMemcpyDeviceToHost, s));
+    MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small + 2, c->dev_flags.p, 4, cudaMemcpyDeviceToHost, s));
+    MJ_CUDA_TRY(cudaStreamSynchronize(s));
+    const uint32_t no = *(uint32_t*)c->h_small;
+    c->stats.band_cells = c->h_small[1];
+    c->stats.device_flags |= *(uint32_t*)(c->h_small + 2);
+    MJ_TRY(c->out_i.reserve((size_t)no * 4 + 16, s));
+    MJ_TRY(c->out_j.reserve((size_t)no * 4 + 16, s));
+    MJ_TRY(c->out_ed.reserve((size_t)no * 4 + 16, s));
+    MJ_TRY(launch_compact_output(c->cand_i.as<uint32_t>(), c->cand_j.as<uint32_t>(), c->ed.as<uint32_t>(),
+                                 c->eflags.as<uint32_t>(), c->eoffs.as<uint32_t>(), m, c->out_i.as<uint32_t>(),
+                                 c->out_j.as<uint32_t>(), c->out_ed.as<uint32_t>(), s));
+    c->n_out = no;
+  }
+  MJ_CUDA_TRY(cudaEventRecord(c->ev[4], s));
+  MJ_CUDA_TRY(cudaEventSynchronize(c->ev[4]));
+  c->stats.n_output = c->n_out;
+  c->stats.ms_derive = elapsed(c->ev[0], c->ev[1]);
+  c->stats.ms_partition = elapsed(c->ev[1], c->ev[2]);
+  c->stats.ms_join_filter = elapsed(c->ev[2], c->ev[3]);
+  c->stats.ms_verify = elapsed(c->ev[3], c->ev[4]);
+  c->stats.ms_total = elapsed(c->ev[0], c->ev[4]);
+  if (c->stats.device_flags) return MJ_ERR_DEVICE;
+  c->have_out = true;
+  *count = c->n_out;
+  return MJ_OK;
+}
+
+int mj_result_copy(mj_ctx* c, uint32_t* d_i, uint32_t* d_j, uint32_t* d_ed, void* stream) {
+  if (!c) return MJ_ERR_ARG;
+  if (!c->have_out) return MJ_ERR_STATE;
+  DeviceGuard g(c->device);
+  cudaStream_t s = S(stream);
+  const size_t n = c->n_out;
+  if (!n) return MJ_OK;
+  if (d_i) MJ_CUDA_TRY(cudaMemcpyAsync(d_i, c->out_i.p, n * 4, cudaMemcpyDeviceToDevice, s));
+  if (d_j) MJ_CUDA_TRY(cudaMemcpyAsync(d_j, c->out_j.p, n * 4, cudaMemcpyDeviceToDevice, s));
+  if (d_ed) MJ_CUDA_TRY(cudaMemcpyAsync(d_ed, c->out_ed.p, n * 4, cudaMemcpyDeviceToDevice, s));
+  return MJ_OK;
+}
+
+int mj_join_host(mj_ctx* c, const uint8_t* h_bytes, const int64_t* h_offsets, uint32_t n, const mj_params* p,
+                 void* stream, uint64_t* count) {
+  if (!c || !h_offsets || !p || !count) return MJ_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = S(stream);
+  const uint64_t nbytes = (uint64_t)h_offsets[n];
+  if (nbytes && !h_bytes) return MJ_ERR_ARG;
+  MJ_TRY(c->in_bytes.reserve(nbytes + 16, s));
+  MJ_TRY(c->in_offsets.reserve(((size_t)n + 1) * 8, s));
+  if (nbytes) MJ_CUDA_TRY(cudaMemcpyAsync(c->in_bytes.p, h_bytes, nbytes, cudaMemcpyHostToDevice, s));
+  MJ_CUDA_TRY(cudaMemcpyAsync(c->in_offsets.p, h_offsets, ((size_t)n + 1) * 8, cudaMemcpyHostToDevice, s));
+  return mj_join(c, c->in_bytes.as<uint8_t>(), c->in_offsets.as<int64_t>(), n, p, stream, count);
+}
+
+int mj_result_copy_host(mj_ctx* c, uint32_t* h_i, uint32_t* h_j, uint32_t* h_ed, void* stream) {
+  if (!c) return MJ_ERR_ARG;
+  if (!c->have_out) return MJ_ERR_STATE;
+  DeviceGuard g(c->device);
+  cudaStream_t s = S(stream);
+  const size_t n = c->n_out;
+  if (n) {
+    if (h_i) MJ_CUDA_TRY(cudaMemcpyAsync(h_i, c->out_i.p, n * 4, cudaMemcpyDeviceToHost, s));
+    if (h_j) MJ_CUDA_TRY(cudaMemcpyAsync(h_j, c->out_j.p, n * 4, cudaMemcpyDeviceToHost, s));
+    if (h_ed) MJ_CUDA_TRY(cudaMemcpyAsync(h_ed, c->out_ed.p, n * 4, cudaMemcpyDeviceToHost, s));
+  }
+  MJ_CUDA_TRY(cudaStreamSynchronize(s));
+  return MJ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,279 @@
+// Steps a1 and a5-a7: parameter statistics, grouping of equal partitions,
+// pair emission under the length and position filters of Alg. 3 (lines 7-8),
+// and deduplication of the candidate pairs (Alg. 3 line 20).
+//
+// The paper's sequential hash join visits strings in length order and evicts
+// bucket entries whose length differs by more than K.  Its result is the set
+// of pairs (i != j) holding byte-identical partitions that pass both filters.
+// Here that set is produced by sorting the partition records by a group key
+// (a hash of (len, substring key) in the high bits, the string length in the
+// low bits), so equal partitions are adjacent and ordered by string length
+// within the run; every record then walks forward through its run while the
+// length difference stays <= K, testing the exact (len, key) equality, i != j,
+// and the position filter.  Count -> scan -> fill.
+#include "mj_internal.cuh"
+
+namespace mj {
+namespace {
+
+__global__ void byte_hist_kernel(const uint8_t* __restrict__ bytes, uint64_t nbytes,
+                                 unsigned long long* __restrict__ hist) {
+  __shared__ uint32_t s[256];
+  s[threadIdx.x] = 0;
+  __syncthreads();
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * 16;
+  for (uint64_t base = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 16; base < nbytes; base += stride) {
+    if (base + 16 <= nbytes && (((uintptr_t)(bytes + base)) & 15) == 0) {
+      uint4 v = __ldg(reinterpret_cast<const uint4*>(bytes + base));
+      uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) atomicAdd(&s[(w[k] >> (8 * b)) & 255u], 1u);
+      }
+    } else {
+      for (uint64_t g = base; g < base + 16 && g < nbytes; ++g) atomicAdd(&s[__ldg(bytes + g)], 1u);
+    }
+  }
+  __syncthreads();
+  if (s[threadIdx.x]) atomicAdd(&hist[threadIdx.x], (unsigned long long)s[threadIdx.x]);
+}
+
+__global__ void max_len_kernel(const int64_t* __restrict__ off, uint32_t n, unsigned long long* __restrict__ out) {
+  unsigned long long m = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    int64_t L = off[i + 1] - off[i];
+    if ((unsigned long long)L > m) m = (unsigned long long)L;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long y = __shfl_down_sync(0xffffffffu, m, o);
+    m = y > m ? y : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t k) {  // MurmurHash3 fmix64
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+// Group key: 32 hash bits of (len, key) above slen_bits bits of string length.
+__global__ void group_keys_kernel(const uint32_t* __restrict__ rec_len, const uint32_t* __restrict__ rec_slen,
+                                  const uint64_t* __restrict__ rec_h61, uint32_t n, int slen_bits,
+                                  uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t g = mix64(rec_h61[t] ^ ((uint64_t)rec_len[t] * 0x9e3779b97f4a7c15ull));
+    keys[t] = ((g >> 32) << slen_bits) | (uint64_t)rec_slen[t];
+    idx[t] = (uint32_t)t;
+  }
+}
+
+__global__ void gather_kernel(const uint32_t* __restrict__ idx, uint32_t n, const uint32_t* __restrict__ sid,
+                              const uint32_t* __restrict__ pos, const uint32_t* __restrict__ slen,
+                              const uint32_t* __restrict__ len, const uint64_t* __restrict__ h61, SortedRecs o) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t s = idx[t];
+    o.sid[t] = sid[s];
+    o.pos[t] = pos[s];
+    o.slen[t] = slen[s];
+    o.len[t] = len[s];
+    o.h61[t] = h61[s];
+  }
+}
+
+__device__ __forceinline__ int64_t iabs64(int64_t x) { return x < 0 ? -x : x; }
+
+// Walks the run of record t; EMIT=false counts, EMIT=true writes pairs.
+template <bool EMIT>
+__global__ void pairs_kernel(const uint64_t* __restrict__ keys, SortedRecs r, uint32_t n, int slen_bits, uint32_t K,
+                             uint32_t* __restrict__ count, const uint64_t* __restrict__ offs,
+                             uint64_t* __restrict__ pairs) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t run = keys[t] >> slen_bits;
+    const uint32_t sid = r.sid[t], len = r.len[t];
+    const int64_t pos = r.pos[t], slen = r.slen[t];
+    const uint64_t h = r.h61[t];
+    uint32_t c = 0;
+    uint64_t out = EMIT ? offs[t] : 0;
+    for (uint64_t u = t + 1; u < n; ++u) {
+      if ((keys[u] >> slen_bits) != run) break;
+      const int64_t slen_u = r.slen[u];
+      if (slen_u - slen > (int64_t)K) break;               // length filter (run sorted by length)
+      if (r.len[u] != len || r.h61[u] != h) continue;        // same partition substring
+      const uint32_t sid_u = r.sid[u];
+      if (sid_u == sid) continue;                            // i != j
+      const int64_t pos_u = r.pos[u];
+      if (iabs64(pos - pos_u) + iabs64((slen - pos) - (slen_u - pos_u)) > (int64_t)K) continue;  // position filter
+      if (EMIT) {
+        uint32_t a = sid < sid_u ? sid : sid_u, b = sid < sid_u ? sid_u : sid;
+        pairs[out++] = ((uint64_t)a << 32) | b;
+      } else {
+        ++c;
+      }
+    }
+    if (!EMIT) count[t] = c;
+  }
+}
+
+// flags bit 0 check: every record's bytes equal the first record of its
+// (len, key) class inside the run.
+__global__ void key_check_kernel(const uint64_t* __restrict__ keys, SortedRecs r, const uint8_t* __restrict__ bytes,
+                                 const int64_t* __restrict__ offsets, uint32_t n, int slen_bits,
+                                 unsigned long long* __restrict__ mismatches) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t run = keys[t] >> slen_bits;
+    // first record of the run with the same (len, key)
+    uint64_t f = t;
+    for (uint64_t u = t; u-- > 0;) {
+      if ((keys[u] >> slen_bits) != run) break;
+      if (r.len[u] == r.len[t] && r.h61[u] == r.h61[t]) f = u;
+    }
+    if (f == t) continue;
+    const uint8_t* a = bytes + offsets[r.sid[t]] + r.pos[t];
+    const uint8_t* b = bytes + offsets[r.sid[f]] + r.pos[f];
+    for (uint32_t x = 0; x < r.len[t]; ++x) {
+      if (a[x] != b[x]) {
+        atomicAdd(mismatches, 1ull);
+        break;
+      }
+    }
+  }
+}
+
+__global__ void unique_flags_kernel(const uint64_t* __restrict__ s, uint64_t n, uint32_t* __restrict__ flags) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x)
+    flags[t] = (t == 0 || s[t] != s[t - 1]) ? 1u : 0u;
+}
+
+__global__ void compact_pairs_kernel(const uint64_t* __restrict__ s, const uint32_t* __restrict__ flags,
+                                     const uint32_t* __restrict__ offs, uint64_t n, uint32_t* __restrict__ oi,
+                                     uint32_t* __restrict__ oj) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
+    if (flags[t]) {
+      uint32_t o = offs[t];
+      oi[o] = (uint32_t)(s[t] >> 32);
+      oj[o] = (uint32_t)s[t];
+    }
+  }
+}
+
+__global__ void ed_flags_kernel(const uint32_t* __restrict__ ed, uint64_t m, uint32_t K, uint32_t* __restrict__ flags) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (uint64_t)gridDim.x * blockDim.x)
+    flags[t] = ed[t] <= K ? 1u : 0u;
+}
+
+__global__ void compact_out_kernel(const uint32_t* __restrict__ ci, const uint32_t* __restrict__ cj,
+                                   const uint32_t* __restrict__ ed, const uint32_t* __restrict__ flags,
+                                   const uint32_t* __restrict__ offs, uint64_t m, uint32_t* __restrict__ oi,
+                                   uint32_t* __restrict__ oj, uint32_t* __restrict__ oed) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (uint64_t)gridDim.x * blockDim.x) {
+    if (flags[t]) {
+      uint32_t o = offs[t];
+      oi[o] = ci[t];
+      oj[o] = cj[t];
+      oed[o] = ed[t];
+    }
+  }
+}
+
+unsigned grid_for(uint64_t n, int threads = 256) {
+  uint64_t g = (n + threads - 1) / threads;
+  uint64_t cap = (uint64_t)kNumSMsHint * 32;
+  return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+}  // namespace
+
+int launch_byte_histogram(const uint8_t* bytes, uint64_t nbytes, unsigned long long* hist, cudaStream_t s) {
+  MJ_CUDA_TRY(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned long long), s));
+  if (!nbytes) return MJ_OK;
+  byte_hist_kernel<<<grid_for((nbytes + 15) / 16), 256, 0, s>>>(bytes, nbytes, hist);
+  MJ_CUDA_TRY(cudaGetLastError());
+  return MJ_OK;
+}
+
+int launch_max_length(const int64_t* offsets, uint32_t n, unsigned long long* out, cudaStream_t s) {
+  MJ_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(unsigned long long), s));
+  if (!n) return MJ_OK;
+  max_len_kernel<<<grid_for(n), 256, 0, s>>>(offsets, n, out);
+  MJ_CUDA_TRY(cudaGetLastError());
+  return MJ_OK;
+}
+
+int launch_make_group_keys(const uint32_t* rec_len, const uint32_t* rec_slen, const uint64_t* rec_h61, uint32_t n,
+                           int slen_bits, uint64_t* keys, uint32_t* idx, cudaStream_t s) {
+  if (!n) return MJ_OK;
+  group_keys_kernel<<<grid_for(n), 256, 0, s>>>(rec_len, rec_slen, rec_h61, n, slen_bits, keys, idx);
+  MJ_CUDA_TRY(cudaGetLastError());
+  return MJ_OK;
+}
+
+int launch_gather_records(const uint32_t* idx, uint32_t n, const uint32_t* sid, const uint32_t* pos,
+                          const uint32_t* slen, const uint32_t* len, const uint64_t* h61, SortedRecs o,
+                          cudaStream_t s) {
+  if (!n) return MJ_OK;
+  gather_kernel<<<grid_for(n), 256, 0, s>>>(idx, n, sid, pos, slen, len, h61, o);
+  MJ_CUDA_TRY(cudaGetLastError());
+  return MJ_OK;
+}
+
+int launch_count_pairs(const uint64_t* keys, SortedRecs r, uint32_t n, int slen_bits, uint32_t K, uint32_t* count,
+                       cudaStream_t s) {
+  if (!n) return MJ_OK;
+  pairs_kernel<false><<<grid_for(n), 256, 0, s>>>(keys, r, n, slen_bits, K, count, nullptr, nullptr);
+  MJ_CUDA_TRY(cudaGetLastError());
+  return MJ_OK;
+}
+
+int launch_fill_pairs(const uint64_t* keys, SortedRecs r, uint32_t n, int slen_bits, uint32_t K, const uint64_t* offs,
+                      uint64_t* pairs, cudaStream_t s) {
+  if (!n) return MJ_OK;
+  pairs_kernel<true><<<grid_for(n), 256, 0, s>>>(keys, r, n, slen_bits, K, nullptr, offs, pairs);
+  MJ_CUDA_TRY(cudaGetLastError());
+  return MJ_OK;
+}
+
+int launch_key_check(const uint64_t* keys, SortedRecs r, const uint8_t* bytes, const int64_t* offsets, uint32_t n,
+                     int slen_bits, unsigned long long* mismatches, cudaStream_t s) {
+  if (!n) return MJ_OK;
+  key_check_kernel<<<grid_for(n), 256, 0, s>>>(keys, r, bytes, offsets, n, slen_bits, mismatches);
+  MJ_CUDA_TRY(cudaGetLastError());
+  return MJ_OK;
+}
+
+int launch_unique_flags(const uint64_t* sorted, uint64_t n, uint32_t* flags, cudaStream_t s) {
+  if (!n) return MJ_OK;
+  unique_flags_kernel<<<grid_for(n), 256, 0, s>>>(sorted, n, flags);
+  MJ_CUDA_TRY(cudaGetLastError());
+  return MJ_OK;
+}
+
+int launch_compact_pairs(const uint64_t* sorted, const uint32_t* flags, const uint32_t* offs, uint64_t n,
+                         uint32_t* out_i, uint32_t* out_j, cudaStream_t s) {
+  if (!n) return MJ_OK;
+  compact_pairs_kernel<<<grid_for(n), 256, 0, s>>>(sorted, flags, offs, n, out_i, out_j);
+  MJ_CUDA_TRY(cudaGetLastError());
+  return MJ_OK;
+}
+
+int launch_ed_flags(const uint32_t* ed, uint64_t m, uint32_t K, uint32_t* flags, cudaStream_t s) {
+  if (!m) return MJ_OK;
+  ed_flags_kernel<<<grid_for(m), 256, 0, s>>>(ed, m, K, flags);
+  MJ_CUDA_TRY(cudaGetLastError());
+  return MJ_OK;
+}
+
+int launch_compact_output(const uint32_t* ci, const uint32_t* cj, const uint32_t* ed, const uint32_t* flags,
+                          const uint32_t* offs, uint64_t m, uint32_t* oi, uint32_t* oj, uint32_t* oed,
+                          cudaStream_t s) {
+  if (!m) return MJ_OK;
+  compact_out_kernel<<<grid_for(m), 256, 0, s>>>(ci, cj, ed, flags, offs, m, oi, oj, oed);
+  MJ_CUDA_TRY(cudaGetLastError());
+  return MJ_OK;
+}
+
+}  // namespace mj

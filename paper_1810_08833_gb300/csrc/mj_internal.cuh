@@ -1,0 +1,168 @@
+// Internal declarations of the MinJoin CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+
+#include "../../include/minjoin.h"
+
+#define MJ_CUDA_TRY(expr)                                   \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) {                                \
+      mj::set_last_cuda_error(_e, #expr, __FILE__, __LINE__); \
+      return MJ_ERR_CUDA;                                   \
+    }                                                       \
+  } while (0)
+
+#define MJ_TRY(expr)          \
+  do {                        \
+    int _s = (expr);          \
+    if (_s != MJ_OK) return _s; \
+  } while (0)
+
+namespace mj {
+
+constexpr int kNumSMsHint = 152;
+
+// device-side error flags (mj_stats.device_flags)
+enum : uint32_t {
+  FLAG_BOUNDS = 1u << 0,       // an index left its buffer (access skipped)
+  FLAG_TIMEOUT = 1u << 1,      // a bounded wait gave up
+  FLAG_CAPACITY = 1u << 2,     // an output buffer was too small (write skipped)
+};
+
+void set_last_cuda_error(cudaError_t e, const char* expr, const char* file, int line);
+
+// ---------------------------------------------------------------- workspace
+// A growable device buffer owned by a context; reallocated (contents
+// dropped) only when a larger size is requested.
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int reserve(size_t need, cudaStream_t s);
+  template <class T>
+  T* as() const { return static_cast<T*>(p); }
+  void release();
+};
+
+// Derived parameters of one input (host copy).
+struct Derived {
+  uint32_t sigma = 0, bits = 1, q = 1, T = 1, K = 0;
+  int32_t r_min = 1, r_max = 0;
+  uint64_t N = 0, seed = 0;
+  uint8_t rank[256] = {0};
+};
+
+// ---------------------------------------------------------------- kernels (launchers)
+// All launchers are stream-ordered and return MJ_OK or MJ_ERR_CUDA.
+
+// a1: 256-bin byte histogram (u64 counts) and the longest string length.
+int launch_byte_histogram(const uint8_t* bytes, uint64_t nbytes, unsigned long long* hist,
+                          cudaStream_t s);
+int launch_max_length(const int64_t* offsets, uint32_t n, unsigned long long* out, cudaStream_t s);
+
+// a2-a3: anchor bitmap (1 bit per byte position) and per-tile anchor counts.
+struct PartitionArgs {
+  const uint8_t* bytes;
+  const int64_t* offsets;
+  uint32_t n;
+  uint64_t nbytes;
+  uint32_t q, bits, T;
+  int32_t r_min, r_max;
+  uint32_t seed32;
+  uint64_t seed64;
+  const uint64_t* table;  // nullable explicit Pi
+  uint8_t rank[256];
+};
+constexpr int kPartTile = 4096;  // byte positions per CTA tile
+uint64_t partition_num_tiles(uint64_t nbytes);
+int launch_anchor_flags(const PartitionArgs& a, uint32_t* bitmap, uint32_t* tile_count,
+                        uint32_t* dev_flags, cudaStream_t s);
+// a4: anchors in position order (global byte position and string id).
+int launch_anchor_emit(const PartitionArgs& a, const uint32_t* bitmap, const uint32_t* tile_offset,
+                       uint32_t* anchor_pos, uint32_t* anchor_sid, cudaStream_t s);
+// a4: partition records from consecutive anchors; key = (len, H61(substring)).
+int launch_partition_records(const uint8_t* bytes, const int64_t* offsets, const uint32_t* anchor_pos,
+                             const uint32_t* anchor_sid, uint32_t n_anchor, uint64_t key_base,
+                             uint32_t* rec_sid, uint32_t* rec_pos, uint32_t* rec_len,
+                             uint32_t* rec_slen, uint64_t* rec_h61, cudaStream_t s);
+
+// scans (exclusive, in place allowed); temp from scan_temp_bytes
+size_t scan_temp_bytes(uint64_t n);
+int launch_exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, void* temp,
+                              uint32_t* total_out, cudaStream_t s);
+int launch_exclusive_scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, void* temp,
+                              uint64_t* total_out, cudaStream_t s);
+int launch_exclusive_scan_u32_to_u64(const uint32_t* in, uint64_t* out, uint64_t n, void* temp,
+                                     uint64_t* total_out, cudaStream_t s);
+
+// LSD radix sort of 64-bit keys (optionally with 32-bit values) on bits
+// [bit_lo, bit_hi).  Ping-pongs between (keys, keys_alt); *result_in_alt
+// tells which buffer holds the sorted data.
+size_t radix_temp_bytes(uint64_t n);
+int radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
+                   uint64_t n, int bit_lo, int bit_hi, void* temp, bool* result_in_alt,
+                   cudaStream_t s);
+
+// a5-a6: grouping keys and pair emission.
+int launch_make_group_keys(const uint32_t* rec_len, const uint32_t* rec_slen, const uint64_t* rec_h61,
+                           uint32_t n_rec, int slen_bits, uint64_t* keys, uint32_t* idx,
+                           cudaStream_t s);
+struct SortedRecs {
+  uint32_t* sid;
+  uint32_t* pos;
+  uint32_t* slen;
+  uint32_t* len;
+  uint64_t* h61;
+};
+int launch_gather_records(const uint32_t* idx, uint32_t n_rec, const uint32_t* rec_sid,
+                          const uint32_t* rec_pos, const uint32_t* rec_slen, const uint32_t* rec_len,
+                          const uint64_t* rec_h61, SortedRecs out, cudaStream_t s);
+int launch_count_pairs(const uint64_t* keys, SortedRecs r, uint32_t n_rec, int slen_bits, uint32_t K,
+                       uint32_t* count, cudaStream_t s);
+int launch_fill_pairs(const uint64_t* keys, SortedRecs r, uint32_t n_rec, int slen_bits, uint32_t K,
+                      const uint64_t* offs, uint64_t* pairs, cudaStream_t s);
+int launch_key_check(const uint64_t* keys, SortedRecs r, const uint8_t* bytes, const int64_t* offsets,
+                     uint32_t n_rec, int slen_bits, unsigned long long* mismatches, cudaStream_t s);
+// a7: unique of sorted u64 pairs -> flags; then compaction.
+int launch_unique_flags(const uint64_t* sorted, uint64_t n, uint32_t* flags, cudaStream_t s);
+int launch_compact_pairs(const uint64_t* sorted, const uint32_t* flags, const uint32_t* offs, uint64_t n,
+                         uint32_t* out_i, uint32_t* out_j, cudaStream_t s);
+
+// a8: banded verification (diagonal bit-vector, one thread per pair).
+struct RankTable {
+  uint8_t r[256];
+};
+struct VerifyArgs {
+  const uint32_t* planes;    // bit-planes of rank codes: plane p at planes + p * plane_words
+  uint32_t bits;
+  const uint8_t* bytes;
+  const int64_t* offsets;
+  uint32_t n_strings;        // pair ids >= n_strings are rejected (flagged, ed = k + 1)
+  const uint32_t* pi;
+  const uint32_t* pj;
+  const uint32_t* pk;        // nullable per-pair band
+  uint32_t K;
+  uint64_t m;
+  uint32_t* ed;
+  unsigned long long* cells; // nullable: K-band cells accumulated
+  uint32_t* dev_flags;
+};
+int verify_words_for(uint32_t kmax);
+inline uint32_t plane_guard_words(uint32_t kmax) { return kmax / 64 + (uint32_t)verify_words_for(kmax) + 4; }
+int launch_build_planes(const uint8_t* bytes, uint64_t nbytes, const RankTable& rt, uint32_t bits,
+                        uint32_t* planes, uint64_t plane_words, uint32_t guard_words, cudaStream_t s);
+int launch_verify(const VerifyArgs& a, const RankTable& rt, uint64_t plane_words, uint32_t guard_words,
+                  uint32_t kmax, cudaStream_t s);
+
+// output compaction (ED <= K)
+int launch_ed_flags(const uint32_t* ed, uint64_t m, uint32_t K, uint32_t* flags, cudaStream_t s);
+int launch_compact_output(const uint32_t* ci, const uint32_t* cj, const uint32_t* ed, const uint32_t* flags,
+                          const uint32_t* offs, uint64_t m, uint32_t* oi, uint32_t* oj, uint32_t* oed,
+                          cudaStream_t s);
+
+}  // namespace mj
