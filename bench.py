@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 MinJoin edit-similarity join.
+
+One step = one whole join (Alg. 3 of the MinJoin paper: parameters, partition,
+hash join with both filters, dedup, banded verification, output compaction)
+over a synthetic string set resident in HBM.  The metric is the join's
+throughput in K-band DP cells per second of join wall time:
+    value = sum over candidate pairs (a, b) of #{(i, j): 1 <= i <= |a|,
+            1 <= j <= |b|, |i - j| <= K}, divided by the join time,
+with the join time itself reported as ms_per_step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config C] [--impl native|reference]
+
+Multi-GPU: N independent replicas (one process per GPU under torchrun), each
+joining its own instance of the workload (different seed): weak scaling, no
+collective on the data path; the barrier and the max over ranks of the step
+time are the only communication.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "join wall time & verified DP cells/s; learned-band vs plain K-band, identical output"
+UNIT = "cells/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+SM_COUNT = 152
+INT_LANES_PER_SM = 64        # 32-bit integer ALU lanes per SM and clock (4 partitions x 16)
+
+
+def band_cells(m: np.ndarray, n: np.ndarray, K: int) -> int:
+    """K-band cells of pairs with lengths m >= n: sum over j = 1..n of
+    min(m, j+K) - max(1, j-K) + 1, in closed form."""
+    m = m.astype(np.int64)
+    n = n.astype(np.int64)
+    a = np.clip(m - K, 0, n)
+    smin = a * (a + 1) // 2 + a * K + (n - a) * m
+    b = np.minimum(K, n)
+    smax = b + np.where(n > K, (n - K) * (n - K + 1) // 2, 0)
+    return int(np.where(n > 0, smin - smax + n, 0).sum())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def workload_name(cfg: int, s) -> str:
+    import synth
+    return f"config {cfg}: {synth.CONFIGS[cfg][0]}; K={s.K}, T={s.T}"
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_sample(cfg: int, roots: int, threads: int | None = None) -> dict:
+    """The oracle (as it stands) on a bounded sample of the workload: the
+    same generator with fewer root families."""
+    import oracle
+    import synth
+    s = synth.make_config(cfg, n_roots=roots)
+    t0 = time.perf_counter()
+    res = oracle.minjoin(s.bytes, s.offsets, K=s.K, T=s.T, threads=threads)
+    dt = time.perf_counter() - t0
+    L = s.lengths()
+    a, b = res.candidates[:, 0], res.candidates[:, 1]
+    cells = band_cells(np.maximum(L[a], L[b]), np.minimum(L[a], L[b]), s.K)
+    return {"seconds": dt, "cells": cells, "value": cells / dt if dt > 0 else 0.0, "n_strings": s.n,
+            "bytes": int(s.bytes.shape[0]), "candidates": int(res.candidates.shape[0]),
+            "output": int(res.pairs.shape[0])}
+
+
+def run_reference(args):
+    """The CPU oracle timed as the reference arm (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    oracle.build()
+    threads = os.cpu_count() or 1
+    roots = args.ref_roots
+    for _ in range(args.warmup):
+        oracle_sample(args.config, roots, threads)
+    runs = [oracle_sample(args.config, roots, threads) for _ in range(args.steps)]
+    secs = sum(r["seconds"] for r in runs)
+    cells = sum(r["cells"] for r in runs)
+    value = cells / secs
+    s_full = synth.CONFIGS[args.config]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": f"config {args.config}: {s_full[0]}; K={s_full[1]}, T={s_full[2]}",
+                   "sample": f"{roots} root families x 10 copies per step ({runs[0]['n_strings']} strings, "
+                             f"{runs[0]['bytes']} bytes)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{roots} of {s_full[3]} root families per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        from paper_1810_08833_gb300 import build
+        build.build()
+    if world > 1:
+        dist.barrier()
+    import paper_1810_08833_gb300 as mj
+    import synth
+
+    cfg = args.config
+    seed = cfg if rank == 0 else cfg + 7919 * rank
+    s = synth.make_config(cfg, seed=seed)
+    data = torch.from_numpy(s.bytes).to(dev)
+    off = torch.from_numpy(s.offsets).to(dev)
+    ctx = mj.Context(local)
+    p = mj.params(s.K, T=s.T)
+    stream = torch.cuda.Stream(dev)
+    L = s.lengths()
+
+    def sync_all():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ctx.join(data, off, p, stream=stream)
+        sync_all()
+        clocks = Clocks(local)
+        clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        stats = []
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.join(data, off, p, stream=stream)
+            stats.append(ctx.stats())
+        e1.record(stream)
+        sync_all()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1) / args.steps
+
+        # end to end through host buffers: H2D of the inputs and D2H of the
+        # output pairs inside every timed step
+        h_data = torch.from_numpy(s.bytes).pin_memory()
+        h_off = torch.from_numpy(s.offsets).pin_memory()
+        n_out = stats[-1]["n_output"]
+        h_out = [torch.empty(max(1, n_out) + 1024, dtype=torch.int32).pin_memory() for _ in range(3)]
+        outs = tuple(o.numpy().view(np.uint32) for o in h_out)
+        for _ in range(max(1, args.warmup // 2)):
+            ctx.join_host(h_data.numpy(), h_off.numpy(), p, stream=stream, out=outs)
+        sync_all()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            ctx.join_host(h_data.numpy(), h_off.numpy(), p, stream=stream, out=outs)
+        f1.record(stream)
+        sync_all()
+        ms_e2e = f0.elapsed_time(f1) / args.steps
+        e2e_stats = ctx.stats()
+
+    last = stats[-1]
+    cells = int(last["band_cells"])
+    sec_ms = {k: statistics.median([st["ms_section"][k] for st in stats]) for k in mj.SECTIONS}
+    launches = int(sum(st["n_launches"] for st in stats))
+
+    if world > 1:
+        t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0]), float(t[1])
+        c = torch.tensor([cells], dtype=torch.float64, device=dev)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        cells_all = float(c[0])
+    else:
+        cells_all = float(cells)
+
+    if rank == 0:
+        peaks = measured_peaks()
+        hbm = peaks.get("hbm_gbs")
+        hbm_src = "measured" if hbm else "fallback"
+        hbm = hbm or FALLBACK_HBM_GBS
+        sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
+        nbytes = int(s.bytes.shape[0])
+        # dominant kernel: the section with the largest share of the step
+        dom = max(sec_ms, key=lambda k: sec_ms[k])
+        roof = roofline(dom, sec_ms[dom], last, nbytes, hbm, hbm_src, sm_mhz, args)
+        line = {
+            "metric": METRIC, "value": cells_all / (ms / 1000.0), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": workload_name(cfg, s), "n_strings": s.n, "bytes": nbytes, "K": s.K, "T": s.T,
+                       "verify_mode": "plain", "parallelism": f"replicas x{world}",
+                       "l2": f"inputs ({nbytes / 1e6:.0f} MB) larger than L2 (129 MB); no flush"},
+            "join_ms": ms,
+            "cells_per_step": cells_all,
+            "candidates": int(last["n_candidates"]), "raw_pairs": int(last["n_raw_pairs"]),
+            "partitions": int(last["n_partitions"]), "output_pairs": int(last["n_output"]),
+            "sections_ms": {k: round(v, 4) for k, v in sec_ms.items()},
+            "roofline": roof,
+            "e2e": {"value": cells_all / (ms_e2e / 1000.0), "unit": UNIT, "ms_per_step": ms_e2e,
+                    "h2d_bytes_per_step": nbytes + 8 * (s.n + 1),
+                    "d2h_bytes_per_step": 12 * int(e2e_stats["n_output"])},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline:
+            ob = oracle_sample(cfg, args.cpu_roots)
+            line["cpu_baseline"] = {"value": ob["value"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                    "sample": f"config {cfg} generator with {args.cpu_roots} root families "
+                                              f"({ob['n_strings']} strings, {ob['bytes']} bytes, "
+                                              f"{ob['candidates']} candidates), {ob['seconds']:.1f} s"}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def roofline(section: str, ms: float, st: dict, nbytes: int, hbm: float, hbm_src: str, sm_mhz: float, args) -> dict:
+    """Roofline entry of the dominant section, from its algorithmic work."""
+    sec = ms / 1000.0
+    if section == "anchor_test":
+        # reads every byte once, writes one anchor bit per byte
+        traffic = nbytes + nbytes / 8
+        ach = traffic / sec / 1e9
+        return {"kernel": section, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "peak_source": hbm_src}
+    if section in ("record_sort", "pair_dedup"):
+        n = st["n_partitions"] if section == "record_sort" else st["n_raw_pairs"]
+        per = 24 if section == "record_sort" else 16   # one read and one write of key (+ value)
+        traffic = n * per
+        ach = traffic / sec / 1e9
+        return {"kernel": section, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "peak_source": hbm_src}
+    # verification and pair emission are integer-ALU work: K-band cells at
+    # one bit per cell, 17 32-bit ops per 32 cells (one word-column)
+    peak = SM_COUNT * INT_LANES_PER_SM * sm_mhz * 1e6 / 1e9   # Gop/s
+    ops = st["band_cells"] / 32.0 * 17.0
+    ach = ops / sec / 1e9
+    return {"kernel": section, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gop/s", "frac": ach / peak,
+            "traffic": None, "peak_source": f"{SM_COUNT} SMs x {INT_LANES_PER_SM} int32 lanes x {sm_mhz:.0f} MHz"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-roots", type=int, default=400)
+    ap.add_argument("--ref-roots", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "native":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -94,6 +94,13 @@ typedef struct {
   uint64_t fallback_pairs;     /* learned mode: pairs re-run with band K */
   uint32_t device_flags;       /* bit set by a failed device-side check */
   float ms_derive, ms_partition, ms_join_filter, ms_verify, ms_total;
+  uint64_t n_launches;         /* kernels the library launched during the call */
+  /* device time (CUDA events on the call's stream) of the sections of the
+   * last mj_join, in this order: 0 anchor test (Alg. 2), 1 anchor list and
+   * partition records (Alg. 1), 2 record grouping sort, 3 pair emission
+   * (filters of Alg. 3), 4 pair dedup, 5 equality bit-planes, 6 verification
+   * kernel(s), 7 output compaction */
+  float ms_section[8];
 } mj_stats;
 
 void mj_params_default(mj_params* p, uint32_t K);

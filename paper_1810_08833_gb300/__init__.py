@@ -52,7 +52,11 @@ class Stats(ctypes.Structure):
                 ("band_cells", ctypes.c_uint64), ("first_pass_settled", ctypes.c_uint64),
                 ("fallback_pairs", ctypes.c_uint64), ("device_flags", ctypes.c_uint32),
                 ("ms_derive", ctypes.c_float), ("ms_partition", ctypes.c_float),
-                ("ms_join_filter", ctypes.c_float), ("ms_verify", ctypes.c_float), ("ms_total", ctypes.c_float)]
+                ("ms_join_filter", ctypes.c_float), ("ms_verify", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("n_launches", ctypes.c_uint64), ("ms_section", ctypes.c_float * 8)]
+
+SECTIONS = ("anchor_test", "partition_records", "record_sort", "pair_emission", "pair_dedup", "eq_planes",
+            "verify_kernel", "output_compaction")
 
 
 VP = ctypes.c_void_p
@@ -167,7 +171,9 @@ class Context:
     def stats(self) -> dict:
         s = Stats()
         _check(self._lib.mj_get_stats(self._h, ctypes.byref(s)), "mj_get_stats")
-        return {name: getattr(s, name) for name, _ in Stats._fields_}
+        out = {name: getattr(s, name) for name, _ in Stats._fields_ if name != "ms_section"}
+        out["ms_section"] = dict(zip(SECTIONS, list(s.ms_section)))
+        return out
 
     def derive(self, data, offsets, p: Params, stream=None) -> dict:
         n = _check_inputs(data, offsets)

@@ -12,6 +12,10 @@
 namespace mj {
 
 static thread_local char g_cuda_err[512];
+static unsigned long long g_launches = 0;  // host-side count of kernel launches
+
+void note_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
+uint64_t launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 void set_last_cuda_error(cudaError_t e, const char* expr, const char* file, int line) {
   snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s (%s:%d)", cudaGetErrorString(e), expr, file, line);
@@ -108,6 +112,12 @@ struct mj_ctx {
   uint64_t n_part = 0, n_cand = 0, n_out = 0;
   bool have_part = false, have_cand = false, have_out = false;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // section timers of mj_join (mj_stats.ms_section)
+  static constexpr int kSections = 8;
+  cudaEvent_t sec_ev[2 * kSections] = {};
+  bool sec_used[kSections] = {};
+  bool timing = false;
+  uint64_t launches_at_start = 0;
 };
 
 namespace {
@@ -129,6 +139,23 @@ int readback(mj_ctx* c, const void* d_src, size_t bytes, cudaStream_t s) {
   MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small, d_src, bytes, cudaMemcpyDeviceToHost, s));
   MJ_CUDA_TRY(cudaStreamSynchronize(s));
   return MJ_OK;
+}
+
+void tstart(mj_ctx* c, int i, cudaStream_t s) {
+  if (c->timing) {
+    cudaEventRecord(c->sec_ev[2 * i], s);
+    c->sec_used[i] = true;
+  }
+}
+void tstop(mj_ctx* c, int i, cudaStream_t s) {
+  if (c->timing) cudaEventRecord(c->sec_ev[2 * i + 1], s);
+}
+
+void begin_call(mj_ctx* c, bool timing) {
+  c->stats = mj_stats{};
+  c->timing = timing;
+  for (bool& u : c->sec_used) u = false;
+  c->launches_at_start = launch_count();
 }
 
 int check_inputs(const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const mj_params* p) {
@@ -219,8 +246,10 @@ int partition(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
   MJ_TRY(c->tile_count.reserve(tiles * sizeof(uint32_t), s));
   MJ_TRY(c->tile_off.reserve(tiles * sizeof(uint32_t) + 16, s));
   MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(tiles), s));
+  tstart(c, 0, s);
   MJ_TRY(launch_anchor_flags(a, c->bitmap.as<uint32_t>(), c->tile_count.as<uint32_t>(),
                              c->dev_flags.as<uint32_t>(), s));
+  tstop(c, 0, s);
   uint32_t* total = c->tile_off.as<uint32_t>() + tiles;
   MJ_TRY(launch_exclusive_scan_u32(c->tile_count.as<uint32_t>(), c->tile_off.as<uint32_t>(), tiles,
                                    c->scan_tmp.p, total, s));
@@ -232,6 +261,7 @@ int partition(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
   if (c->stats.device_flags) return MJ_ERR_DEVICE;
   MJ_TRY(c->anchor_pos.reserve((size_t)n_anchor * 4 + 16, s));
   MJ_TRY(c->anchor_sid.reserve((size_t)n_anchor * 4 + 16, s));
+  tstart(c, 1, s);
   MJ_TRY(launch_anchor_emit(a, c->bitmap.as<uint32_t>(), c->tile_off.as<uint32_t>(), c->anchor_pos.as<uint32_t>(),
                             c->anchor_sid.as<uint32_t>(), s));
   MJ_TRY(c->rec_sid.reserve((size_t)n_anchor * 4 + 16, s));
@@ -243,6 +273,7 @@ int partition(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
                                   n_anchor, key_base_for(d.seed), c->rec_sid.as<uint32_t>(),
                                   c->rec_pos.as<uint32_t>(), c->rec_len.as<uint32_t>(), c->rec_slen.as<uint32_t>(),
                                   c->rec_h61.as<uint64_t>(), s));
+  tstop(c, 1, s);
   c->n_part = n_anchor;
   c->stats.n_partitions = n_anchor;
   return MJ_OK;
@@ -263,6 +294,7 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   MJ_TRY(c->idx.reserve((size_t)nr * 4, s));
   MJ_TRY(c->idx_alt.reserve((size_t)nr * 4, s));
   MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(nr), s));
+  tstart(c, 2, s);
   MJ_TRY(launch_make_group_keys(c->rec_len.as<uint32_t>(), c->rec_slen.as<uint32_t>(), c->rec_h61.as<uint64_t>(), nr,
                                 slen_bits, c->keys.as<uint64_t>(), c->idx.as<uint32_t>(), s));
   bool alt = false;
@@ -280,6 +312,7 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   MJ_TRY(launch_gather_records(sidx, nr, c->rec_sid.as<uint32_t>(), c->rec_pos.as<uint32_t>(),
                                c->rec_slen.as<uint32_t>(), c->rec_len.as<uint32_t>(), c->rec_h61.as<uint64_t>(), r,
                                s));
+  tstop(c, 2, s);
   if (flags & 1u) {
     MJ_TRY(c->small.reserve(64, s));
     MJ_CUDA_TRY(cudaMemsetAsync(c->small.p, 0, 8, s));
@@ -290,17 +323,20 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   MJ_TRY(c->pair_count.reserve((size_t)nr * 4, s));
   MJ_TRY(c->pair_off.reserve((size_t)nr * 8 + 16, s));
   MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(nr), s));
+  tstart(c, 3, s);
   MJ_TRY(launch_count_pairs(skeys, r, nr, slen_bits, d.K, c->pair_count.as<uint32_t>(), s));
   uint64_t* total = c->pair_off.as<uint64_t>() + nr;
   MJ_TRY(launch_exclusive_scan_u32_to_u64(c->pair_count.as<uint32_t>(), c->pair_off.as<uint64_t>(), nr,
                                           c->scan_tmp.p, total, s));
   MJ_TRY(readback(c, total, 8, s));
+  tstop(c, 3, s);
   const uint64_t raw = c->h_small[0];
   c->stats.n_raw_pairs = raw;
   if (raw == 0) return MJ_OK;
   if (raw >= (1ull << 32)) return MJ_ERR_UNSUPPORTED;
   MJ_TRY(c->pairs.reserve(raw * 8, s));
   MJ_TRY(c->pairs_alt.reserve(raw * 8, s));
+  tstart(c, 4, s);
   MJ_TRY(launch_fill_pairs(skeys, r, nr, slen_bits, d.K, c->pair_off.as<uint64_t>(), c->pairs.as<uint64_t>(), s));
   MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(raw), s));
   const int nb = bits_for(n ? n - 1 : 0);
@@ -319,6 +355,7 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   MJ_TRY(c->cand_j.reserve((size_t)nc * 4 + 16, s));
   MJ_TRY(launch_compact_pairs(sp, c->uflags.as<uint32_t>(), c->uoffs.as<uint32_t>(), raw, c->cand_i.as<uint32_t>(),
                               c->cand_j.as<uint32_t>(), s));
+  tstop(c, 4, s);
   c->n_cand = nc;
   c->stats.n_candidates = nc;
   return MJ_OK;
@@ -337,7 +374,9 @@ int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const ui
   MJ_TRY(c->planes.reserve(PW * d.bits * 4, s));
   RankTable rt;
   memcpy(rt.r, d.rank, 256);
+  tstart(c, 5, s);
   MJ_TRY(launch_build_planes(d_bytes, nbytes, rt, d.bits, c->planes.as<uint32_t>(), PW, GW, s));
+  tstop(c, 5, s);
   MJ_TRY(c->dev_flags.reserve(64, s));
   MJ_CUDA_TRY(cudaMemsetAsync(c->dev_flags.p, 0, 64, s));
   MJ_TRY(c->small.reserve(64, s));
@@ -356,7 +395,9 @@ int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const ui
   a.ed = d_ed;
   a.cells = count_cells ? c->small.as<unsigned long long>() : nullptr;
   a.dev_flags = c->dev_flags.as<uint32_t>();
+  tstart(c, 6, s);
   MJ_TRY(launch_verify(a, rt, PW, GW, kmax, s));
+  tstop(c, 6, s);
   return MJ_OK;
 }
 
@@ -406,6 +447,13 @@ int mj_create(mj_ctx** ctx, int device) {
     delete c;
     return MJ_ERR_OOM;
   }
+  for (auto& e : c->sec_ev) {
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      mj_destroy(c);
+      return MJ_ERR_CUDA;
+    }
+  }
   for (auto& e : c->ev) {
     if (cudaEventCreate(&e) != cudaSuccess) {
       cudaGetLastError();
@@ -430,6 +478,8 @@ void mj_destroy(mj_ctx* c) {
   for (Buf* b : bufs) b->release();
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : c->sec_ev)
+    if (e) cudaEventDestroy(e);
   if (c->h_small) cudaFreeHost(c->h_small);
   delete c;
 }
@@ -445,7 +495,7 @@ int mj_derive(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
   if (!c || !out) return MJ_ERR_ARG;
   MJ_TRY(check_inputs(d_bytes, d_offsets, n, p));
   DeviceGuard g(c->device);
-  c->stats = mj_stats{};
+  begin_call(c, false);
   MJ_TRY(derive(c, d_bytes, d_offsets, n, p, S(stream)));
   const Derived& d = c->d;
   out->sigma = d.sigma;
@@ -465,12 +515,13 @@ int mj_partition(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, ui
   MJ_TRY(check_inputs(d_bytes, d_offsets, n, p));
   DeviceGuard g(c->device);
   cudaStream_t s = S(stream);
-  c->stats = mj_stats{};
+  begin_call(c, false);
   c->have_part = false;
   MJ_TRY(derive(c, d_bytes, d_offsets, n, p, s));
   MJ_TRY(partition(c, d_bytes, d_offsets, n, d_table, s));
   MJ_CUDA_TRY(cudaStreamSynchronize(s));
   c->have_part = true;
+  c->stats.n_launches = launch_count() - c->launches_at_start;
   *count = c->n_part;
   return MJ_OK;
 }
@@ -496,7 +547,7 @@ int mj_candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, u
   MJ_TRY(check_inputs(d_bytes, d_offsets, n, p));
   DeviceGuard g(c->device);
   cudaStream_t s = S(stream);
-  c->stats = mj_stats{};
+  begin_call(c, false);
   c->have_part = c->have_cand = false;
   MJ_TRY(derive(c, d_bytes, d_offsets, n, p, s));
   MJ_TRY(partition(c, d_bytes, d_offsets, n, d_table, s));
@@ -504,6 +555,7 @@ int mj_candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, u
   MJ_TRY(candidates(c, d_bytes, d_offsets, n, p->flags, s));
   MJ_CUDA_TRY(cudaStreamSynchronize(s));
   c->have_cand = true;
+  c->stats.n_launches = launch_count() - c->launches_at_start;
   *count = c->n_cand;
   return MJ_OK;
 }
@@ -528,7 +580,7 @@ int mj_verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
   cudaStream_t s = S(stream);
   mj_params p;
   mj_params_default(&p, K);
-  c->stats = mj_stats{};
+  begin_call(c, false);
   MJ_TRY(derive(c, d_bytes, d_offsets, n, &p, s));
   uint32_t kmax = K;
   if (d_k) {
@@ -539,7 +591,9 @@ int mj_verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
     kmax = 0;
     for (uint32_t v : hk) kmax = std::max(kmax, v);
   }
-  return verify(c, d_bytes, d_offsets, d_i, d_j, d_k, m, K, kmax, d_ed, true, s);
+  MJ_TRY(verify(c, d_bytes, d_offsets, d_i, d_j, d_k, m, K, kmax, d_ed, true, s));
+  c->stats.n_launches = launch_count() - c->launches_at_start;
+  return MJ_OK;
 }
 
 int mj_join(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const mj_params* p,
@@ -549,7 +603,7 @@ int mj_join(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_
   if (p->verify_mode != MJ_VERIFY_PLAIN) return MJ_ERR_STATE;
   DeviceGuard g(c->device);
   cudaStream_t s = S(stream);
-  c->stats = mj_stats{};
+  begin_call(c, true);
   c->have_part = c->have_cand = c->have_out = false;
   MJ_CUDA_TRY(cudaEventRecord(c->ev[0], s));
   MJ_TRY(derive(c, d_bytes, d_offsets, n, p, s));
@@ -569,6 +623,7 @@ int mj_join(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_
     MJ_TRY(c->eflags.reserve(m * 4, s));
     MJ_TRY(c->eoffs.reserve(m * 4 + 16, s));
     MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(m), s));
+    tstart(c, 7, s);
     MJ_TRY(launch_ed_flags(c->ed.as<uint32_t>(), m, p->K, c->eflags.as<uint32_t>(), s));
     uint32_t* tot = c->eoffs.as<uint32_t>() + m;
     MJ_TRY(launch_exclusive_scan_u32(c->eflags.as<uint32_t>(), c->eoffs.as<uint32_t>(), m, c->scan_tmp.p, tot, s));
@@ -585,6 +640,7 @@ int mj_join(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_
     MJ_TRY(launch_compact_output(c->cand_i.as<uint32_t>(), c->cand_j.as<uint32_t>(), c->ed.as<uint32_t>(),
                                  c->eflags.as<uint32_t>(), c->eoffs.as<uint32_t>(), m, c->out_i.as<uint32_t>(),
                                  c->out_j.as<uint32_t>(), c->out_ed.as<uint32_t>(), s));
+    tstop(c, 7, s);
     c->n_out = no;
   }
   MJ_CUDA_TRY(cudaEventRecord(c->ev[4], s));
@@ -595,6 +651,9 @@ int mj_join(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_
   c->stats.ms_join_filter = elapsed(c->ev[2], c->ev[3]);
   c->stats.ms_verify = elapsed(c->ev[3], c->ev[4]);
   c->stats.ms_total = elapsed(c->ev[0], c->ev[4]);
+  for (int i = 0; i < mj_ctx::kSections; ++i)
+    c->stats.ms_section[i] = c->sec_used[i] ? elapsed(c->sec_ev[2 * i], c->sec_ev[2 * i + 1]) : 0.f;
+  c->stats.n_launches = launch_count() - c->launches_at_start;
   if (c->stats.device_flags) return MJ_ERR_DEVICE;
   c->have_out = true;
   *count = c->n_out;

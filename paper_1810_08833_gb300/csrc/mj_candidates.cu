@@ -192,7 +192,7 @@ int launch_byte_histogram(const uint8_t* bytes, uint64_t nbytes, unsigned long l
   MJ_CUDA_TRY(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned long long), s));
   if (!nbytes) return MJ_OK;
   byte_hist_kernel<<<grid_for((nbytes + 15) / 16), 256, 0, s>>>(bytes, nbytes, hist);
-  MJ_CUDA_TRY(cudaGetLastError());
+  MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
@@ -200,7 +200,7 @@ int launch_max_length(const int64_t* offsets, uint32_t n, unsigned long long* ou
   MJ_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(unsigned long long), s));
   if (!n) return MJ_OK;
   max_len_kernel<<<grid_for(n), 256, 0, s>>>(offsets, n, out);
-  MJ_CUDA_TRY(cudaGetLastError());
+  MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
@@ -208,7 +208,7 @@ int launch_make_group_keys(const uint32_t* rec_len, const uint32_t* rec_slen, co
                            int slen_bits, uint64_t* keys, uint32_t* idx, cudaStream_t s) {
   if (!n) return MJ_OK;
   group_keys_kernel<<<grid_for(n), 256, 0, s>>>(rec_len, rec_slen, rec_h61, n, slen_bits, keys, idx);
-  MJ_CUDA_TRY(cudaGetLastError());
+  MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
@@ -217,7 +217,7 @@ int launch_gather_records(const uint32_t* idx, uint32_t n, const uint32_t* sid, 
                           cudaStream_t s) {
   if (!n) return MJ_OK;
   gather_kernel<<<grid_for(n), 256, 0, s>>>(idx, n, sid, pos, slen, len, h61, o);
-  MJ_CUDA_TRY(cudaGetLastError());
+  MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
@@ -225,7 +225,7 @@ int launch_count_pairs(const uint64_t* keys, SortedRecs r, uint32_t n, int slen_
                        cudaStream_t s) {
   if (!n) return MJ_OK;
   pairs_kernel<false><<<grid_for(n), 256, 0, s>>>(keys, r, n, slen_bits, K, count, nullptr, nullptr);
-  MJ_CUDA_TRY(cudaGetLastError());
+  MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
@@ -233,7 +233,7 @@ int launch_fill_pairs(const uint64_t* keys, SortedRecs r, uint32_t n, int slen_b
                       uint64_t* pairs, cudaStream_t s) {
   if (!n) return MJ_OK;
   pairs_kernel<true><<<grid_for(n), 256, 0, s>>>(keys, r, n, slen_bits, K, nullptr, offs, pairs);
-  MJ_CUDA_TRY(cudaGetLastError());
+  MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
@@ -241,14 +241,14 @@ int launch_key_check(const uint64_t* keys, SortedRecs r, const uint8_t* bytes, c
                      int slen_bits, unsigned long long* mismatches, cudaStream_t s) {
   if (!n) return MJ_OK;
   key_check_kernel<<<grid_for(n), 256, 0, s>>>(keys, r, bytes, offsets, n, slen_bits, mismatches);
-  MJ_CUDA_TRY(cudaGetLastError());
+  MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
 int launch_unique_flags(const uint64_t* sorted, uint64_t n, uint32_t* flags, cudaStream_t s) {
   if (!n) return MJ_OK;
   unique_flags_kernel<<<grid_for(n), 256, 0, s>>>(sorted, n, flags);
-  MJ_CUDA_TRY(cudaGetLastError());
+  MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
@@ -256,14 +256,14 @@ int launch_compact_pairs(const uint64_t* sorted, const uint32_t* flags, const ui
                          uint32_t* out_i, uint32_t* out_j, cudaStream_t s) {
   if (!n) return MJ_OK;
   compact_pairs_kernel<<<grid_for(n), 256, 0, s>>>(sorted, flags, offs, n, out_i, out_j);
-  MJ_CUDA_TRY(cudaGetLastError());
+  MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
 int launch_ed_flags(const uint32_t* ed, uint64_t m, uint32_t K, uint32_t* flags, cudaStream_t s) {
   if (!m) return MJ_OK;
   ed_flags_kernel<<<grid_for(m), 256, 0, s>>>(ed, m, K, flags);
-  MJ_CUDA_TRY(cudaGetLastError());
+  MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
@@ -272,7 +272,7 @@ int launch_compact_output(const uint32_t* ci, const uint32_t* cj, const uint32_t
                           cudaStream_t s) {
   if (!m) return MJ_OK;
   compact_out_kernel<<<grid_for(m), 256, 0, s>>>(ci, cj, ed, flags, offs, m, oi, oj, oed);
-  MJ_CUDA_TRY(cudaGetLastError());
+  MJ_KERNEL_DONE();
   return MJ_OK;
 }
 

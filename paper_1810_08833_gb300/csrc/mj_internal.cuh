@@ -18,6 +18,14 @@
     }                                                       \
   } while (0)
 
+// every kernel launch of the library is followed by MJ_KERNEL_DONE(): it
+// counts the launch (mj_stats.n_launches) and checks the launch error
+#define MJ_KERNEL_DONE()                  \
+  do {                                    \
+    mj::note_launch();                    \
+    MJ_CUDA_TRY(cudaGetLastError());      \
+  } while (0)
+
 #define MJ_TRY(expr)          \
   do {                        \
     int _s = (expr);          \
@@ -36,6 +44,8 @@ enum : uint32_t {
 };
 
 void set_last_cuda_error(cudaError_t e, const char* expr, const char* file, int line);
+void note_launch();
+uint64_t launch_count();
 
 // ---------------------------------------------------------------- workspace
 // A growable device buffer owned by a context; reallocated (contents

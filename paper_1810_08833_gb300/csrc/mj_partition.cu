@@ -274,7 +274,7 @@ int launch_anchor_flags(const PartitionArgs& a, uint32_t* bitmap, uint32_t* tile
     MJ_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<(unsigned)tiles, kThreads, smem, s>>>(a, bitmap, tile_count, dev_flags);
   }
-  MJ_CUDA_TRY(cudaGetLastError());
+  MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
@@ -283,7 +283,7 @@ int launch_anchor_emit(const PartitionArgs& a, const uint32_t* bitmap, const uin
   const uint64_t tiles = partition_num_tiles(a.nbytes);
   if (tiles == 0) return MJ_OK;
   anchor_emit_kernel<<<(unsigned)tiles, kThreads, 0, s>>>(a, bitmap, tile_offset, anchor_pos, anchor_sid);
-  MJ_CUDA_TRY(cudaGetLastError());
+  MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
@@ -295,7 +295,7 @@ int launch_partition_records(const uint8_t* bytes, const int64_t* offsets, const
   unsigned grid = (unsigned)std::min<uint64_t>((n_anchor + 255) / 256, (uint64_t)kNumSMsHint * 16);
   partition_records_kernel<<<grid, 256, 0, s>>>(bytes, offsets, anchor_pos, anchor_sid, n_anchor, key_base,
                                                 rec_sid, rec_pos, rec_len, rec_slen, rec_h61);
-  MJ_CUDA_TRY(cudaGetLastError());
+  MJ_KERNEL_DONE();
   return MJ_OK;
 }
 

@@ -98,18 +98,21 @@ int exclusive_scan(const TI* in, TO* out, uint64_t n, TO* temp, TO* total_out, c
   }
   uint64_t b = blocks_for(n);
   if (b == 1) {
-    if (total_out) scan_reduce_kernel<TI, TO><<<1, kScanThreads, 0, s>>>(in, n, total_out);
+    if (total_out) {
+      scan_reduce_kernel<TI, TO><<<1, kScanThreads, 0, s>>>(in, n, total_out);
+      MJ_KERNEL_DONE();
+    }
     scan_down_kernel<TI, TO><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
-    MJ_CUDA_TRY(cudaGetLastError());
+    MJ_KERNEL_DONE();
     return MJ_OK;
   }
   TO* sums = temp;
   TO* sums_scanned = temp + b;
   scan_reduce_kernel<TI, TO><<<(unsigned)b, kScanThreads, 0, s>>>(in, n, sums);
-  MJ_CUDA_TRY(cudaGetLastError());
+  MJ_KERNEL_DONE();
   MJ_TRY((exclusive_scan<TO, TO>(sums, sums_scanned, b, temp + 2 * b, total_out, s)));
   scan_down_kernel<TI, TO><<<(unsigned)b, kScanThreads, 0, s>>>(in, out, n, sums_scanned);
-  MJ_CUDA_TRY(cudaGetLastError());
+  MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
@@ -233,10 +236,10 @@ int radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t*
   bool alt = false;
   for (int shift = bit_lo; shift < bit_hi; shift += 8) {
     radix_hist_kernel<<<tiles, kSortThreads, 0, s>>>(src_k, n, shift, tiles, hist);
-    MJ_CUDA_TRY(cudaGetLastError());
+    MJ_KERNEL_DONE();
     MJ_TRY(launch_exclusive_scan_u32(hist, offs, h, scan_tmp, nullptr, s));
     radix_scatter_kernel<<<tiles, kSortThreads, 0, s>>>(src_k, src_v, n, shift, tiles, offs, dst_k, dst_v);
-    MJ_CUDA_TRY(cudaGetLastError());
+    MJ_KERNEL_DONE();
     std::swap(src_k, dst_k);
     std::swap(src_v, dst_v);
     alt = !alt;

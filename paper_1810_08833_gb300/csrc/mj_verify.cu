@@ -234,7 +234,7 @@ int launch_w(const VerifyArgs& a, const RankTable& rt, uint64_t PW, uint32_t GW,
   uint64_t cap = (uint64_t)kNumSMsHint * 16;
   unsigned grid = (unsigned)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
   verify_diag_kernel<W><<<grid, 128, 0, s>>>(a, rt, PW, GW);
-  MJ_CUDA_TRY(cudaGetLastError());
+  MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
@@ -247,7 +247,7 @@ int launch_build_planes(const uint8_t* bytes, uint64_t nbytes, const RankTable& 
   uint64_t cap = (uint64_t)kNumSMsHint * 32;
   build_planes_kernel<<<(unsigned)(blocks > cap ? cap : blocks), 256, 0, s>>>(bytes, nbytes, rt, bits, planes,
                                                                               plane_words, guard_words);
-  MJ_CUDA_TRY(cudaGetLastError());
+  MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
