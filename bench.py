@@ -39,6 +39,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 SM_COUNT = 152
 INT_LANES_PER_SM = 64        # 32-bit integer ALU lanes per SM and clock (4 partitions x 16)
+ALU_OPS_PER_WORD_COLUMN = 16 # ops of one band word in one column of the bit-vector recurrence
 
 
 def band_cells(m: np.ndarray, n: np.ndarray, K: int) -> int:
@@ -280,6 +281,7 @@ def run_native(args):
             "cells_per_step": cells_all,
             "candidates": int(last["n_candidates"]), "raw_pairs": int(last["n_raw_pairs"]),
             "partitions": int(last["n_partitions"]), "output_pairs": int(last["n_output"]),
+            "verify_word_columns": int(last["verify_word_columns"]),
             "sections_ms": {k: round(v, 4) for k, v in sec_ms.items()},
             "roofline": roof,
             "e2e": {"value": cells_all / (ms_e2e / 1000.0), "unit": UNIT, "ms_per_step": ms_e2e,
@@ -317,10 +319,11 @@ def roofline(section: str, ms: float, st: dict, nbytes: int, hbm: float, hbm_src
         ach = traffic / sec / 1e9
         return {"kernel": section, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "traffic": None, "peak_source": hbm_src}
-    # verification and pair emission are integer-ALU work: K-band cells at
-    # one bit per cell, 17 32-bit ops per 32 cells (one word-column)
+    # verification is integer-ALU work: the bit-vector recurrence costs 16
+    # 32-bit operations per band word and column (ALU_OPS_PER_WORD_COLUMN),
+    # counted over the word-columns the verifier actually advanced
     peak = SM_COUNT * INT_LANES_PER_SM * sm_mhz * 1e6 / 1e9   # Gop/s
-    ops = st["band_cells"] / 32.0 * 17.0
+    ops = st["verify_word_columns"] * ALU_OPS_PER_WORD_COLUMN
     ach = ops / sec / 1e9
     return {"kernel": section, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gop/s", "frac": ach / peak,
             "traffic": None, "peak_source": f"{SM_COUNT} SMs x {INT_LANES_PER_SM} int32 lanes x {sm_mhz:.0f} MHz"}

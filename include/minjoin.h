@@ -101,6 +101,7 @@ typedef struct {
    * (filters of Alg. 3), 4 pair dedup, 5 equality bit-planes, 6 verification
    * kernel(s), 7 output compaction */
   float ms_section[8];
+  uint64_t verify_word_columns; /* 32-bit band words x columns the verifier advanced */
 } mj_stats;
 
 void mj_params_default(mj_params* p, uint32_t K);

@@ -99,7 +99,7 @@ struct mj_ctx {
   unsigned long long* h_small = nullptr;
   // workspace
   Buf hist, dev_flags, small;
-  Buf bitmap, tile_count, tile_off, scan_tmp;
+  Buf bitmap, tile_count, tile_off, scan_tmp, tile_first;
   Buf anchor_pos, anchor_sid;
   Buf rec_sid, rec_pos, rec_len, rec_slen, rec_h61;
   Buf keys, keys_alt, idx, idx_alt, sort_tmp;
@@ -110,6 +110,10 @@ struct mj_ctx {
   Buf out_i, out_j, out_ed;
   Buf in_bytes, in_offsets;  // staging for mj_join_host
   uint64_t n_part = 0, n_cand = 0, n_out = 0;
+  // bit-planes written by the partition kernel for the verifier
+  bool planes_ready = false;
+  uint64_t planes_pw = 0;
+  uint32_t planes_gw = 0;
   bool have_part = false, have_cand = false, have_out = false;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   // section timers of mj_join (mj_stats.ms_section)
@@ -153,6 +157,7 @@ void tstop(mj_ctx* c, int i, cudaStream_t s) {
 
 void begin_call(mj_ctx* c, bool timing) {
   c->stats = mj_stats{};
+  c->planes_ready = false;
   c->timing = timing;
   for (bool& u : c->sec_used) u = false;
   c->launches_at_start = launch_count();
@@ -218,8 +223,10 @@ uint64_t key_base_for(uint64_t seed) {
 }
 
 // a2-a4 (after derive): records in c->rec_*.
+// plane_kmax > 0: also write the verifier's bit-planes (guard sized for bands
+// up to plane_kmax).
 int partition(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const uint64_t* d_table,
-              cudaStream_t s) {
+              uint32_t plane_kmax, cudaStream_t s) {
   const Derived& d = c->d;
   const uint64_t nbytes = c->stats.n_bytes;
   if (d.r_max > 8192) return MJ_ERR_UNSUPPORTED;
@@ -232,7 +239,7 @@ int partition(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
   a.bits = d.bits;
   a.T = d.T;
   a.r_min = d.r_min;
-  a.r_max = d.r_max;
+  a.r_max = d.r_max < 1 ? 1 : d.r_max;   // halo of at least one position
   a.seed32 = (uint32_t)d.seed ^ (uint32_t)(d.seed >> 32);
   a.seed64 = d.seed;
   a.table = d_table;
@@ -244,12 +251,35 @@ int partition(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
   MJ_CUDA_TRY(cudaMemsetAsync(c->dev_flags.p, 0, 64, s));
   MJ_TRY(c->bitmap.reserve(tiles * (kPartTile / 32) * sizeof(uint32_t), s));
   MJ_TRY(c->tile_count.reserve(tiles * sizeof(uint32_t), s));
+  MJ_TRY(c->tile_first.reserve(tiles * sizeof(uint32_t), s));
   MJ_TRY(c->tile_off.reserve(tiles * sizeof(uint32_t) + 16, s));
   MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(tiles), s));
+  c->planes_ready = false;
+  uint32_t* planes = nullptr;
+  uint64_t PW = 0;
+  uint32_t GW = 0;
+  if (plane_kmax > 0) {
+    GW = plane_guard_words(plane_kmax);
+    PW = tiles * (kPartTile / 32) + 2 * (uint64_t)GW;
+    MJ_TRY(c->planes.reserve(PW * d.bits * 4, s));
+    planes = c->planes.as<uint32_t>();
+    // guard words before and after every plane's data are zero
+    MJ_CUDA_TRY(cudaMemsetAsync(planes, 0, (size_t)GW * 4, s));
+    for (uint32_t p = 0; p < d.bits; ++p) {
+      const uint64_t from = (uint64_t)p * PW + GW + tiles * (kPartTile / 32);
+      const uint64_t words = (p + 1 < d.bits) ? 2 * (uint64_t)GW : (uint64_t)GW;
+      MJ_CUDA_TRY(cudaMemsetAsync(planes + from, 0, words * 4, s));
+    }
+  }
   tstart(c, 0, s);
   MJ_TRY(launch_anchor_flags(a, c->bitmap.as<uint32_t>(), c->tile_count.as<uint32_t>(),
-                             c->dev_flags.as<uint32_t>(), s));
+                             c->dev_flags.as<uint32_t>(), planes, PW, GW, c->tile_first.as<uint32_t>(), s));
   tstop(c, 0, s);
+  if (planes) {
+    c->planes_ready = true;
+    c->planes_pw = PW;
+    c->planes_gw = GW;
+  }
   uint32_t* total = c->tile_off.as<uint32_t>() + tiles;
   MJ_TRY(launch_exclusive_scan_u32(c->tile_count.as<uint32_t>(), c->tile_off.as<uint32_t>(), tiles,
                                    c->scan_tmp.p, total, s));
@@ -262,7 +292,8 @@ int partition(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
   MJ_TRY(c->anchor_pos.reserve((size_t)n_anchor * 4 + 16, s));
   MJ_TRY(c->anchor_sid.reserve((size_t)n_anchor * 4 + 16, s));
   tstart(c, 1, s);
-  MJ_TRY(launch_anchor_emit(a, c->bitmap.as<uint32_t>(), c->tile_off.as<uint32_t>(), c->anchor_pos.as<uint32_t>(),
+  MJ_TRY(launch_anchor_emit(a, c->bitmap.as<uint32_t>(), c->tile_off.as<uint32_t>(), c->tile_first.as<uint32_t>(),
+                            c->anchor_pos.as<uint32_t>(),
                             c->anchor_sid.as<uint32_t>(), s));
   MJ_TRY(c->rec_sid.reserve((size_t)n_anchor * 4 + 16, s));
   MJ_TRY(c->rec_pos.reserve((size_t)n_anchor * 4 + 16, s));
@@ -337,10 +368,10 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   MJ_TRY(c->pairs.reserve(raw * 8, s));
   MJ_TRY(c->pairs_alt.reserve(raw * 8, s));
   tstart(c, 4, s);
-  MJ_TRY(launch_fill_pairs(skeys, r, nr, slen_bits, d.K, c->pair_off.as<uint64_t>(), c->pairs.as<uint64_t>(), s));
+  const int nb = bits_for(n ? n - 1 : 0);   // pair (i, j) packed as i << nb | j
+  MJ_TRY(launch_fill_pairs(skeys, r, nr, slen_bits, d.K, nb, c->pair_off.as<uint64_t>(), c->pairs.as<uint64_t>(), s));
   MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(raw), s));
-  const int nb = bits_for(n ? n - 1 : 0);
-  MJ_TRY(radix_sort_u64(c->pairs.as<uint64_t>(), c->pairs_alt.as<uint64_t>(), nullptr, nullptr, raw, 0, 32 + nb,
+  MJ_TRY(radix_sort_u64(c->pairs.as<uint64_t>(), c->pairs_alt.as<uint64_t>(), nullptr, nullptr, raw, 0, 2 * nb,
                         c->sort_tmp.p, &alt, s));
   const uint64_t* sp = alt ? c->pairs_alt.as<uint64_t>() : c->pairs.as<uint64_t>();
   MJ_TRY(c->uflags.reserve(raw * 4, s));
@@ -353,8 +384,8 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   const uint32_t nc = *(uint32_t*)c->h_small;
   MJ_TRY(c->cand_i.reserve((size_t)nc * 4 + 16, s));
   MJ_TRY(c->cand_j.reserve((size_t)nc * 4 + 16, s));
-  MJ_TRY(launch_compact_pairs(sp, c->uflags.as<uint32_t>(), c->uoffs.as<uint32_t>(), raw, c->cand_i.as<uint32_t>(),
-                              c->cand_j.as<uint32_t>(), s));
+  MJ_TRY(launch_compact_pairs(sp, c->uflags.as<uint32_t>(), c->uoffs.as<uint32_t>(), raw, nb,
+                              c->cand_i.as<uint32_t>(), c->cand_j.as<uint32_t>(), s));
   tstop(c, 4, s);
   c->n_cand = nc;
   c->stats.n_candidates = nc;
@@ -364,23 +395,28 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
 // a8 on arbitrary pairs (rank codes from c->d).
 int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const uint32_t* d_i, const uint32_t* d_j,
            const uint32_t* d_k, uint64_t m, uint32_t K, uint32_t kmax, uint32_t* d_ed, bool count_cells,
-           cudaStream_t s) {
+           cudaStream_t s, const uint32_t* order = nullptr) {
   const Derived& d = c->d;
   if (m == 0) return MJ_OK;
   if (kmax >= (1u << 16)) return MJ_ERR_UNSUPPORTED;
   const uint64_t nbytes = c->stats.n_bytes;
-  const uint32_t GW = plane_guard_words(kmax);
-  const uint64_t PW = (nbytes + 31) / 32 + 2 * (uint64_t)GW;
-  MJ_TRY(c->planes.reserve(PW * d.bits * 4, s));
-  RankTable rt;
-  memcpy(rt.r, d.rank, 256);
-  tstart(c, 5, s);
-  MJ_TRY(launch_build_planes(d_bytes, nbytes, rt, d.bits, c->planes.as<uint32_t>(), PW, GW, s));
-  tstop(c, 5, s);
+  uint32_t GW = plane_guard_words(kmax);
+  uint64_t PW = (nbytes + 31) / 32 + 2 * (uint64_t)GW;
+  if (c->planes_ready && c->planes_gw >= GW) {
+    GW = c->planes_gw;   // written by the partition kernel of this call
+    PW = c->planes_pw;
+  } else {
+    MJ_TRY(c->planes.reserve(PW * d.bits * 4, s));
+    RankTable rt;
+    memcpy(rt.r, d.rank, 256);
+    tstart(c, 5, s);
+    MJ_TRY(launch_build_planes(d_bytes, nbytes, rt, d.bits, c->planes.as<uint32_t>(), PW, GW, s));
+    tstop(c, 5, s);
+  }
   MJ_TRY(c->dev_flags.reserve(64, s));
   MJ_CUDA_TRY(cudaMemsetAsync(c->dev_flags.p, 0, 64, s));
   MJ_TRY(c->small.reserve(64, s));
-  MJ_CUDA_TRY(cudaMemsetAsync(c->small.p, 0, 16, s));
+  MJ_CUDA_TRY(cudaMemsetAsync(c->small.p, 0, 32, s));
   VerifyArgs a;
   a.planes = c->planes.as<uint32_t>();
   a.bits = d.bits;
@@ -390,13 +426,15 @@ int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const ui
   a.pi = d_i;
   a.pj = d_j;
   a.pk = d_k;
+  a.order = order;
   a.K = K;
   a.m = m;
   a.ed = d_ed;
   a.cells = count_cells ? c->small.as<unsigned long long>() : nullptr;
+  a.work = c->small.as<unsigned long long>() + 2;
   a.dev_flags = c->dev_flags.as<uint32_t>();
   tstart(c, 6, s);
-  MJ_TRY(launch_verify(a, rt, PW, GW, kmax, s));
+  MJ_TRY(launch_verify(a, PW, GW, kmax, c->small.as<unsigned long long>() + 1, s));
   tstop(c, 6, s);
   return MJ_OK;
 }
@@ -470,6 +508,7 @@ void mj_destroy(mj_ctx* c) {
   DeviceGuard g(c->device);
   cudaDeviceSynchronize();
   Buf* bufs[] = {&c->hist, &c->dev_flags, &c->small, &c->bitmap, &c->tile_count, &c->tile_off, &c->scan_tmp,
+                 &c->tile_first,
                  &c->anchor_pos, &c->anchor_sid, &c->rec_sid, &c->rec_pos, &c->rec_len, &c->rec_slen,
                  &c->rec_h61, &c->keys, &c->keys_alt, &c->idx, &c->idx_alt, &c->sort_tmp, &c->s_sid, &c->s_pos,
                  &c->s_slen, &c->s_len, &c->s_h61, &c->pair_count, &c->pair_off, &c->pairs, &c->pairs_alt,
@@ -518,7 +557,7 @@ int mj_partition(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, ui
   begin_call(c, false);
   c->have_part = false;
   MJ_TRY(derive(c, d_bytes, d_offsets, n, p, s));
-  MJ_TRY(partition(c, d_bytes, d_offsets, n, d_table, s));
+  MJ_TRY(partition(c, d_bytes, d_offsets, n, d_table, 0, s));
   MJ_CUDA_TRY(cudaStreamSynchronize(s));
   c->have_part = true;
   c->stats.n_launches = launch_count() - c->launches_at_start;
@@ -550,7 +589,7 @@ int mj_candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, u
   begin_call(c, false);
   c->have_part = c->have_cand = false;
   MJ_TRY(derive(c, d_bytes, d_offsets, n, p, s));
-  MJ_TRY(partition(c, d_bytes, d_offsets, n, d_table, s));
+  MJ_TRY(partition(c, d_bytes, d_offsets, n, d_table, 0, s));
   c->have_part = true;
   MJ_TRY(candidates(c, d_bytes, d_offsets, n, p->flags, s));
   MJ_CUDA_TRY(cudaStreamSynchronize(s));
@@ -608,7 +647,7 @@ int mj_join(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_
   MJ_CUDA_TRY(cudaEventRecord(c->ev[0], s));
   MJ_TRY(derive(c, d_bytes, d_offsets, n, p, s));
   MJ_CUDA_TRY(cudaEventRecord(c->ev[1], s));
-  MJ_TRY(partition(c, d_bytes, d_offsets, n, nullptr, s));
+  MJ_TRY(partition(c, d_bytes, d_offsets, n, nullptr, p->K, s));
   c->have_part = true;
   MJ_CUDA_TRY(cudaEventRecord(c->ev[2], s));
   MJ_TRY(candidates(c, d_bytes, d_offsets, n, p->flags, s));
@@ -618,8 +657,21 @@ int mj_join(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_
   c->n_out = 0;
   if (m) {
     MJ_TRY(c->ed.reserve(m * 4, s));
+    // longest pairs first, so that the persistent verifier does not end on a
+    // tail of long pairs
+    MJ_TRY(c->keys.reserve(m * 8, s));
+    MJ_TRY(c->keys_alt.reserve(m * 8, s));
+    MJ_TRY(c->idx.reserve(m * 4, s));
+    MJ_TRY(c->idx_alt.reserve(m * 4, s));
+    MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(m), s));
+    MJ_TRY(launch_work_keys(c->cand_i.as<uint32_t>(), c->cand_j.as<uint32_t>(), d_offsets, m, c->d.N,
+                            c->keys.as<uint64_t>(), c->idx.as<uint32_t>(), s));
+    bool oalt = false;
+    MJ_TRY(radix_sort_u64(c->keys.as<uint64_t>(), c->keys_alt.as<uint64_t>(), c->idx.as<uint32_t>(),
+                          c->idx_alt.as<uint32_t>(), m, 0, bits_for(c->d.N), c->sort_tmp.p, &oalt, s));
+    const uint32_t* order = oalt ? c->idx_alt.as<uint32_t>() : c->idx.as<uint32_t>();
     MJ_TRY(verify(c, d_bytes, d_offsets, c->cand_i.as<uint32_t>(), c->cand_j.as<uint32_t>(), nullptr, m, p->K, p->K,
-                  c->ed.as<uint32_t>(), true, s));
+                  c->ed.as<uint32_t>(), true, s, order));
     MJ_TRY(c->eflags.reserve(m * 4, s));
     MJ_TRY(c->eoffs.reserve(m * 4 + 16, s));
     MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(m), s));
@@ -629,10 +681,12 @@ int mj_join(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_
     MJ_TRY(launch_exclusive_scan_u32(c->eflags.as<uint32_t>(), c->eoffs.as<uint32_t>(), m, c->scan_tmp.p, tot, s));
     MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small, tot, 4, cudaMemcpyDeviceToHost, s));
     MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small + 1, c->small.p, 8, cudaMemcpyDeviceToHost, s));
+    MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small + 3, c->small.as<unsigned long long>() + 2, 8, cudaMemcpyDeviceToHost, s));
     MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small + 2, c->dev_flags.p, 4, cudaMemcpyDeviceToHost, s));
     MJ_CUDA_TRY(cudaStreamSynchronize(s));
     const uint32_t no = *(uint32_t*)c->h_small;
     c->stats.band_cells = c->h_small[1];
+    c->stats.verify_word_columns = c->h_small[3];
     c->stats.device_flags |= *(uint32_t*)(c->h_small + 2);
     MJ_TRY(c->out_i.reserve((size_t)no * 4 + 16, s));
     MJ_TRY(c->out_j.reserve((size_t)no * 4 + 16, s));

@@ -90,7 +90,7 @@ __device__ __forceinline__ int64_t iabs64(int64_t x) { return x < 0 ? -x : x; }
 // Walks the run of record t; EMIT=false counts, EMIT=true writes pairs.
 template <bool EMIT>
 __global__ void pairs_kernel(const uint64_t* __restrict__ keys, SortedRecs r, uint32_t n, int slen_bits, uint32_t K,
-                             uint32_t* __restrict__ count, const uint64_t* __restrict__ offs,
+                             int nb, uint32_t* __restrict__ count, const uint64_t* __restrict__ offs,
                              uint64_t* __restrict__ pairs) {
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t run = keys[t] >> slen_bits;
@@ -110,7 +110,7 @@ __global__ void pairs_kernel(const uint64_t* __restrict__ keys, SortedRecs r, ui
       if (iabs64(pos - pos_u) + iabs64((slen - pos) - (slen_u - pos_u)) > (int64_t)K) continue;  // position filter
       if (EMIT) {
         uint32_t a = sid < sid_u ? sid : sid_u, b = sid < sid_u ? sid_u : sid;
-        pairs[out++] = ((uint64_t)a << 32) | b;
+        pairs[out++] = ((uint64_t)a << nb) | b;
       } else {
         ++c;
       }
@@ -150,13 +150,13 @@ __global__ void unique_flags_kernel(const uint64_t* __restrict__ s, uint64_t n, 
 }
 
 __global__ void compact_pairs_kernel(const uint64_t* __restrict__ s, const uint32_t* __restrict__ flags,
-                                     const uint32_t* __restrict__ offs, uint64_t n, uint32_t* __restrict__ oi,
+                                     const uint32_t* __restrict__ offs, uint64_t n, int nb, uint32_t* __restrict__ oi,
                                      uint32_t* __restrict__ oj) {
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
     if (flags[t]) {
       uint32_t o = offs[t];
-      oi[o] = (uint32_t)(s[t] >> 32);
-      oj[o] = (uint32_t)s[t];
+      oi[o] = (uint32_t)(s[t] >> nb);
+      oj[o] = (uint32_t)(s[t] & ((1ull << nb) - 1));
     }
   }
 }
@@ -177,6 +177,19 @@ __global__ void compact_out_kernel(const uint32_t* __restrict__ ci, const uint32
       oj[o] = cj[t];
       oed[o] = ed[t];
     }
+  }
+}
+
+// Work-order key of a candidate: longest pairs first (key = N - min length).
+__global__ void work_keys_kernel(const uint32_t* __restrict__ ci, const uint32_t* __restrict__ cj,
+                                 const int64_t* __restrict__ offsets, uint64_t m, uint64_t N,
+                                 uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t x = ci[t], y = cj[t];
+    const int64_t lx = offsets[x + 1] - offsets[x], ly = offsets[y + 1] - offsets[y];
+    const int64_t n = lx < ly ? lx : ly;
+    keys[t] = N - (uint64_t)n;
+    vals[t] = (uint32_t)t;
   }
 }
 
@@ -224,15 +237,15 @@ int launch_gather_records(const uint32_t* idx, uint32_t n, const uint32_t* sid, 
 int launch_count_pairs(const uint64_t* keys, SortedRecs r, uint32_t n, int slen_bits, uint32_t K, uint32_t* count,
                        cudaStream_t s) {
   if (!n) return MJ_OK;
-  pairs_kernel<false><<<grid_for(n), 256, 0, s>>>(keys, r, n, slen_bits, K, count, nullptr, nullptr);
+  pairs_kernel<false><<<grid_for(n), 256, 0, s>>>(keys, r, n, slen_bits, K, 0, count, nullptr, nullptr);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
-int launch_fill_pairs(const uint64_t* keys, SortedRecs r, uint32_t n, int slen_bits, uint32_t K, const uint64_t* offs,
-                      uint64_t* pairs, cudaStream_t s) {
+int launch_fill_pairs(const uint64_t* keys, SortedRecs r, uint32_t n, int slen_bits, uint32_t K, int nb,
+                      const uint64_t* offs, uint64_t* pairs, cudaStream_t s) {
   if (!n) return MJ_OK;
-  pairs_kernel<true><<<grid_for(n), 256, 0, s>>>(keys, r, n, slen_bits, K, nullptr, offs, pairs);
+  pairs_kernel<true><<<grid_for(n), 256, 0, s>>>(keys, r, n, slen_bits, K, nb, nullptr, offs, pairs);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }
@@ -252,10 +265,18 @@ int launch_unique_flags(const uint64_t* sorted, uint64_t n, uint32_t* flags, cud
   return MJ_OK;
 }
 
-int launch_compact_pairs(const uint64_t* sorted, const uint32_t* flags, const uint32_t* offs, uint64_t n,
+int launch_compact_pairs(const uint64_t* sorted, const uint32_t* flags, const uint32_t* offs, uint64_t n, int nb,
                          uint32_t* out_i, uint32_t* out_j, cudaStream_t s) {
   if (!n) return MJ_OK;
-  compact_pairs_kernel<<<grid_for(n), 256, 0, s>>>(sorted, flags, offs, n, out_i, out_j);
+  compact_pairs_kernel<<<grid_for(n), 256, 0, s>>>(sorted, flags, offs, n, nb, out_i, out_j);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
+int launch_work_keys(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m, uint64_t N,
+                     uint64_t* keys, uint32_t* vals, cudaStream_t s) {
+  if (!m) return MJ_OK;
+  work_keys_kernel<<<grid_for(m), 256, 0, s>>>(ci, cj, offsets, m, N, keys, vals);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }

@@ -88,13 +88,16 @@ struct PartitionArgs {
   const uint64_t* table;  // nullable explicit Pi
   uint8_t rank[256];
 };
-constexpr int kPartTile = 4096;  // byte positions per CTA tile
+constexpr int kPartTile = 2048;  // byte positions per CTA tile
 uint64_t partition_num_tiles(uint64_t nbytes);
+// planes (nullable): also writes the rank-code bit-planes of the tile for the
+// verifier (plane p word guard_words + g/32 holds positions g .. g+31).
 int launch_anchor_flags(const PartitionArgs& a, uint32_t* bitmap, uint32_t* tile_count,
-                        uint32_t* dev_flags, cudaStream_t s);
+                        uint32_t* dev_flags, uint32_t* planes, uint64_t plane_words,
+                        uint32_t guard_words, uint32_t* tile_first, cudaStream_t s);
 // a4: anchors in position order (global byte position and string id).
 int launch_anchor_emit(const PartitionArgs& a, const uint32_t* bitmap, const uint32_t* tile_offset,
-                       uint32_t* anchor_pos, uint32_t* anchor_sid, cudaStream_t s);
+                       const uint32_t* tile_first, uint32_t* anchor_pos, uint32_t* anchor_sid, cudaStream_t s);
 // a4: partition records from consecutive anchors; key = (len, H61(substring)).
 int launch_partition_records(const uint8_t* bytes, const int64_t* offsets, const uint32_t* anchor_pos,
                              const uint32_t* anchor_sid, uint32_t n_anchor, uint64_t key_base,
@@ -134,13 +137,14 @@ int launch_gather_records(const uint32_t* idx, uint32_t n_rec, const uint32_t* r
                           const uint64_t* rec_h61, SortedRecs out, cudaStream_t s);
 int launch_count_pairs(const uint64_t* keys, SortedRecs r, uint32_t n_rec, int slen_bits, uint32_t K,
                        uint32_t* count, cudaStream_t s);
-int launch_fill_pairs(const uint64_t* keys, SortedRecs r, uint32_t n_rec, int slen_bits, uint32_t K,
+// pairs are packed as (i << nb) | j, i < j
+int launch_fill_pairs(const uint64_t* keys, SortedRecs r, uint32_t n_rec, int slen_bits, uint32_t K, int nb,
                       const uint64_t* offs, uint64_t* pairs, cudaStream_t s);
 int launch_key_check(const uint64_t* keys, SortedRecs r, const uint8_t* bytes, const int64_t* offsets,
                      uint32_t n_rec, int slen_bits, unsigned long long* mismatches, cudaStream_t s);
 // a7: unique of sorted u64 pairs -> flags; then compaction.
 int launch_unique_flags(const uint64_t* sorted, uint64_t n, uint32_t* flags, cudaStream_t s);
-int launch_compact_pairs(const uint64_t* sorted, const uint32_t* flags, const uint32_t* offs, uint64_t n,
+int launch_compact_pairs(const uint64_t* sorted, const uint32_t* flags, const uint32_t* offs, uint64_t n, int nb,
                          uint32_t* out_i, uint32_t* out_j, cudaStream_t s);
 
 // a8: banded verification (diagonal bit-vector, one thread per pair).
@@ -156,18 +160,25 @@ struct VerifyArgs {
   const uint32_t* pi;
   const uint32_t* pj;
   const uint32_t* pk;        // nullable per-pair band
+  const uint32_t* order;     // nullable: pair indices in the order to verify them
   uint32_t K;
   uint64_t m;
   uint32_t* ed;
   unsigned long long* cells; // nullable: K-band cells accumulated
+  unsigned long long* work;  // nullable: word-columns processed (columns x W) accumulated
   uint32_t* dev_flags;
 };
 int verify_words_for(uint32_t kmax);
 inline uint32_t plane_guard_words(uint32_t kmax) { return kmax / 64 + (uint32_t)verify_words_for(kmax) + 4; }
 int launch_build_planes(const uint8_t* bytes, uint64_t nbytes, const RankTable& rt, uint32_t bits,
                         uint32_t* planes, uint64_t plane_words, uint32_t guard_words, cudaStream_t s);
-int launch_verify(const VerifyArgs& a, const RankTable& rt, uint64_t plane_words, uint32_t guard_words,
-                  uint32_t kmax, cudaStream_t s);
+// `next` is a device counter the persistent kernel hands pairs out from.
+int launch_verify(const VerifyArgs& a, uint64_t plane_words, uint32_t guard_words, uint32_t kmax,
+                  unsigned long long* next, cudaStream_t s);
+
+// verification order: candidate indices sorted by key = N - min length
+int launch_work_keys(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m, uint64_t N,
+                     uint64_t* keys, uint32_t* vals, cudaStream_t s);
 
 // output compaction (ED <= K)
 int launch_ed_flags(const uint32_t* ed, uint64_t m, uint32_t K, uint32_t* flags, cudaStream_t s);

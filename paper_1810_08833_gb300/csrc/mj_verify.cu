@@ -40,6 +40,7 @@ namespace {
 
 constexpr int kMaxBits = 8;
 
+// One 32-symbol word per thread (two 16-byte loads where aligned).
 __global__ void build_planes_kernel(const uint8_t* __restrict__ bytes, uint64_t nbytes, RankTable rt, uint32_t bits,
                                     uint32_t* __restrict__ planes, uint64_t plane_words, uint32_t guard_words) {
   __shared__ uint8_t s_rank[256];
@@ -48,11 +49,29 @@ __global__ void build_planes_kernel(const uint8_t* __restrict__ bytes, uint64_t 
   for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < plane_words;
        w += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t acc[kMaxBits] = {0};
-    int64_t c0 = ((int64_t)w - (int64_t)guard_words) * 32;
+    const int64_t c0 = ((int64_t)w - (int64_t)guard_words) * 32;
+    uint32_t sym[8];
+    const bool full = c0 >= 0 && (uint64_t)c0 + 32 <= nbytes && ((uintptr_t)(bytes + c0) & 15) == 0;
+    if (full) {
+      const uint4 u = __ldg(reinterpret_cast<const uint4*>(bytes + c0));
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(bytes + c0 + 16));
+      sym[0] = u.x; sym[1] = u.y; sym[2] = u.z; sym[3] = u.w;
+      sym[4] = v.x; sym[5] = v.y; sym[6] = v.z; sym[7] = v.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        uint32_t x = 0;
+        for (int b = 0; b < 4; ++b) {
+          const int64_t c = c0 + 4 * q + b;
+          if (c >= 0 && (uint64_t)c < nbytes) x |= (uint32_t)__ldg(bytes + c) << (8 * b);
+        }
+        sym[q] = x;
+      }
+    }
+#pragma unroll
     for (int t = 0; t < 32; ++t) {
-      int64_t c = c0 + t;
-      if (c < 0 || (uint64_t)c >= nbytes) continue;
-      uint32_t r = s_rank[__ldg(bytes + c)];
+      const int64_t c = c0 + t;
+      const uint32_t r = (c >= 0 && (uint64_t)c < nbytes) ? s_rank[(sym[t >> 2] >> (8 * (t & 3))) & 255u] : 0u;
 #pragma unroll
       for (int p = 0; p < kMaxBits; ++p) acc[p] |= ((r >> p) & 1u) << t;
     }
@@ -73,108 +92,160 @@ __device__ __forceinline__ uint64_t band_cells(int64_t m, int64_t n, int64_t K) 
   return (uint64_t)(smin - smax + n);
 }
 
-template <int W>
-__device__ uint32_t verify_pair(const VerifyArgs& a, const uint8_t* s_rank, uint64_t PW, uint32_t GW,
-                                uint32_t x, uint32_t y, uint32_t k) {
+// Per-lane state of one pair in flight.
+template <int W, int P>
+struct PairState {
+  uint32_t Pv[W], Mv[W], M1[W];
+  uint32_t pw[P][W + 1];   // window of A's plane words (row-fixed)
+  uint32_t bw[P];          // B's plane bits of the current 32 columns
+  uint64_t wbase;          // plane word index of pw[.][0]
+  uint64_t bpos;           // plane bit index of B's next column symbol
+  int64_t j, n;            // next column, number of columns
+  int32_t score;           // D at the band's top row
+  uint32_t sh;             // bit offset of the window in pw
+  uint32_t k;              // band of this pair
+  uint64_t t;              // pair index
+};
+
+// Sets up pair t; returns false if the pair is decided without the DP
+// (result written to *res).
+template <int W, int P>
+__device__ __forceinline__ bool pair_init(PairState<W, P>& st, const VerifyArgs& a, uint64_t PW, uint32_t GW,
+                                          uint64_t t, uint32_t* res) {
+  const uint32_t x = a.pi[t], y = a.pj[t];
+  const uint32_t k = a.pk ? a.pk[t] : a.K;
+  st.t = t;
+  st.k = k;
+  if (x >= a.n_strings || y >= a.n_strings) {
+    atomicOr(a.dev_flags, FLAG_BOUNDS);
+    *res = k + 1;
+    return false;
+  }
   const int64_t ox = __ldg(a.offsets + x), lx = __ldg(a.offsets + x + 1) - ox;
   const int64_t oy = __ldg(a.offsets + y), ly = __ldg(a.offsets + y + 1) - oy;
   const bool xa = lx >= ly;
   const int64_t oA = xa ? ox : oy, m = xa ? lx : ly;
   const int64_t oB = xa ? oy : ox, n = xa ? ly : lx;
   const int64_t d0 = m - n;
-  if (d0 > (int64_t)k) return k + 1;
-  if (n == 0) return (uint32_t)d0;
-  const int32_t dlo = -(int32_t)(((int64_t)k - d0) >> 1);
-  const int32_t t0 = (int32_t)d0 - dlo;                // bit of diagonal d0, < 32W by dispatch
-  if (t0 >= 32 * W) {                                  // cannot happen with a correct dispatch
-    atomicOr(a.dev_flags, FLAG_BOUNDS);
-    return k + 1;
+  if (d0 > (int64_t)k) {
+    *res = k + 1;
+    return false;
   }
-
-  uint32_t Pv[W], Mv[W], M1[W];
-  const int32_t nneg = 1 - dlo;                        // band rows dlo..0 (virtual or row 0)
+  if (n == 0) {
+    *res = (uint32_t)d0;
+    return false;
+  }
+  const int32_t dlo = -(int32_t)(((int64_t)k - d0) >> 1);
+  const int32_t t0 = (int32_t)d0 - dlo;  // bit of diagonal d0
+  if (t0 >= 32 * W) {                    // cannot happen with a correct dispatch
+    atomicOr(a.dev_flags, FLAG_BOUNDS);
+    *res = k + 1;
+    return false;
+  }
+  const int32_t nneg = 1 - dlo;          // band rows dlo..0 (virtual rows and row 0)
 #pragma unroll
   for (int w = 0; w < W; ++w) {
     const int lo = 32 * w;
-    uint32_t neg = nneg >= lo + 32 ? 0xffffffffu : (nneg <= lo ? 0u : ((1u << (nneg - lo)) - 1u));
-    Mv[w] = neg;
-    Pv[w] = ~neg;
-    // bits 1..t0
-    int32_t a0 = 1 - lo, a1 = t0 + 1 - lo;             // [a0, a1) within this word
+    const uint32_t neg = nneg >= lo + 32 ? 0xffffffffu : (nneg <= lo ? 0u : ((1u << (nneg - lo)) - 1u));
+    st.Mv[w] = neg;
+    st.Pv[w] = ~neg;
+    int32_t a0 = 1 - lo, a1 = t0 + 1 - lo;  // bits 1..t0 within this word: [a0, a1)
     a0 = a0 < 0 ? 0 : a0;
     a1 = a1 > 32 ? 32 : a1;
-    uint32_t hiMask = a1 >= 32 ? 0xffffffffu : (a1 <= 0 ? 0u : ((1u << a1) - 1u));
-    uint32_t loMask = a0 >= 32 ? 0xffffffffu : ((1u << a0) - 1u);
-    M1[w] = a1 > a0 ? (hiMask & ~loMask) : 0u;
+    const uint32_t hiMask = a1 >= 32 ? 0xffffffffu : (a1 <= 0 ? 0u : ((1u << a1) - 1u));
+    const uint32_t loMask = a0 >= 32 ? 0xffffffffu : ((1u << a0) - 1u);
+    st.M1[w] = a1 > a0 ? (hiMask & ~loMask) : 0u;
   }
-  int64_t score = -dlo;                                // D[dlo][0] = -dlo
+  st.score = -dlo;                       // D[dlo][0] = -dlo
+  const uint64_t S = (uint64_t)(oA + dlo + 32 * (int64_t)GW);  // plane bit of row 1 + dlo (column 1)
+  st.wbase = S >> 5;
+  st.sh = (uint32_t)(S & 31);
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+#pragma unroll
+    for (int w = 0; w <= W; ++w) st.pw[p][w] = p < (int)a.bits ? __ldg(a.planes + (uint64_t)p * PW + st.wbase + w) : 0u;
+  }
+  st.bpos = (uint64_t)(oB + 32 * (int64_t)GW);
+  st.j = 1;
+  st.n = n;
+  return true;
+}
 
-  // plane window: bit S = oA + j + dlo - 1 + 32*GW of every plane is row j + dlo
-  uint64_t S = (uint64_t)(oA + dlo + 32 * (int64_t)GW);  // for j = 1
-  uint64_t wbase = S >> 5;
-  uint32_t sh = (uint32_t)(S & 31);
-  const int bits = (int)a.bits;
-  uint32_t pw[kMaxBits][W + 1];
+constexpr int kChunk = 16;   // columns between two early-exit checks
+
+// Advances up to kChunk columns; returns true when the pair is decided.
+template <int W, int P>
+__device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs& a, uint64_t PW, uint32_t* res) {
+  // B's symbol bits for columns j .. j+kChunk-1
+  {
+    const uint64_t wb = st.bpos >> 5;
+    const uint32_t sb = (uint32_t)(st.bpos & 31);
 #pragma unroll
-  for (int p = 0; p < kMaxBits; ++p) {
-#pragma unroll
-    for (int w = 0; w <= W; ++w) pw[p][w] = p < bits ? __ldg(a.planes + (uint64_t)p * PW + wbase + w) : 0u;
+    for (int p = 0; p < P; ++p) {
+      if (p < (int)a.bits) {
+        const uint32_t lo = __ldg(a.planes + (uint64_t)p * PW + wb);
+        const uint32_t hi = __ldg(a.planes + (uint64_t)p * PW + wb + 1);
+        st.bw[p] = __funnelshift_r(lo, hi, sb);
+      } else {
+        st.bw[p] = 0;
+      }
+    }
   }
-  const uint8_t* B = a.bytes + oB;
-  uint32_t result = 0;
-  bool rejected = false;
-  for (int64_t j = 1; j <= n; ++j) {
+  const int64_t jend = st.j + (kChunk - 1) < st.n ? st.j + (kChunk - 1) : st.n;
+  const int64_t j0 = st.j;
+#pragma unroll 1
+  for (int64_t j = j0; j <= jend; ++j) {
     if (j > 1) {
-      sh = (sh + 1) & 31;
-      if (sh == 0) {
-        ++wbase;
+      st.sh = (st.sh + 1) & 31;
+      if (st.sh == 0) {
+        ++st.wbase;
 #pragma unroll
-        for (int p = 0; p < kMaxBits; ++p) {
+        for (int p = 0; p < P; ++p) {
 #pragma unroll
-          for (int w = 0; w < W; ++w) pw[p][w] = pw[p][w + 1];
-          pw[p][W] = p < bits ? __ldg(a.planes + (uint64_t)p * PW + wbase + W) : 0u;
+          for (int w = 0; w < W; ++w) st.pw[p][w] = st.pw[p][w + 1];
+          st.pw[p][W] = p < (int)a.bits ? __ldg(a.planes + (uint64_t)p * PW + st.wbase + W) : 0u;
         }
       }
     }
-    // equality bits of column j
-    const uint32_t c = s_rank[__ldg(B + j - 1)];
+    // equality bits of column j: XNOR of A's plane bits with B[j-1]'s code
+    const uint32_t c = (uint32_t)(j - j0);
     uint32_t EqF[W + 1];
 #pragma unroll
     for (int w = 0; w <= W; ++w) EqF[w] = 0xffffffffu;
 #pragma unroll
-    for (int p = 0; p < kMaxBits; ++p) {
-      if (p < bits) {
-        const uint32_t cm = ((c >> p) & 1u) ? 0u : 0xffffffffu;
+    for (int p = 0; p < P; ++p) {
+      if (p < (int)a.bits) {
+        const uint32_t cm = ((st.bw[p] >> c) & 1u) - 1u;   // 0 if B's bit is 1, all ones if 0
 #pragma unroll
-        for (int w = 0; w <= W; ++w) EqF[w] &= pw[p][w] ^ cm;
+        for (int w = 0; w <= W; ++w) EqF[w] &= st.pw[p][w] ^ cm;
       }
     }
     uint32_t Eq[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) Eq[w] = __funnelshift_r(EqF[w], EqF[w + 1], sh);
+    for (int w = 0; w < W; ++w) Eq[w] = __funnelshift_r(EqF[w], EqF[w + 1], st.sh);
 
-    // band slides down one row: new bottom row gets a +1 vertical delta
+    // band slides down one row: the new bottom row gets a +1 vertical delta
 #pragma unroll
     for (int w = 0; w < W - 1; ++w) {
-      Pv[w] = __funnelshift_r(Pv[w], Pv[w + 1], 1);
-      Mv[w] = __funnelshift_r(Mv[w], Mv[w + 1], 1);
+      st.Pv[w] = __funnelshift_r(st.Pv[w], st.Pv[w + 1], 1);
+      st.Mv[w] = __funnelshift_r(st.Mv[w], st.Mv[w + 1], 1);
     }
-    Pv[W - 1] = (Pv[W - 1] >> 1) | 0x80000000u;
-    Mv[W - 1] = Mv[W - 1] >> 1;
-    const int sv = (int)(Pv[0] & 1u) - (int)(Mv[0] & 1u);
+    st.Pv[W - 1] = (st.Pv[W - 1] >> 1) | 0x80000000u;
+    st.Mv[W - 1] = st.Mv[W - 1] >> 1;
+    const int32_t sv = (int32_t)(st.Pv[0] & 1u) - (int32_t)(st.Mv[0] & 1u);
 
     uint32_t Xv[W], Ph[W], Mh[W];
     uint32_t carry = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-      Xv[w] = Eq[w] | Mv[w];
-      const uint64_t sum = (uint64_t)(Eq[w] & Pv[w]) + Pv[w] + carry;
+      Xv[w] = Eq[w] | st.Mv[w];
+      const uint64_t sum = (uint64_t)(Eq[w] & st.Pv[w]) + st.Pv[w] + carry;
       carry = (uint32_t)(sum >> 32);
-      const uint32_t Xh = ((uint32_t)sum ^ Pv[w]) | Eq[w];
-      Ph[w] = Mv[w] | ~(Xh | Pv[w]);
-      Mh[w] = Pv[w] & Xh;
+      const uint32_t Xh = ((uint32_t)sum ^ st.Pv[w]) | Eq[w];
+      Ph[w] = st.Mv[w] | ~(Xh | st.Pv[w]);
+      Mh[w] = st.Pv[w] & Xh;
     }
-    score += sv + (int)(Ph[0] & 1u) - (int)(Mh[0] & 1u);
+    st.score += sv + (int32_t)(Ph[0] & 1u) - (int32_t)(Mh[0] & 1u);
 #pragma unroll
     for (int w = W - 1; w > 0; --w) {
       Ph[w] = __funnelshift_l(Ph[w - 1], Ph[w], 1);
@@ -184,58 +255,112 @@ __device__ uint32_t verify_pair(const VerifyArgs& a, const uint8_t* s_rank, uint
     Mh[0] = Mh[0] << 1;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-      Pv[w] = Mh[w] | ~(Xv[w] | Ph[w]);
-      Mv[w] = Ph[w] & Xv[w];
-    }
-    if ((j & 31) == 0 || j == n) {
-      int64_t diag = score;
-#pragma unroll
-      for (int w = 0; w < W; ++w) diag += (int)__popc(Pv[w] & M1[w]) - (int)__popc(Mv[w] & M1[w]);
-      if (diag > (int64_t)k) {
-        rejected = true;
-        break;
-      }
-      if (j == n) result = (uint32_t)diag;
+      st.Pv[w] = Mh[w] | ~(Xv[w] | Ph[w]);
+      st.Mv[w] = Ph[w] & Xv[w];
     }
   }
-  return rejected ? k + 1 : result;
+  st.j = jend + 1;
+  st.bpos += kChunk;
+  // D on diagonal d0 at column jend: a lower bound of D[m][n] (exact at n)
+  int32_t diag = st.score;
+#pragma unroll
+  for (int w = 0; w < W; ++w) diag += (int32_t)__popc(st.Pv[w] & st.M1[w]) - (int32_t)__popc(st.Mv[w] & st.M1[w]);
+  if (diag > (int32_t)st.k) {
+    *res = st.k + 1;
+    return true;
+  }
+  if (jend == st.n) {
+    *res = (uint32_t)diag;
+    return true;
+  }
+  return false;
 }
 
-template <int W>
-__global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, RankTable rt, uint64_t PW, uint32_t GW) {
-  __shared__ uint8_t s_rank[256];
-  for (int t = threadIdx.x; t < 256; t += blockDim.x) s_rank[t] = rt.r[t];
-  __syncthreads();
-  uint64_t cells = 0;
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.m; t += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t x = a.pi[t], y = a.pj[t];
-    const uint32_t k = a.pk ? a.pk[t] : a.K;
-    if (x >= a.n_strings || y >= a.n_strings) {
-      atomicOr(a.dev_flags, FLAG_BOUNDS);
-      a.ed[t] = k + 1;
-      continue;
+// Persistent verifier: every lane keeps one pair in flight and fetches the
+// next pair index (warp-aggregated atomic on *next) as soon as its pair is
+// decided, so early exits do not leave lanes idle behind slow pairs.
+template <int W, int P>
+__global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t PW, uint32_t GW,
+                                                          unsigned long long* __restrict__ next) {
+  const int lane = threadIdx.x & 31;
+  PairState<W, P> st;
+  bool active = false;
+  bool more = true;
+  uint64_t cells = 0, work = 0;
+  while (true) {
+    // lanes without a pair fetch the next indices
+    const bool need = !active && more;
+    const uint32_t nmask = __ballot_sync(0xffffffffu, need);
+    if (nmask) {
+      unsigned long long base = 0;
+      const int leader = __ffs(nmask) - 1;
+      if (lane == leader) base = atomicAdd(next, (unsigned long long)__popc(nmask));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (need) {
+        const uint64_t q = base + __popc(nmask & ((1u << lane) - 1u));
+        if (q >= a.m) {
+          more = false;
+        } else {
+          const uint64_t t = a.order ? a.order[q] : q;
+          uint32_t res;
+          if (a.cells) {
+            const uint32_t x = a.pi[t], y = a.pj[t];
+            if (x < a.n_strings && y < a.n_strings) {
+              const int64_t lx = __ldg(a.offsets + x + 1) - __ldg(a.offsets + x);
+              const int64_t ly = __ldg(a.offsets + y + 1) - __ldg(a.offsets + y);
+              cells += band_cells(lx > ly ? lx : ly, lx > ly ? ly : lx, a.K);
+            }
+          }
+          if (pair_init<W, P>(st, a, PW, GW, t, &res)) {
+            active = true;
+          } else {
+            a.ed[t] = res;
+          }
+        }
+      }
     }
-    a.ed[t] = verify_pair<W>(a, s_rank, PW, GW, x, y, k);
-    if (a.cells) {
-      const int64_t lx = __ldg(a.offsets + x + 1) - __ldg(a.offsets + x);
-      const int64_t ly = __ldg(a.offsets + y + 1) - __ldg(a.offsets + y);
-      cells += band_cells(lx > ly ? lx : ly, lx > ly ? ly : lx, a.K);
+    if (!__any_sync(0xffffffffu, active || more)) break;
+    if (active) {
+      uint32_t res;
+      const int64_t j_before = st.j;
+      const bool done = pair_chunk<W, P>(st, a, PW, &res);
+      work += (uint64_t)(st.j - j_before) * W;
+      if (done) {
+        a.ed[st.t] = res;
+        active = false;
+      }
     }
   }
   if (a.cells) {
     for (int o = 16; o > 0; o >>= 1) cells += __shfl_down_sync(0xffffffffu, cells, o);
-    if ((threadIdx.x & 31) == 0 && cells) atomicAdd(a.cells, (unsigned long long)cells);
+    if (lane == 0 && cells) atomicAdd(a.cells, (unsigned long long)cells);
+  }
+  if (a.work) {
+    for (int o = 16; o > 0; o >>= 1) work += __shfl_down_sync(0xffffffffu, work, o);
+    if (lane == 0 && work) atomicAdd(a.work, (unsigned long long)work);
   }
 }
 
-template <int W>
-int launch_w(const VerifyArgs& a, const RankTable& rt, uint64_t PW, uint32_t GW, cudaStream_t s) {
-  uint64_t blocks = (a.m + 127) / 128;
-  uint64_t cap = (uint64_t)kNumSMsHint * 16;
-  unsigned grid = (unsigned)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
-  verify_diag_kernel<W><<<grid, 128, 0, s>>>(a, rt, PW, GW);
+template <int W, int P>
+int launch_wp(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long* next, cudaStream_t s) {
+  int dev = 0, sms = kNumSMsHint, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, verify_diag_kernel<W, P>, 128, 0);
+  if (per_sm < 1) per_sm = 1;
+  uint64_t need = (a.m + 127) / 128;
+  uint64_t grid = (uint64_t)sms * per_sm;
+  if (need < grid) grid = need;
+  verify_diag_kernel<W, P><<<(unsigned)(grid ? grid : 1), 128, 0, s>>>(a, PW, GW, next);
   MJ_KERNEL_DONE();
   return MJ_OK;
+}
+
+template <int W>
+int launch_w(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long* next, cudaStream_t s) {
+  if (a.bits <= 2) return launch_wp<W, 2>(a, PW, GW, next, s);
+  if (a.bits <= 5) return launch_wp<W, 5>(a, PW, GW, next, s);
+  return launch_wp<W, 8>(a, PW, GW, next, s);
 }
 
 }  // namespace
@@ -256,22 +381,24 @@ int verify_words_for(uint32_t kmax) {
   return (int)((kmax + 1 + 31) / 32);
 }
 
-int launch_verify(const VerifyArgs& a, const RankTable& rt, uint64_t PW, uint32_t GW, uint32_t kmax, cudaStream_t s) {
+int launch_verify(const VerifyArgs& a, uint64_t PW, uint32_t GW, uint32_t kmax, unsigned long long* next,
+                  cudaStream_t s) {
   if (a.m == 0) return MJ_OK;
-  int W = verify_words_for(kmax);
+  MJ_CUDA_TRY(cudaMemsetAsync(next, 0, sizeof(unsigned long long), s));
+  const int W = verify_words_for(kmax);
   switch (W) {
-    case 1: return launch_w<1>(a, rt, PW, GW, s);
-    case 2: return launch_w<2>(a, rt, PW, GW, s);
-    case 3: return launch_w<3>(a, rt, PW, GW, s);
-    case 4: return launch_w<4>(a, rt, PW, GW, s);
-    case 5: return launch_w<5>(a, rt, PW, GW, s);
-    case 6: return launch_w<6>(a, rt, PW, GW, s);
-    case 7: return launch_w<7>(a, rt, PW, GW, s);
-    case 8: return launch_w<8>(a, rt, PW, GW, s);
+    case 1: return launch_w<1>(a, PW, GW, next, s);
+    case 2: return launch_w<2>(a, PW, GW, next, s);
+    case 3: return launch_w<3>(a, PW, GW, next, s);
+    case 4: return launch_w<4>(a, PW, GW, next, s);
+    case 5: return launch_w<5>(a, PW, GW, next, s);
+    case 6: return launch_w<6>(a, PW, GW, next, s);
+    case 7: return launch_w<7>(a, PW, GW, next, s);
+    case 8: return launch_w<8>(a, PW, GW, next, s);
     default: break;
   }
-  if (W <= 16) return launch_w<16>(a, rt, PW, GW, s);
-  if (W <= 32) return launch_w<32>(a, rt, PW, GW, s);
+  if (W <= 16) return launch_wp<16, 8>(a, PW, GW, next, s);
+  if (W <= 32) return launch_wp<32, 8>(a, PW, GW, next, s);
   return MJ_ERR_UNSUPPORTED;
 }
 
