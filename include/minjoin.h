@@ -143,6 +143,33 @@ int mj_verify(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_offsets, uin
               const uint32_t* d_i, const uint32_t* d_j, const uint32_t* d_k, uint64_t m, uint32_t K,
               void* stream, uint32_t* d_ed);
 
+/* mj_verify for callers that cannot allocate device memory.  No counterpart
+ * in the paper: it exists for code that may not call cudaMalloc, such as a
+ * plug-in whose host application owns all device memory through its own
+ * pool, a latency-critical path that must avoid the synchronisation an
+ * allocation can imply, or a deployment with a device-memory budget fixed at
+ * start-up.  It allocates nothing: its scratch (equality bit-planes of the
+ * input and a work counter) is one file-scope __device__ array of
+ * MJ_VERIFY_STATIC_SCRATCH_BYTES that every GPU loading the library keeps
+ * until the process exits.  No context is needed.
+ *  - Arguments as for mj_verify without d_k (one band K for all pairs); the
+ *    caller passes the inputs and the output array d_ed.
+ *  - Limits: the input may hold at most about MJ_VERIFY_STATIC_SCRATCH_BYTES
+ *    bytes (one byte of scratch per input byte, plus guard words) and K at
+ *    most MJ_VERIFY_STATIC_MAX_K; larger inputs or bands return
+ *    MJ_ERR_UNSUPPORTED without running anything.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.  The call synchronises `stream` once to read
+ *    the input size, then queues the work and returns.
+ *  - All calls share the one array: calls that overlap on the GPU (other
+ *    streams, other threads) race and give wrong results; serialise them.
+ *    Every call clears what must start at zero. */
+#define MJ_VERIFY_STATIC_SCRATCH_BYTES (16u << 20)
+#define MJ_VERIFY_STATIC_MAX_K 255u
+int mj_verify_static(const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const uint32_t* d_i,
+                     const uint32_t* d_j, uint64_t m, uint32_t K, void* stream, uint32_t* d_ed);
+
 /* The whole path (Alg. 3): *count receives the number of output pairs;
  * mj_result_copy writes them sorted by (i, j) with their edit distances.
  * In MJ_VERIFY_LEARNED mode a band model must have been trained or loaded. */

@@ -76,6 +76,7 @@ _SIGS = {
     "mj_candidates": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, VP, ctypes.POINTER(U64)]),
     "mj_candidates_copy": (ctypes.c_int, [VP, VP, VP, VP]),
     "mj_verify": (ctypes.c_int, [VP, VP, VP, U32, VP, VP, VP, U64, U32, VP, VP]),
+    "mj_verify_static": (ctypes.c_int, [VP, VP, U32, VP, VP, U64, U32, VP, VP]),
     "mj_join": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, ctypes.POINTER(U64)]),
     "mj_result_copy": (ctypes.c_int, [VP, VP, VP, VP, VP]),
     "mj_join_host": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, ctypes.POINTER(U64)]),
