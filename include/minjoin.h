@@ -46,7 +46,21 @@ extern "C" {
 #define MJ_VERIFY_PLAIN 0        /* one pass with band K */
 #define MJ_VERIFY_LEARNED 1      /* learned first-pass band k' < K, fallback to K */
 
+/* verification kernels (mj_verify_config.kernel) */
+#define MJ_VERIFY_KERNEL_AUTO 0       /* diagonal for K <= 255, wavefront above */
+#define MJ_VERIFY_KERNEL_DIAGONAL 1   /* one thread per pair, band as ceil((K+1)/32) words */
+#define MJ_VERIFY_KERNEL_WAVEFRONT 2  /* G lanes per pair, 32-row blocks, skewed wavefront */
+
 typedef struct mj_ctx mj_ctx;
+
+/* Choice of verification kernel for a context (used by mj_verify and mj_join).
+ *  kernel  MJ_VERIFY_KERNEL_*.
+ *  lanes   wavefront only: lanes per pair (2, 4, 8, 16 or 32); 0 = the fewest
+ *          that hold the band.  Too few lanes for a band is MJ_ERR_UNSUPPORTED. */
+typedef struct {
+  uint32_t kernel;
+  uint32_t lanes;
+} mj_verify_config;
 
 /* Parameters of one join.
  *  K       edit-distance threshold (Sec. 1).
@@ -112,6 +126,8 @@ const char* mj_strerror(int status);
 int mj_create(mj_ctx** ctx, int device);
 void mj_destroy(mj_ctx* ctx);
 int mj_get_stats(const mj_ctx* ctx, mj_stats* out);
+/* Sets the verification kernel of the context (default: MJ_VERIFY_KERNEL_AUTO). */
+int mj_set_verify_config(mj_ctx* ctx, const mj_verify_config* cfg);
 
 /* Step a1 (Sec. 2.2, Alg. 2 line 2): Sigma, rank codes, N, q, T, r_max. */
 int mj_derive(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n,

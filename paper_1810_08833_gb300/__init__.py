@@ -45,6 +45,15 @@ class Derived(ctypes.Structure):
                 ("N", ctypes.c_uint64), ("rank", ctypes.c_uint8 * 256)]
 
 
+class VerifyConfig(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_uint32), ("lanes", ctypes.c_uint32)]
+
+
+MJ_VERIFY_KERNEL_AUTO = 0
+MJ_VERIFY_KERNEL_DIAGONAL = 1
+MJ_VERIFY_KERNEL_WAVEFRONT = 2
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("n_strings", ctypes.c_uint64), ("n_bytes", ctypes.c_uint64), ("n_partitions", ctypes.c_uint64),
                 ("n_raw_pairs", ctypes.c_uint64), ("n_candidates", ctypes.c_uint64),
@@ -70,6 +79,7 @@ _SIGS = {
     "mj_create": (ctypes.c_int, [ctypes.POINTER(VP), ctypes.c_int]),
     "mj_destroy": (None, [VP]),
     "mj_get_stats": (ctypes.c_int, [VP, ctypes.POINTER(Stats)]),
+    "mj_set_verify_config": (ctypes.c_int, [VP, ctypes.POINTER(VerifyConfig)]),
     "mj_derive": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, ctypes.POINTER(Derived)]),
     "mj_partition": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, VP, ctypes.POINTER(U64)]),
     "mj_partition_copy": (ctypes.c_int, [VP, VP, VP, VP, VP, VP]),
@@ -176,6 +186,10 @@ class Context:
         out = {name: getattr(s, name) for name, _ in Stats._fields_ if name != "ms_section"}
         out["ms_section"] = dict(zip(SECTIONS, list(s.ms_section)))
         return out
+
+    def set_verify_config(self, kernel: int = MJ_VERIFY_KERNEL_AUTO, lanes: int = 0):
+        cfg = VerifyConfig(kernel, lanes)
+        _check(self._lib.mj_set_verify_config(self._h, ctypes.byref(cfg)), "mj_set_verify_config")
 
     def derive(self, data, offsets, p: Params, stream=None) -> dict:
         n = _check_inputs(data, offsets)

@@ -111,6 +111,7 @@ struct mj_ctx {
   Buf in_bytes, in_offsets;  // staging for mj_join_host
   uint64_t n_part = 0, n_cand = 0, n_out = 0;
   // bit-planes written by the partition kernel for the verifier
+  mj_verify_config vcfg{MJ_VERIFY_KERNEL_AUTO, 0};
   bool planes_ready = false;
   uint64_t planes_pw = 0;
   uint32_t planes_gw = 0;
@@ -434,7 +435,8 @@ int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const ui
   a.work = c->small.as<unsigned long long>() + 2;
   a.dev_flags = c->dev_flags.as<uint32_t>();
   tstart(c, 6, s);
-  MJ_TRY(launch_verify(a, PW, GW, kmax, c->small.as<unsigned long long>() + 1, s));
+  MJ_TRY(launch_verify(a, PW, GW, kmax, c->small.as<unsigned long long>() + 1, s, (int)c->vcfg.kernel,
+                       (int)c->vcfg.lanes));
   tstop(c, 6, s);
   return MJ_OK;
 }
@@ -521,6 +523,14 @@ void mj_destroy(mj_ctx* c) {
     if (e) cudaEventDestroy(e);
   if (c->h_small) cudaFreeHost(c->h_small);
   delete c;
+}
+
+int mj_set_verify_config(mj_ctx* c, const mj_verify_config* cfg) {
+  if (!c || !cfg) return MJ_ERR_ARG;
+  if (cfg->kernel > MJ_VERIFY_KERNEL_WAVEFRONT) return MJ_ERR_ARG;
+  if (cfg->lanes && (cfg->lanes > 32 || (cfg->lanes & (cfg->lanes - 1)) || cfg->lanes < 2)) return MJ_ERR_ARG;
+  c->vcfg = *cfg;
+  return MJ_OK;
 }
 
 int mj_get_stats(const mj_ctx* c, mj_stats* out) {

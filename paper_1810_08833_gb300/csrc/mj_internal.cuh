@@ -173,8 +173,10 @@ inline uint32_t plane_guard_words(uint32_t kmax) { return kmax / 64 + (uint32_t)
 int launch_build_planes(const uint8_t* bytes, uint64_t nbytes, const RankTable& rt, uint32_t bits,
                         uint32_t* planes, uint64_t plane_words, uint32_t guard_words, cudaStream_t s);
 // `next` is a device counter the persistent kernel hands pairs out from.
+// kernel: MJ_VERIFY_KERNEL_*; lanes: wavefront lanes per pair (0 = fewest that fit).
 int launch_verify(const VerifyArgs& a, uint64_t plane_words, uint32_t guard_words, uint32_t kmax,
-                  unsigned long long* next, cudaStream_t s);
+                  unsigned long long* next, cudaStream_t s, int kernel = MJ_VERIFY_KERNEL_AUTO, int lanes = 0);
+int wave_lanes_for(uint32_t kmax);
 
 // verification order: candidate indices sorted by key = N - min length
 int launch_work_keys(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m, uint64_t N,

@@ -341,6 +341,234 @@ __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t
   }
 }
 
+// ---------------------------------------------------------------- wide bands
+// Row-fixed blocks with a skewed wavefront, G lanes per pair.
+//
+// Rows are cut into 32-row blocks (block b = rows 32b+1 .. 32b+32, one 32-bit
+// word per vector); lane b mod G of the pair's group owns block b.  Block b
+// advances column j at step s = j + b: it needs the horizontal delta of the
+// row just above it in column j, which the lane owning block b-1 produced one
+// step earlier and passes on by a shuffle.  A block works on the columns in
+// which some of its rows lie in the band [j + dlo, j + dhi]; outside, a block
+// entering the band starts from vertical deltas of +1 and the row above a
+// retired block gets a horizontal delta of +1 (the same over-estimates as the
+// diagonal kernel).  With an incoming horizontal delta hin in {-1, 0, +1}, a
+// block step is the recurrence of the diagonal kernel with the top row's
+// chain seeded by hin: Xh's carry chain starts set when hin = -1, and the
+// shifted-in top bit of Ph (Mh) is set when hin = +1 (-1).  Each block keeps
+// D of its bottom row; the bottom row of the block holding row m at column n
+// gives D[m][n], and the block holding row j + d0 at column j gives the
+// diagonal lower bound used for the early exit.
+constexpr int kWaveCheck = 8;   // steps between early-exit votes
+
+template <int G, int P>
+__global__ void __launch_bounds__(128) verify_wave_kernel(VerifyArgs a, uint64_t PW, uint32_t GW,
+                                                          unsigned long long* __restrict__ next) {
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (G - 1);
+  const int gbase = lane - gl;
+  const uint32_t gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
+  const int prev_lane = gbase + ((gl + G - 1) & (G - 1));
+  // pair state (identical in the G lanes of a group)
+  bool has = false, more = true;
+  uint64_t t = 0;
+  uint32_t k = 0;
+  int64_t oA = 0, oB = 0, m = 0, n = 0, d0 = 0, s = 0, s_end = 0;
+  int32_t dlo = 0, dhi = 0, bm = 0;
+  // block state (this lane)
+  int32_t b = 0;
+  uint32_t Pv = 0, Mv = 0;
+  uint32_t pa[P], bw[P];
+  int64_t bw_col = 0;
+  int32_t score = 0;
+  // what this lane produced at the previous step: tag = block << 2 | (hout + 1)
+  int32_t pub_tag = -1, pub_score = 0;
+  uint64_t work = 0, cells = 0;
+
+  while (true) {
+    // ---- groups without a pair take the next one
+    const bool need = !has && more;
+    const uint32_t leaders = __ballot_sync(0xffffffffu, need && gl == 0);
+    unsigned long long base = 0;
+    if (leaders) {
+      const int first = __ffs(leaders) - 1;
+      if (lane == first) base = atomicAdd(next, (unsigned long long)__popc(leaders));
+      base = __shfl_sync(0xffffffffu, base, first);
+    }
+    const uint64_t q = base + __popc(leaders & ((1u << gbase) - 1u));
+    if (need) {
+      if (q >= a.m) {
+        more = false;
+      } else {
+        t = a.order ? a.order[q] : q;
+        const uint32_t x = a.pi[t], y = a.pj[t];
+        k = a.pk ? a.pk[t] : a.K;
+        uint32_t res = 0xffffffffu;
+        if (x >= a.n_strings || y >= a.n_strings) {
+          if (gl == 0) atomicOr(a.dev_flags, FLAG_BOUNDS);
+          res = k + 1;
+        } else {
+          const int64_t ox = __ldg(a.offsets + x), lx = __ldg(a.offsets + x + 1) - ox;
+          const int64_t oy = __ldg(a.offsets + y), ly = __ldg(a.offsets + y + 1) - oy;
+          const bool xa = lx >= ly;
+          if (a.cells && gl == 0) cells += band_cells(xa ? lx : ly, xa ? ly : lx, a.K);
+          oA = xa ? ox : oy;
+          m = xa ? lx : ly;
+          oB = xa ? oy : ox;
+          n = xa ? ly : lx;
+          d0 = m - n;
+          if (d0 > (int64_t)k) {
+            res = k + 1;
+          } else if (n == 0) {
+            res = (uint32_t)d0;
+          } else {
+            dlo = -(int32_t)(((int64_t)k - d0) >> 1);
+            dhi = (int32_t)d0 + (int32_t)(((int64_t)k - d0) >> 1);
+            if (dhi - dlo < 63) dlo = dhi - 63;        // at least 64 band rows (any wider band is exact)
+            bm = (int32_t)((m - 1) >> 5);
+            s = 0;
+            s_end = n + bm;
+            b = gl;
+            pub_tag = -1;
+          }
+        }
+        if (res != 0xffffffffu) {
+          if (gl == 0) a.ed[t] = res;
+        } else {
+          has = true;
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, has || more)) break;
+
+    // ---- one wavefront step for groups holding a pair
+    const int32_t in_tag = __shfl_sync(0xffffffffu, pub_tag, prev_lane);
+    const int32_t in_score = __shfl_sync(0xffffffffu, pub_score, prev_lane);
+    bool done = false, reject = false;
+    int32_t result = 0;
+    pub_tag = -1;
+    if (has) {
+      ++s;
+      const int64_t j = s - b;
+      const int64_t jf = (32 * (int64_t)b + 1 - dhi) > 1 ? (32 * (int64_t)b + 1 - dhi) : 1;
+      const int64_t jl = (32 * (int64_t)b + 32 - dlo) < n ? (32 * (int64_t)b + 32 - dlo) : n;
+      if (b <= bm && j >= jf && j <= jl) {
+        const bool first_col = (j == jf);
+        if (first_col) {
+          Pv = 0xffffffffu;
+          Mv = 0u;
+          const uint64_t pos = (uint64_t)(oA + 32 * (int64_t)b + 32 * (int64_t)GW);
+#pragma unroll
+          for (int p = 0; p < P; ++p) {
+            const uint32_t lo = p < (int)a.bits ? __ldg(a.planes + (uint64_t)p * PW + (pos >> 5)) : 0u;
+            const uint32_t hi = p < (int)a.bits ? __ldg(a.planes + (uint64_t)p * PW + (pos >> 5) + 1) : 0u;
+            pa[p] = __funnelshift_r(lo, hi, (uint32_t)(pos & 31));
+          }
+        }
+        if (first_col || j - bw_col >= 32) {
+          bw_col = j;
+          const uint64_t pos = (uint64_t)(oB + j - 1 + 32 * (int64_t)GW);
+#pragma unroll
+          for (int p = 0; p < P; ++p) {
+            const uint32_t lo = p < (int)a.bits ? __ldg(a.planes + (uint64_t)p * PW + (pos >> 5)) : 0u;
+            const uint32_t hi = p < (int)a.bits ? __ldg(a.planes + (uint64_t)p * PW + (pos >> 5) + 1) : 0u;
+            bw[p] = __funnelshift_r(lo, hi, (uint32_t)(pos & 31));
+          }
+        }
+        const uint32_t c = (uint32_t)(j - bw_col);
+        uint32_t Eq = 0xffffffffu;
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+          if (p < (int)a.bits) Eq &= pa[p] ^ (((bw[p] >> c) & 1u) - 1u);
+        // horizontal delta entering the block's top row in column j
+        const bool from_prev = b > 0 && in_tag >= 0 && (in_tag >> 2) == b - 1;
+        const int hin = from_prev ? ((in_tag & 3) - 1) : 1;
+        const uint32_t hneg = hin < 0 ? 1u : 0u;
+        const uint32_t Xv = Eq | Mv;
+        const uint32_t Eh = Eq | hneg;
+        const uint32_t Xh = (((Eh & Pv) + Pv) ^ Pv) | Eh;
+        uint32_t Ph = Mv | ~(Xh | Pv);
+        uint32_t Mh = Pv & Xh;
+        const int hout = (int)(Ph >> 31) - (int)(Mh >> 31);
+        Ph = (Ph << 1) | (hin > 0 ? 1u : 0u);
+        Mh = (Mh << 1) | hneg;
+        Pv = Mh | ~(Xv | Ph);
+        Mv = Ph & Xv;
+        if (first_col) {
+          // D of the row above the block in column j, plus the block's deltas
+          const int32_t above = (b == 0) ? (int32_t)j : in_score;
+          score = above + (int32_t)__popc(Pv) - (int32_t)__popc(Mv);
+        } else {
+          score += hout;
+        }
+        pub_tag = (b << 2) | (hout + 1);
+        pub_score = score;
+        work += 1;
+        // D at row r of this block = score minus the deltas of the rows below r
+        if (b == bm && j == n) {
+          const int tm = (int)((m - 1) & 31);
+          const uint32_t below = tm == 31 ? 0u : (0xffffffffu << (tm + 1));
+          result = score - (int32_t)__popc(Pv & below) + (int32_t)__popc(Mv & below);
+          done = true;
+        } else if ((s & (kWaveCheck - 1)) == 0) {
+          const int64_t rd = j + d0;   // row of diagonal d0 in column j
+          if (rd >= 32 * (int64_t)b + 1 && rd <= 32 * (int64_t)b + 32) {
+            const int tr = (int)((rd - 1) & 31);
+            const uint32_t below = tr == 31 ? 0u : (0xffffffffu << (tr + 1));
+            const int32_t diag = score - (int32_t)__popc(Pv & below) + (int32_t)__popc(Mv & below);
+            if (diag > (int32_t)k) reject = true;
+          }
+        }
+        if (j == jl) b += G;   // this block left the band: take the next one of this lane
+      }
+    }
+    const uint32_t dmask = __ballot_sync(0xffffffffu, done) & gmask;
+    const uint32_t rmask = __ballot_sync(0xffffffffu, reject) & gmask;
+    const int src = dmask ? __ffs(dmask) - 1 : lane;
+    const int32_t fin = __shfl_sync(0xffffffffu, result, src);
+    if (has && (dmask || rmask)) {
+      if (gl == 0) a.ed[t] = rmask ? k + 1 : (fin > (int32_t)k ? k + 1 : (uint32_t)fin);
+      has = false;
+    } else if (has && s >= s_end) {   // cannot happen: the last block ends at step s_end
+      if (gl == 0) {
+        atomicOr(a.dev_flags, FLAG_BOUNDS);
+        a.ed[t] = k + 1;
+      }
+      has = false;
+    }
+  }
+  if (a.work) {
+    for (int o = 16; o > 0; o >>= 1) work += __shfl_down_sync(0xffffffffu, work, o);
+    if (lane == 0 && work) atomicAdd(a.work, (unsigned long long)work);
+  }
+  if (a.cells) {
+    for (int o = 16; o > 0; o >>= 1) cells += __shfl_down_sync(0xffffffffu, cells, o);
+    if (lane == 0 && cells) atomicAdd(a.cells, (unsigned long long)cells);
+  }
+}
+
+template <int G, int P>
+int launch_gp(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long* next, cudaStream_t s) {
+  int dev = 0, sms = kNumSMsHint, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, verify_wave_kernel<G, P>, 128, 0);
+  if (per_sm < 1) per_sm = 1;
+  uint64_t need = (a.m * G + 127) / 128;
+  uint64_t grid = (uint64_t)sms * per_sm;
+  if (need < grid) grid = need;
+  verify_wave_kernel<G, P><<<(unsigned)(grid ? grid : 1), 128, 0, s>>>(a, PW, GW, next);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
+template <int G>
+int launch_g(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long* next, cudaStream_t s) {
+  if (a.bits <= 2) return launch_gp<G, 2>(a, PW, GW, next, s);
+  if (a.bits <= 5) return launch_gp<G, 5>(a, PW, GW, next, s);
+  return launch_gp<G, 8>(a, PW, GW, next, s);
+}
+
 template <int W, int P>
 int launch_wp(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long* next, cudaStream_t s) {
   int dev = 0, sms = kNumSMsHint, per_sm = 1;
@@ -381,11 +609,35 @@ int verify_words_for(uint32_t kmax) {
   return (int)((kmax + 1 + 31) / 32);
 }
 
+int wave_lanes_for(uint32_t kmax) {
+  // blocks of one pair active at one step: floor((w + 30) / 33) + 1, w <= kmax + 1 (>= 64)
+  uint32_t w = kmax + 1 < 64 ? 64 : kmax + 1;
+  uint32_t cnt = (w + 30) / 33 + 1;
+  uint32_t g = 2;
+  while (g < cnt) g <<= 1;
+  return (int)g;
+}
+
 int launch_verify(const VerifyArgs& a, uint64_t PW, uint32_t GW, uint32_t kmax, unsigned long long* next,
-                  cudaStream_t s) {
+                  cudaStream_t s, int kernel, int lanes) {
   if (a.m == 0) return MJ_OK;
   MJ_CUDA_TRY(cudaMemsetAsync(next, 0, sizeof(unsigned long long), s));
   const int W = verify_words_for(kmax);
+  if (kernel == MJ_VERIFY_KERNEL_AUTO) kernel = W <= 8 ? MJ_VERIFY_KERNEL_DIAGONAL : MJ_VERIFY_KERNEL_WAVEFRONT;
+  if (kernel == MJ_VERIFY_KERNEL_WAVEFRONT) {
+    const int need = wave_lanes_for(kmax);
+    int G = lanes > 0 ? lanes : need;
+    if (G < need || G > 32 || (G & (G - 1))) return MJ_ERR_UNSUPPORTED;
+    switch (G) {
+      case 2: return launch_g<2>(a, PW, GW, next, s);
+      case 4: return launch_g<4>(a, PW, GW, next, s);
+      case 8: return launch_g<8>(a, PW, GW, next, s);
+      case 16: return launch_g<16>(a, PW, GW, next, s);
+      case 32: return launch_g<32>(a, PW, GW, next, s);
+      default: return MJ_ERR_UNSUPPORTED;
+    }
+  }
+  if (kernel != MJ_VERIFY_KERNEL_DIAGONAL) return MJ_ERR_ARG;
   switch (W) {
     case 1: return launch_w<1>(a, PW, GW, next, s);
     case 2: return launch_w<2>(a, PW, GW, next, s);

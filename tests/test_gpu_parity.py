@@ -290,3 +290,55 @@ def test_verify_rejects_bad_ids(ctx):
     ed = ctx.verify(data, off, i, j, 2)
     torch.cuda.synchronize()
     assert ed.cpu().tolist() == [1, 3]
+
+
+KERNEL_CASES = [(K, 1, 0) for K in (5, 40, 100, 255, 600)] + \
+               [(K, 2, 0) for K in (0, 1, 7, 40, 63, 64, 100, 255, 256, 600, 1000)] + \
+               [(40, 2, 8), (100, 2, 16), (100, 2, 32), (255, 2, 32)]
+
+
+@pytest.mark.parametrize("K,kernel,lanes", KERNEL_CASES,
+                         ids=[f"K{K}-{'diag' if k == 1 else 'wave'}{l or ''}" for K, k, l in KERNEL_CASES])
+def test_verify_kernel_parity(ctx, K, kernel, lanes):
+    """Each verification kernel, forced, agrees with the oracle's banded DP."""
+    import torch
+    lens = (0, 3 * K + 40) if K < 300 else (K, 3 * K)
+    count = 100 if K < 300 else 24
+    s, pairs = _pairs_set(2000 + K, K, count, lens)
+    want = oracle.ed_band_pairs(s.bytes, s.offsets, pairs, K)
+    data, off = to_device(s)
+    i = torch.from_numpy(pairs[:, 0].astype(np.int32)).cuda()
+    j = torch.from_numpy(pairs[:, 1].astype(np.int32)).cuda()
+    ctx.set_verify_config(kernel, lanes)
+    try:
+        got = ctx.verify(data, off, i, j, K).cpu().numpy().astype(np.int64)
+        got_swapped = ctx.verify(data, off, j, i, K).cpu().numpy().astype(np.int64)
+    finally:
+        ctx.set_verify_config(0, 0)
+    assert np.array_equal(got, want), np.nonzero(got != want)[0][:10]
+    assert np.array_equal(got_swapped, want)
+
+
+def test_wavefront_other_alphabets(ctx):
+    import torch
+    rng = np.random.Generator(np.random.PCG64(19))
+    for symbols in (synth.PROTEIN, synth.PRINTABLE):
+        strs, pairs = [], []
+        for t in range(60):
+            L = int(rng.integers(0, 900))
+            a = symbols[rng.integers(0, symbols.shape[0], size=L)]
+            b = synth.mutate(rng, a, float(rng.uniform(0, 0.15)), symbols)
+            strs += [a.tobytes(), b.tobytes()]
+            pairs.append((2 * t, 2 * t + 1))
+        s = synth.from_strings(strs, K=80, T=80)
+        pairs = np.array(pairs, np.int64)
+        data, off = to_device(s)
+        i = torch.from_numpy(pairs[:, 0].astype(np.int32)).cuda()
+        j = torch.from_numpy(pairs[:, 1].astype(np.int32)).cuda()
+        want = oracle.ed_band_pairs(s.bytes, s.offsets, pairs, 80)
+        ctx.set_verify_config(2, 0)
+        try:
+            got = ctx.verify(data, off, i, j, 80).cpu().numpy().astype(np.int64)
+        finally:
+            ctx.set_verify_config(0, 0)
+        assert np.array_equal(got, want)
