@@ -42,6 +42,10 @@ extern "C" {
 #define MJ_ERR_TIMEOUT (-6)      /* a bounded device-side wait ran out */
 #define MJ_ERR_STATE (-7)        /* call order (e.g. copy before compute, no trained band model) */
 
+/* mj_params.flags */
+#define MJ_FLAG_KEY_CHECK 1u     /* check byte equality of every group of equal partition keys */
+#define MJ_FLAG_FEATURES 16u     /* mj_join keeps every candidate's band features (mj_features_copy) */
+
 /* verification modes (mj_params.verify_mode) */
 #define MJ_VERIFY_PLAIN 0        /* one pass with band K */
 #define MJ_VERIFY_LEARNED 1      /* learned first-pass band k' < K, fallback to K */
@@ -72,8 +76,9 @@ typedef struct {
  *          (default 1; the literal rule gives r <= 0 for short strings).
  *  seed    seed of the random q-gram function Pi and of the partition key.
  *  verify_mode  MJ_VERIFY_PLAIN or MJ_VERIFY_LEARNED.
- *  flags   bit 0: check every group of equal partition keys for byte equality
- *          (counts mismatches in mj_stats.key_collisions). */
+ *  flags   MJ_FLAG_KEY_CHECK: check every group of equal partition keys for
+ *          byte equality (mismatches counted in mj_stats.key_collisions);
+ *          MJ_FLAG_FEATURES: keep the candidates' band features. */
 typedef struct {
   uint32_t K;
   uint32_t T;
@@ -200,6 +205,58 @@ int mj_result_copy(mj_ctx* ctx, uint32_t* d_i, uint32_t* d_j, uint32_t* d_ed, vo
 int mj_join_host(mj_ctx* ctx, const uint8_t* h_bytes, const int64_t* h_offsets, uint32_t n,
                  const mj_params* p, void* stream, uint64_t* count);
 int mj_result_copy_host(mj_ctx* ctx, uint32_t* h_i, uint32_t* h_j, uint32_t* h_ed, void* stream);
+
+/* ---- Learned first-pass band (no counterpart in the paper).
+ * A small FP32 MLP (MJ_BAND_FEATURES -> 64 -> 64 -> 1, ReLU) predicts, from
+ * features of a candidate pair, its edit distance as a fraction of K.  In
+ * MJ_VERIFY_LEARNED mode mj_join verifies each candidate first with the
+ * widest band that fits in the fewest 32-bit words holding the prediction
+ * (plus `margin`), but only when that is fewer words than band K needs and
+ * the candidate came from at least `min_multiplicity` matched partition
+ * pairs; every pair the first pass does not settle (result > its band) is
+ * verified again with band K, so the output equals the plain mode's.
+ * Features of candidate (i, j), with n the shorter length, d0 the length
+ * difference, c the matched partition pairs behind the candidate and pa, pb
+ * the partition counts of the two strings:
+ *   log2(1+n)/16, d0/K, c/(T+1), pa/(T+1), pb/(T+1), c/min(pa,pb),
+ *   log2(1+c)/8, K/(K+100).
+ * Parameters are MJ_BAND_PARAMS floats: W1[64][8], b1[64], W2[64][64],
+ * b2[64], W3[64], b3. */
+#define MJ_BAND_FEATURES 8
+#define MJ_BAND_PARAMS 4801
+
+typedef struct {
+  uint32_t steps;   /* Adam steps */
+  uint32_t batch;   /* samples per step, drawn with replacement */
+  float lr;         /* Adam step size */
+  float tau;        /* pinball-loss quantile in (0,1); 0 = mean squared error */
+  uint64_t seed;    /* sampling seed (non-zero) */
+} mj_band_train_params;
+
+/* Features and band-K results of every candidate of the last mj_join run
+ * with MJ_FLAG_FEATURES (or in learned mode): d_x gets m x MJ_BAND_FEATURES
+ * floats (row-major), d_ed min(ED, K+1) per candidate (plain mode), d_i/d_j
+ * the pairs (all nullable).  *count (nullable) receives m. */
+int mj_features_copy(mj_ctx* ctx, float* d_x, uint32_t* d_ed, uint32_t* d_i, uint32_t* d_j, uint64_t* count,
+                     void* stream);
+/* Fresh model: He-normal weights from `seed`, zero biases; sets the band rule. */
+int mj_band_init(mj_ctx* ctx, uint64_t seed, uint32_t margin, uint32_t min_multiplicity);
+/* Trains the model on m samples (features d_x, band-K results d_ed with
+ * target min(ED, K+1)/K) with the project's forward, backward and Adam
+ * kernels; *final_loss (nullable) gets the last step's batch loss. */
+int mj_band_train(mj_ctx* ctx, const float* d_x, const uint32_t* d_ed, uint64_t m, uint32_t K,
+                  const mj_band_train_params* tp, void* stream, float* final_loss);
+/* Model output for m feature rows (no gate). */
+int mj_band_forward(mj_ctx* ctx, const float* d_x, uint64_t m, void* stream, float* d_yhat);
+/* Loss and its gradient with respect to all MJ_BAND_PARAMS parameters over
+ * the m samples (targets d_y), tau as in mj_band_train; synchronises. */
+int mj_band_grad(mj_ctx* ctx, const float* d_x, const float* d_y, uint64_t m, float tau, void* stream,
+                 float* d_grad, float* loss);
+int mj_band_get_weights(const mj_ctx* ctx, float* h_w, uint64_t count);
+int mj_band_set_weights(mj_ctx* ctx, const float* h_w, uint64_t count);
+/* Binary file: magic "MJBAND01", margin, min_multiplicity, the parameters. */
+int mj_band_save(const mj_ctx* ctx, const char* path);
+int mj_band_load(mj_ctx* ctx, const char* path);
 
 #ifdef __cplusplus
 }

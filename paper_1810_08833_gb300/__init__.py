@@ -45,6 +45,17 @@ class Derived(ctypes.Structure):
                 ("N", ctypes.c_uint64), ("rank", ctypes.c_uint8 * 256)]
 
 
+class BandTrainParams(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint32), ("batch", ctypes.c_uint32), ("lr", ctypes.c_float),
+                ("tau", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+MJ_FLAG_KEY_CHECK = 1
+MJ_FLAG_FEATURES = 16
+BAND_FEATURES = 8
+BAND_PARAMS = 4801
+
+
 class VerifyConfig(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_uint32), ("lanes", ctypes.c_uint32)]
 
@@ -91,6 +102,16 @@ _SIGS = {
     "mj_result_copy": (ctypes.c_int, [VP, VP, VP, VP, VP]),
     "mj_join_host": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, ctypes.POINTER(U64)]),
     "mj_result_copy_host": (ctypes.c_int, [VP, VP, VP, VP, VP]),
+    "mj_features_copy": (ctypes.c_int, [VP, VP, VP, VP, VP, ctypes.POINTER(U64), VP]),
+    "mj_band_init": (ctypes.c_int, [VP, U64, U32, U32]),
+    "mj_band_train": (ctypes.c_int, [VP, VP, VP, U64, U32, ctypes.POINTER(BandTrainParams), VP,
+                                     ctypes.POINTER(ctypes.c_float)]),
+    "mj_band_forward": (ctypes.c_int, [VP, VP, U64, VP, VP]),
+    "mj_band_grad": (ctypes.c_int, [VP, VP, VP, U64, ctypes.c_float, VP, VP, ctypes.POINTER(ctypes.c_float)]),
+    "mj_band_get_weights": (ctypes.c_int, [VP, VP, U64]),
+    "mj_band_set_weights": (ctypes.c_int, [VP, VP, U64]),
+    "mj_band_save": (ctypes.c_int, [VP, ctypes.c_char_p]),
+    "mj_band_load": (ctypes.c_int, [VP, ctypes.c_char_p]),
 }
 
 _lib = None
@@ -251,6 +272,63 @@ class Context:
         oe = torch.empty(m, dtype=torch.int32, device=data.device)
         _check(self._lib.mj_result_copy(self._h, _ptr(oi), _ptr(oj), _ptr(oe), _stream(stream)), "mj_result_copy")
         return oi, oj, oe
+
+    # ---- learned first-pass band
+    def features(self, stream=None):
+        """Features, band-K results and pairs of every candidate of the last
+        join run with MJ_FLAG_FEATURES (or in learned mode)."""
+        import torch
+        cnt = U64()
+        _check(self._lib.mj_features_copy(self._h, None, None, None, None, ctypes.byref(cnt), _stream(stream)),
+               "mj_features_copy")
+        m = cnt.value
+        x = torch.empty((m, BAND_FEATURES), dtype=torch.float32, device="cuda")
+        ed = torch.empty(m, dtype=torch.int32, device="cuda")
+        ci = torch.empty(m, dtype=torch.int32, device="cuda")
+        cj = torch.empty(m, dtype=torch.int32, device="cuda")
+        _check(self._lib.mj_features_copy(self._h, _ptr(x), _ptr(ed), _ptr(ci), _ptr(cj), None, _stream(stream)),
+               "mj_features_copy")
+        return x, ed, ci, cj
+
+    def band_init(self, seed: int = 1, margin: int = 0, min_multiplicity: int = 2):
+        _check(self._lib.mj_band_init(self._h, seed, margin, min_multiplicity), "mj_band_init")
+
+    def band_train(self, x, ed, K: int, steps: int = 2000, batch: int = 1024, lr: float = 1e-3, tau: float = 0.9,
+                   seed: int = 1, stream=None) -> float:
+        tp = BandTrainParams(steps, batch, lr, tau, seed)
+        loss = ctypes.c_float()
+        _check(self._lib.mj_band_train(self._h, _ptr(x), _ptr(ed), x.shape[0], K, ctypes.byref(tp), _stream(stream),
+                                       ctypes.byref(loss)), "mj_band_train")
+        return loss.value
+
+    def band_forward(self, x, stream=None):
+        import torch
+        out = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        _check(self._lib.mj_band_forward(self._h, _ptr(x), x.shape[0], _stream(stream), _ptr(out)), "mj_band_forward")
+        return out
+
+    def band_grad(self, x, y, tau: float = 0.0, stream=None):
+        import torch
+        g = torch.empty(BAND_PARAMS, dtype=torch.float32, device=x.device)
+        loss = ctypes.c_float()
+        _check(self._lib.mj_band_grad(self._h, _ptr(x), _ptr(y), x.shape[0], tau, _stream(stream), _ptr(g),
+                                      ctypes.byref(loss)), "mj_band_grad")
+        return g, loss.value
+
+    def band_weights(self) -> np.ndarray:
+        w = np.empty(BAND_PARAMS, dtype=np.float32)
+        _check(self._lib.mj_band_get_weights(self._h, w.ctypes.data, BAND_PARAMS), "mj_band_get_weights")
+        return w
+
+    def band_set_weights(self, w: np.ndarray):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(self._lib.mj_band_set_weights(self._h, w.ctypes.data, w.shape[0]), "mj_band_set_weights")
+
+    def band_save(self, path: str):
+        _check(self._lib.mj_band_save(self._h, path.encode()), "mj_band_save")
+
+    def band_load(self, path: str):
+        _check(self._lib.mj_band_load(self._h, path.encode()), "mj_band_load")
 
     def join_host(self, data: np.ndarray, offsets: np.ndarray, p: Params, stream=None, out=None):
         """Host buffers in, host arrays out (pinned buffers avoid staging copies)."""

@@ -112,6 +112,14 @@ struct mj_ctx {
   uint64_t n_part = 0, n_cand = 0, n_out = 0;
   // bit-planes written by the partition kernel for the verifier
   mj_verify_config vcfg{MJ_VERIFY_KERNEL_AUTO, 0};
+  // learned first-pass band: parameters P, Adam moments M and V, gradient G, loss
+  Buf band;
+  bool band_ready = false;
+  uint32_t band_margin = 0, band_min_mult = 2;
+  int band_step = 0;
+  Buf feat_x, mult, run_start, parts, yhat, kband, vlist, vflags, voffs;
+  bool have_features = false;
+  bool work_started = false;   // verification counters cleared in this call
   bool planes_ready = false;
   uint64_t planes_pw = 0;
   uint32_t planes_gw = 0;
@@ -159,6 +167,7 @@ void tstop(mj_ctx* c, int i, cudaStream_t s) {
 void begin_call(mj_ctx* c, bool timing) {
   c->stats = mj_stats{};
   c->planes_ready = false;
+  c->work_started = false;
   c->timing = timing;
   for (bool& u : c->sec_used) u = false;
   c->launches_at_start = launch_count();
@@ -313,7 +322,7 @@ int partition(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
 
 // a5-a7 (after partition): candidates in c->cand_i/j (sorted, distinct).
 int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, uint32_t flags,
-               cudaStream_t s) {
+               cudaStream_t s, bool want_run_start = false) {
   const Derived& d = c->d;
   const uint32_t nr = (uint32_t)c->n_part;
   c->n_cand = 0;
@@ -385,8 +394,10 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   const uint32_t nc = *(uint32_t*)c->h_small;
   MJ_TRY(c->cand_i.reserve((size_t)nc * 4 + 16, s));
   MJ_TRY(c->cand_j.reserve((size_t)nc * 4 + 16, s));
+  if (want_run_start) MJ_TRY(c->run_start.reserve((size_t)nc * 4 + 16, s));
   MJ_TRY(launch_compact_pairs(sp, c->uflags.as<uint32_t>(), c->uoffs.as<uint32_t>(), raw, nb,
-                              c->cand_i.as<uint32_t>(), c->cand_j.as<uint32_t>(), s));
+                              c->cand_i.as<uint32_t>(), c->cand_j.as<uint32_t>(),
+                              want_run_start ? c->run_start.as<uint32_t>() : nullptr, s));
   tstop(c, 4, s);
   c->n_cand = nc;
   c->stats.n_candidates = nc;
@@ -417,7 +428,10 @@ int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const ui
   MJ_TRY(c->dev_flags.reserve(64, s));
   MJ_CUDA_TRY(cudaMemsetAsync(c->dev_flags.p, 0, 64, s));
   MJ_TRY(c->small.reserve(64, s));
-  MJ_CUDA_TRY(cudaMemsetAsync(c->small.p, 0, 32, s));
+  if (!c->work_started) {
+    MJ_CUDA_TRY(cudaMemsetAsync(c->small.p, 0, 32, s));
+    c->work_started = true;
+  }
   VerifyArgs a;
   a.planes = c->planes.as<uint32_t>();
   a.bits = d.bits;
@@ -439,6 +453,117 @@ int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const ui
                        (int)c->vcfg.lanes));
   tstop(c, 6, s);
   return MJ_OK;
+}
+
+uint64_t readback_u32(mj_ctx* c, const uint32_t* d, cudaStream_t s, int* st) {
+  *st = readback(c, d, 4, s);
+  return *st == MJ_OK ? (uint64_t)*(uint32_t*)c->h_small : 0;
+}
+
+// Verification of all candidates of the last mj_join (a8, and a9 in learned
+// mode), then the K-band cell count.  Plain: one pass with band K.  Learned:
+// features -> MLP -> first-pass band per pair; first passes grouped by band
+// words (narrower than band K's), then band K for every pair not settled.
+int verify_stage(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const mj_params* p,
+                 cudaStream_t s) {
+  const uint64_t m = c->n_cand;
+  const uint32_t K = p->K;
+  const bool learned = p->verify_mode == MJ_VERIFY_LEARNED;
+  const bool want_feat = learned || (p->flags & MJ_FLAG_FEATURES);
+  const uint32_t* ci = c->cand_i.as<uint32_t>();
+  const uint32_t* cj = c->cand_j.as<uint32_t>();
+  MJ_TRY(c->ed.reserve(m * 4, s));
+  MJ_TRY(c->small.reserve(64, s));
+  if (want_feat) {
+    MJ_TRY(c->mult.reserve(m * 4, s));
+    MJ_TRY(c->parts.reserve((size_t)n * 4 + 16, s));
+    MJ_TRY(c->feat_x.reserve(m * 4 * kBandFeatures, s));
+    MJ_TRY(launch_multiplicity(c->run_start.as<uint32_t>(), m, c->stats.n_raw_pairs, c->mult.as<uint32_t>(), s));
+    MJ_CUDA_TRY(cudaMemsetAsync(c->parts.p, 0, (size_t)n * 4, s));
+    MJ_TRY(launch_partition_counts(c->anchor_sid.as<uint32_t>(), c->n_part, c->parts.as<uint32_t>(), s));
+    MJ_TRY(launch_band_features(ci, cj, c->mult.as<uint32_t>(), c->parts.as<uint32_t>(), d_offsets, m, K, c->d.T,
+                                c->feat_x.as<float>(), s));
+  }
+  // longest pairs first, so that the persistent verifier does not end on a
+  // tail of long pairs
+  MJ_TRY(c->keys.reserve(m * 8, s));
+  MJ_TRY(c->keys_alt.reserve(m * 8, s));
+  MJ_TRY(c->idx.reserve(m * 4, s));
+  MJ_TRY(c->idx_alt.reserve(m * 4, s));
+  MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(m), s));
+  MJ_TRY(launch_work_keys(ci, cj, d_offsets, m, c->d.N, c->keys.as<uint64_t>(), c->idx.as<uint32_t>(), s));
+  bool oalt = false;
+  MJ_TRY(radix_sort_u64(c->keys.as<uint64_t>(), c->keys_alt.as<uint64_t>(), c->idx.as<uint32_t>(),
+                        c->idx_alt.as<uint32_t>(), m, 0, bits_for(c->d.N), c->sort_tmp.p, &oalt, s));
+  const uint32_t* order = oalt ? c->idx_alt.as<uint32_t>() : c->idx.as<uint32_t>();
+  uint32_t* ed = c->ed.as<uint32_t>();
+  if (!learned) {
+    MJ_TRY(verify(c, d_bytes, d_offsets, ci, cj, nullptr, m, K, K, ed, false, s, order));
+  } else {
+    if (!c->band_ready) return MJ_ERR_STATE;
+    MJ_TRY(c->yhat.reserve(m * 4, s));
+    MJ_TRY(c->kband.reserve(m * 4, s));
+    MJ_TRY(c->vflags.reserve(m * 4, s));
+    MJ_TRY(c->voffs.reserve(m * 4 + 16, s));
+    MJ_TRY(c->vlist.reserve(m * 4 + 16, s));
+    MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(m), s));
+    MJ_TRY(launch_band_forward(c->band.as<float>(), c->feat_x.as<float>(), m, c->mult.as<uint32_t>(),
+                               c->band_min_mult, c->yhat.as<float>(), s));
+    MJ_TRY(launch_band_rule(c->yhat.as<float>(), ci, cj, d_offsets, m, K, c->band_margin, c->kband.as<uint32_t>(), s));
+    uint32_t* tot = c->voffs.as<uint32_t>() + m;
+    uint64_t first = 0;
+    int st = MJ_OK;
+    const uint32_t wK = (K + 1 + 31) / 32;
+    for (uint32_t w = 1; w < wK; ++w) {
+      MJ_TRY(launch_bucket_flags(c->kband.as<uint32_t>(), order, m, K, w, c->vflags.as<uint32_t>(), s));
+      MJ_TRY(launch_exclusive_scan_u32(c->vflags.as<uint32_t>(), c->voffs.as<uint32_t>(), m, c->scan_tmp.p, tot, s));
+      const uint64_t cnt = readback_u32(c, tot, s, &st);
+      MJ_TRY(st);
+      if (!cnt) continue;
+      MJ_TRY(launch_compact_index(c->vflags.as<uint32_t>(), c->voffs.as<uint32_t>(), order, m,
+                                  c->vlist.as<uint32_t>(), s));
+      MJ_TRY(verify(c, d_bytes, d_offsets, ci, cj, c->kband.as<uint32_t>(), cnt, K, 32 * w - 1, ed, false, s,
+                    c->vlist.as<uint32_t>()));
+      first += cnt;
+    }
+    MJ_TRY(launch_fallback_flags(c->kband.as<uint32_t>(), ed, order, m, K, c->vflags.as<uint32_t>(), s));
+    MJ_TRY(launch_exclusive_scan_u32(c->vflags.as<uint32_t>(), c->voffs.as<uint32_t>(), m, c->scan_tmp.p, tot, s));
+    const uint64_t cnt2 = readback_u32(c, tot, s, &st);
+    MJ_TRY(st);
+    if (cnt2) {
+      MJ_TRY(launch_compact_index(c->vflags.as<uint32_t>(), c->voffs.as<uint32_t>(), order, m,
+                                  c->vlist.as<uint32_t>(), s));
+      MJ_TRY(verify(c, d_bytes, d_offsets, ci, cj, nullptr, cnt2, K, K, ed, false, s, c->vlist.as<uint32_t>()));
+    }
+    const uint64_t rerun = cnt2 - (m - first);
+    c->stats.first_pass_settled = first - rerun;
+    c->stats.fallback_pairs = rerun;
+  }
+  c->have_features = want_feat;
+  return launch_band_cells(ci, cj, d_offsets, m, K, c->small.as<unsigned long long>() + 3, s);
+}
+
+// He-normal initial weights from a seeded host generator (splitmix64 +
+// Box-Muller); biases zero.
+void band_initial_weights(uint64_t seed, float* w) {
+  uint64_t state = seed;
+  auto uni = [&]() {
+    state += 0x9e3779b97f4a7c15ull;
+    uint64_t z = splitmix(state);
+    return ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  };
+  auto normal = [&]() {
+    double u1 = uni(), u2 = uni();
+    return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+  };
+  const int F = kBandFeatures, H = kBandHidden;
+  int o = 0;
+  for (int i = 0; i < H * F; ++i) w[o++] = (float)(normal() * sqrt(2.0 / F));
+  for (int i = 0; i < H; ++i) w[o++] = 0.f;
+  for (int i = 0; i < H * H; ++i) w[o++] = (float)(normal() * sqrt(2.0 / H));
+  for (int i = 0; i < H; ++i) w[o++] = 0.f;
+  for (int i = 0; i < H; ++i) w[o++] = (float)(normal() * sqrt(1.0 / H));
+  w[o++] = 0.5f;
 }
 
 }  // namespace
@@ -649,7 +774,8 @@ int mj_join(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_
             void* stream, uint64_t* count) {
   if (!c || !count) return MJ_ERR_ARG;
   MJ_TRY(check_inputs(d_bytes, d_offsets, n, p));
-  if (p->verify_mode != MJ_VERIFY_PLAIN) return MJ_ERR_STATE;
+  if (p->verify_mode > MJ_VERIFY_LEARNED) return MJ_ERR_ARG;
+  if (p->verify_mode == MJ_VERIFY_LEARNED && !c->band_ready) return MJ_ERR_STATE;
   DeviceGuard g(c->device);
   cudaStream_t s = S(stream);
   begin_call(c, true);
@@ -660,28 +786,14 @@ int mj_join(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_
   MJ_TRY(partition(c, d_bytes, d_offsets, n, nullptr, p->K, s));
   c->have_part = true;
   MJ_CUDA_TRY(cudaEventRecord(c->ev[2], s));
-  MJ_TRY(candidates(c, d_bytes, d_offsets, n, p->flags, s));
+  MJ_TRY(candidates(c, d_bytes, d_offsets, n, p->flags, s,
+                    p->verify_mode == MJ_VERIFY_LEARNED || (p->flags & MJ_FLAG_FEATURES)));
   c->have_cand = true;
   MJ_CUDA_TRY(cudaEventRecord(c->ev[3], s));
   const uint64_t m = c->n_cand;
   c->n_out = 0;
   if (m) {
-    MJ_TRY(c->ed.reserve(m * 4, s));
-    // longest pairs first, so that the persistent verifier does not end on a
-    // tail of long pairs
-    MJ_TRY(c->keys.reserve(m * 8, s));
-    MJ_TRY(c->keys_alt.reserve(m * 8, s));
-    MJ_TRY(c->idx.reserve(m * 4, s));
-    MJ_TRY(c->idx_alt.reserve(m * 4, s));
-    MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(m), s));
-    MJ_TRY(launch_work_keys(c->cand_i.as<uint32_t>(), c->cand_j.as<uint32_t>(), d_offsets, m, c->d.N,
-                            c->keys.as<uint64_t>(), c->idx.as<uint32_t>(), s));
-    bool oalt = false;
-    MJ_TRY(radix_sort_u64(c->keys.as<uint64_t>(), c->keys_alt.as<uint64_t>(), c->idx.as<uint32_t>(),
-                          c->idx_alt.as<uint32_t>(), m, 0, bits_for(c->d.N), c->sort_tmp.p, &oalt, s));
-    const uint32_t* order = oalt ? c->idx_alt.as<uint32_t>() : c->idx.as<uint32_t>();
-    MJ_TRY(verify(c, d_bytes, d_offsets, c->cand_i.as<uint32_t>(), c->cand_j.as<uint32_t>(), nullptr, m, p->K, p->K,
-                  c->ed.as<uint32_t>(), true, s, order));
+    MJ_TRY(verify_stage(c, d_bytes, d_offsets, n, p, s));
     MJ_TRY(c->eflags.reserve(m * 4, s));
     MJ_TRY(c->eoffs.reserve(m * 4 + 16, s));
     MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(m), s));
@@ -690,14 +802,14 @@ int mj_join(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_
     uint32_t* tot = c->eoffs.as<uint32_t>() + m;
     MJ_TRY(launch_exclusive_scan_u32(c->eflags.as<uint32_t>(), c->eoffs.as<uint32_t>(), m, c->scan_tmp.p, tot, s));
     MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small, tot, 4, cudaMemcpyDeviceToHost, s));
-    MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small + 1, c->small.p, 8, cudaMemcpyDeviceToHost, s));
-    MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small + 3, c->small.as<unsigned long long>() + 2, 8, cudaMemcpyDeviceToHost, s));
+    MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small + 1, c->small.as<unsigned long long>() + 3, 8, cudaMemcpyDeviceToHost, s));
     MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small + 2, c->dev_flags.p, 4, cudaMemcpyDeviceToHost, s));
+    MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small + 3, c->small.as<unsigned long long>() + 2, 8, cudaMemcpyDeviceToHost, s));
     MJ_CUDA_TRY(cudaStreamSynchronize(s));
     const uint32_t no = *(uint32_t*)c->h_small;
     c->stats.band_cells = c->h_small[1];
-    c->stats.verify_word_columns = c->h_small[3];
     c->stats.device_flags |= *(uint32_t*)(c->h_small + 2);
+    c->stats.verify_word_columns = c->h_small[3];
     MJ_TRY(c->out_i.reserve((size_t)no * 4 + 16, s));
     MJ_TRY(c->out_j.reserve((size_t)no * 4 + 16, s));
     MJ_TRY(c->out_ed.reserve((size_t)no * 4 + 16, s));
@@ -721,6 +833,146 @@ int mj_join(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_
   if (c->stats.device_flags) return MJ_ERR_DEVICE;
   c->have_out = true;
   *count = c->n_out;
+  return MJ_OK;
+}
+
+int mj_features_copy(mj_ctx* c, float* d_x, uint32_t* d_ed, uint32_t* d_i, uint32_t* d_j, uint64_t* count,
+                     void* stream) {
+  if (!c) return MJ_ERR_ARG;
+  if (!c->have_features) return MJ_ERR_STATE;
+  DeviceGuard g(c->device);
+  cudaStream_t s = S(stream);
+  const size_t m = c->n_cand;
+  if (count) *count = m;
+  if (!m) return MJ_OK;
+  if (d_x) MJ_CUDA_TRY(cudaMemcpyAsync(d_x, c->feat_x.p, m * 4 * kBandFeatures, cudaMemcpyDeviceToDevice, s));
+  if (d_ed) MJ_CUDA_TRY(cudaMemcpyAsync(d_ed, c->ed.p, m * 4, cudaMemcpyDeviceToDevice, s));
+  if (d_i) MJ_CUDA_TRY(cudaMemcpyAsync(d_i, c->cand_i.p, m * 4, cudaMemcpyDeviceToDevice, s));
+  if (d_j) MJ_CUDA_TRY(cudaMemcpyAsync(d_j, c->cand_j.p, m * 4, cudaMemcpyDeviceToDevice, s));
+  return MJ_OK;
+}
+
+static int band_buffers(mj_ctx* c, cudaStream_t s) {
+  return c->band.reserve(sizeof(float) * (4 * (size_t)kBandParams + 8), s);
+}
+
+int mj_band_init(mj_ctx* c, uint64_t seed, uint32_t margin, uint32_t min_multiplicity) {
+  if (!c) return MJ_ERR_ARG;
+  DeviceGuard g(c->device);
+  MJ_TRY(band_buffers(c, nullptr));
+  std::vector<float> w(kBandParams);
+  band_initial_weights(seed, w.data());
+  MJ_CUDA_TRY(cudaMemcpy(c->band.p, w.data(), sizeof(float) * kBandParams, cudaMemcpyHostToDevice));
+  MJ_CUDA_TRY(cudaMemset(c->band.as<float>() + kBandParams, 0, sizeof(float) * 2 * kBandParams));
+  c->band_margin = margin;
+  c->band_min_mult = min_multiplicity;
+  c->band_step = 0;
+  c->band_ready = true;
+  return MJ_OK;
+}
+
+int mj_band_train(mj_ctx* c, const float* d_x, const uint32_t* d_ed, uint64_t m, uint32_t K,
+                  const mj_band_train_params* tp, void* stream, float* final_loss) {
+  if (!c || !tp || (m && (!d_x || !d_ed))) return MJ_ERR_ARG;
+  if (!c->band_ready) return MJ_ERR_STATE;
+  if (!m || !tp->steps || !tp->batch) return MJ_ERR_ARG;
+  if (tp->tau < 0.f || tp->tau >= 1.f || tp->seed == 0) return MJ_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = S(stream);
+  begin_call(c, false);
+  float* P = c->band.as<float>();
+  float* M = P + kBandParams;
+  float* V = M + kBandParams;
+  float* G = V + kBandParams;
+  float* L = G + kBandParams;
+  for (uint32_t step = 0; step < tp->steps; ++step) {
+    MJ_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(float) * (kBandParams + 1), s));
+    MJ_TRY(launch_band_grad(P, d_x, nullptr, d_ed, K, m, tp->batch, tp->seed + (uint64_t)step * tp->batch, tp->tau,
+                            G, L, s));
+    MJ_TRY(launch_band_adam(P, G, M, V, tp->lr, 0.9f, 0.999f, 1e-8f, ++c->band_step, s));
+  }
+  float loss = 0.f;
+  MJ_CUDA_TRY(cudaMemcpyAsync(&loss, L, sizeof(float), cudaMemcpyDeviceToHost, s));
+  MJ_CUDA_TRY(cudaStreamSynchronize(s));
+  if (final_loss) *final_loss = loss;
+  c->stats.n_launches = launch_count() - c->launches_at_start;
+  return MJ_OK;
+}
+
+int mj_band_forward(mj_ctx* c, const float* d_x, uint64_t m, void* stream, float* d_yhat) {
+  if (!c || (m && (!d_x || !d_yhat))) return MJ_ERR_ARG;
+  if (!c->band_ready) return MJ_ERR_STATE;
+  DeviceGuard g(c->device);
+  return launch_band_forward(c->band.as<float>(), d_x, m, nullptr, 0, d_yhat, S(stream));
+}
+
+int mj_band_grad(mj_ctx* c, const float* d_x, const float* d_y, uint64_t m, float tau, void* stream, float* d_grad,
+                 float* loss) {
+  if (!c || !d_grad || (m && (!d_x || !d_y))) return MJ_ERR_ARG;
+  if (!c->band_ready) return MJ_ERR_STATE;
+  if (tau < 0.f || tau >= 1.f || !m) return MJ_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = S(stream);
+  float* L = c->band.as<float>() + 4 * kBandParams;
+  MJ_CUDA_TRY(cudaMemsetAsync(d_grad, 0, sizeof(float) * kBandParams, s));
+  MJ_CUDA_TRY(cudaMemsetAsync(L, 0, sizeof(float), s));
+  MJ_TRY(launch_band_grad(c->band.as<float>(), d_x, d_y, nullptr, 0, m, m, 0, tau, d_grad, L, s));
+  float l = 0.f;
+  MJ_CUDA_TRY(cudaMemcpyAsync(&l, L, sizeof(float), cudaMemcpyDeviceToHost, s));
+  MJ_CUDA_TRY(cudaStreamSynchronize(s));
+  if (loss) *loss = l;
+  return MJ_OK;
+}
+
+int mj_band_get_weights(const mj_ctx* c, float* h_w, uint64_t count) {
+  if (!c || !h_w || count != (uint64_t)kBandParams) return MJ_ERR_ARG;
+  if (!c->band_ready) return MJ_ERR_STATE;
+  DeviceGuard g(c->device);
+  MJ_CUDA_TRY(cudaMemcpy(h_w, c->band.p, sizeof(float) * kBandParams, cudaMemcpyDeviceToHost));
+  return MJ_OK;
+}
+
+int mj_band_set_weights(mj_ctx* c, const float* h_w, uint64_t count) {
+  if (!c || !h_w || count != (uint64_t)kBandParams) return MJ_ERR_ARG;
+  DeviceGuard g(c->device);
+  MJ_TRY(band_buffers(c, nullptr));
+  MJ_CUDA_TRY(cudaMemcpy(c->band.p, h_w, sizeof(float) * kBandParams, cudaMemcpyHostToDevice));
+  if (!c->band_ready) {
+    MJ_CUDA_TRY(cudaMemset(c->band.as<float>() + kBandParams, 0, sizeof(float) * 2 * kBandParams));
+    c->band_step = 0;
+  }
+  c->band_ready = true;
+  return MJ_OK;
+}
+
+int mj_band_save(const mj_ctx* c, const char* path) {
+  if (!c || !path) return MJ_ERR_ARG;
+  if (!c->band_ready) return MJ_ERR_STATE;
+  std::vector<float> w(kBandParams);
+  MJ_TRY(mj_band_get_weights(c, w.data(), kBandParams));
+  FILE* f = fopen(path, "wb");
+  if (!f) return MJ_ERR_ARG;
+  const uint32_t hdr[4] = {1u, (uint32_t)kBandParams, c->band_margin, c->band_min_mult};
+  bool ok = fwrite("MJBAND01", 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+            fwrite(w.data(), sizeof(float), w.size(), f) == w.size();
+  ok = (fclose(f) == 0) && ok;
+  return ok ? MJ_OK : MJ_ERR_ARG;
+}
+
+int mj_band_load(mj_ctx* c, const char* path) {
+  if (!c || !path) return MJ_ERR_ARG;
+  FILE* f = fopen(path, "rb");
+  if (!f) return MJ_ERR_ARG;
+  char magic[8];
+  uint32_t hdr[4];
+  std::vector<float> w(kBandParams);
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "MJBAND01", 8) == 0 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
+            hdr[0] == 1u && hdr[1] == (uint32_t)kBandParams && fread(w.data(), sizeof(float), w.size(), f) == w.size();
+  fclose(f);
+  if (!ok) return MJ_ERR_ARG;
+  MJ_TRY(mj_band_set_weights(c, w.data(), kBandParams));
+  c->band_margin = hdr[2];
+  c->band_min_mult = hdr[3];
   return MJ_OK;
 }
 

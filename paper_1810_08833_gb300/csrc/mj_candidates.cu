@@ -151,12 +151,13 @@ __global__ void unique_flags_kernel(const uint64_t* __restrict__ s, uint64_t n, 
 
 __global__ void compact_pairs_kernel(const uint64_t* __restrict__ s, const uint32_t* __restrict__ flags,
                                      const uint32_t* __restrict__ offs, uint64_t n, int nb, uint32_t* __restrict__ oi,
-                                     uint32_t* __restrict__ oj) {
+                                     uint32_t* __restrict__ oj, uint32_t* __restrict__ run_start) {
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
     if (flags[t]) {
       uint32_t o = offs[t];
       oi[o] = (uint32_t)(s[t] >> nb);
       oj[o] = (uint32_t)(s[t] & ((1ull << nb) - 1));
+      if (run_start) run_start[o] = (uint32_t)t;
     }
   }
 }
@@ -191,6 +192,72 @@ __global__ void work_keys_kernel(const uint32_t* __restrict__ ci, const uint32_t
     keys[t] = N - (uint64_t)n;
     vals[t] = (uint32_t)t;
   }
+}
+
+__global__ void multiplicity_kernel(const uint32_t* __restrict__ run_start, uint64_t nc, uint64_t raw,
+                                    uint32_t* __restrict__ mult) {
+  for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nc; u += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t e = u + 1 < nc ? run_start[u + 1] : raw;
+    mult[u] = (uint32_t)(e - run_start[u]);
+  }
+}
+
+__global__ void partition_counts_kernel(const uint32_t* __restrict__ sid, uint64_t n_anchor,
+                                        uint32_t* __restrict__ parts) {
+  // the anchor list is in string order: count runs of equal string ids
+  for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n_anchor;
+       a += (uint64_t)gridDim.x * blockDim.x) {
+    if (a == 0 || sid[a] != sid[a - 1]) {
+      uint64_t e = a + 1;
+      while (e < n_anchor && sid[e] == sid[a]) ++e;
+      parts[sid[a]] = (uint32_t)(e - a);
+    }
+  }
+}
+
+__global__ void bucket_flags_kernel(const uint32_t* __restrict__ kband, const uint32_t* __restrict__ order, uint64_t m,
+                                    uint32_t K, uint32_t w, uint32_t* __restrict__ flags) {
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t u = order ? order[q] : q;
+    const uint32_t k = kband[u];
+    flags[q] = (k < K && (k + 1 + 31) / 32 == w) ? 1u : 0u;
+  }
+}
+
+__global__ void fallback_flags_kernel(const uint32_t* __restrict__ kband, const uint32_t* __restrict__ ed,
+                                      const uint32_t* __restrict__ order, uint64_t m, uint32_t K,
+                                      uint32_t* __restrict__ flags) {
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t u = order ? order[q] : q;
+    const uint32_t k = kband[u];
+    flags[q] = (k >= K || ed[u] > k) ? 1u : 0u;
+  }
+}
+
+__global__ void compact_index_kernel(const uint32_t* __restrict__ flags, const uint32_t* __restrict__ offs,
+                                     const uint32_t* __restrict__ order, uint64_t m, uint32_t* __restrict__ out) {
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x)
+    if (flags[q]) out[offs[q]] = order ? order[q] : (uint32_t)q;
+}
+
+// K-band cells of every candidate, summed (mj_stats.band_cells).
+__global__ void band_cells_kernel(const uint32_t* __restrict__ ci, const uint32_t* __restrict__ cj,
+                                  const int64_t* __restrict__ offsets, uint64_t m, uint32_t K,
+                                  unsigned long long* __restrict__ out) {
+  unsigned long long acc = 0;
+  for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < m; u += (uint64_t)gridDim.x * blockDim.x) {
+    const int64_t lx = offsets[ci[u] + 1] - offsets[ci[u]], ly = offsets[cj[u] + 1] - offsets[cj[u]];
+    const int64_t mm = lx > ly ? lx : ly, n = lx > ly ? ly : lx;
+    if (n <= 0) continue;
+    int64_t a = mm - (int64_t)K;
+    a = a < 0 ? 0 : (a > n ? n : a);
+    const int64_t smin = a * (a + 1) / 2 + a * (int64_t)K + (n - a) * mm;
+    const int64_t b = (int64_t)K < n ? (int64_t)K : n;
+    const int64_t smax = b + (n > (int64_t)K ? (n - (int64_t)K) * (n - (int64_t)K + 1) / 2 : 0);
+    acc += (unsigned long long)(smin - smax + n);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
 }
 
 unsigned grid_for(uint64_t n, int threads = 256) {
@@ -266,9 +333,9 @@ int launch_unique_flags(const uint64_t* sorted, uint64_t n, uint32_t* flags, cud
 }
 
 int launch_compact_pairs(const uint64_t* sorted, const uint32_t* flags, const uint32_t* offs, uint64_t n, int nb,
-                         uint32_t* out_i, uint32_t* out_j, cudaStream_t s) {
+                         uint32_t* out_i, uint32_t* out_j, uint32_t* run_start, cudaStream_t s) {
   if (!n) return MJ_OK;
-  compact_pairs_kernel<<<grid_for(n), 256, 0, s>>>(sorted, flags, offs, n, nb, out_i, out_j);
+  compact_pairs_kernel<<<grid_for(n), 256, 0, s>>>(sorted, flags, offs, n, nb, out_i, out_j, run_start);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }
@@ -277,6 +344,53 @@ int launch_work_keys(const uint32_t* ci, const uint32_t* cj, const int64_t* offs
                      uint64_t* keys, uint32_t* vals, cudaStream_t s) {
   if (!m) return MJ_OK;
   work_keys_kernel<<<grid_for(m), 256, 0, s>>>(ci, cj, offsets, m, N, keys, vals);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
+int launch_multiplicity(const uint32_t* run_start, uint64_t nc, uint64_t raw, uint32_t* mult, cudaStream_t s) {
+  if (!nc) return MJ_OK;
+  multiplicity_kernel<<<grid_for(nc), 256, 0, s>>>(run_start, nc, raw, mult);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
+int launch_partition_counts(const uint32_t* anchor_sid, uint64_t n_anchor, uint32_t* parts, cudaStream_t s) {
+  if (!n_anchor) return MJ_OK;
+  partition_counts_kernel<<<grid_for(n_anchor), 256, 0, s>>>(anchor_sid, n_anchor, parts);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
+int launch_bucket_flags(const uint32_t* kband, const uint32_t* order, uint64_t m, uint32_t K, uint32_t w,
+                        uint32_t* flags, cudaStream_t s) {
+  if (!m) return MJ_OK;
+  bucket_flags_kernel<<<grid_for(m), 256, 0, s>>>(kband, order, m, K, w, flags);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
+int launch_fallback_flags(const uint32_t* kband, const uint32_t* ed, const uint32_t* order, uint64_t m, uint32_t K,
+                          uint32_t* flags, cudaStream_t s) {
+  if (!m) return MJ_OK;
+  fallback_flags_kernel<<<grid_for(m), 256, 0, s>>>(kband, ed, order, m, K, flags);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
+int launch_compact_index(const uint32_t* flags, const uint32_t* offs, const uint32_t* order, uint64_t m, uint32_t* out,
+                         cudaStream_t s) {
+  if (!m) return MJ_OK;
+  compact_index_kernel<<<grid_for(m), 256, 0, s>>>(flags, offs, order, m, out);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
+int launch_band_cells(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m, uint32_t K,
+                      unsigned long long* out, cudaStream_t s) {
+  MJ_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(unsigned long long), s));
+  if (!m) return MJ_OK;
+  band_cells_kernel<<<grid_for(m), 256, 0, s>>>(ci, cj, offsets, m, K, out);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }

@@ -144,8 +144,9 @@ int launch_key_check(const uint64_t* keys, SortedRecs r, const uint8_t* bytes, c
                      uint32_t n_rec, int slen_bits, unsigned long long* mismatches, cudaStream_t s);
 // a7: unique of sorted u64 pairs -> flags; then compaction.
 int launch_unique_flags(const uint64_t* sorted, uint64_t n, uint32_t* flags, cudaStream_t s);
+// run_start (nullable): run_start[u] = index of candidate u's first raw pair
 int launch_compact_pairs(const uint64_t* sorted, const uint32_t* flags, const uint32_t* offs, uint64_t n, int nb,
-                         uint32_t* out_i, uint32_t* out_j, cudaStream_t s);
+                         uint32_t* out_i, uint32_t* out_j, uint32_t* run_start, cudaStream_t s);
 
 // a8: banded verification (diagonal bit-vector, one thread per pair).
 struct RankTable {
@@ -181,6 +182,44 @@ int wave_lanes_for(uint32_t kmax);
 // verification order: candidate indices sorted by key = N - min length
 int launch_work_keys(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m, uint64_t N,
                      uint64_t* keys, uint32_t* vals, cudaStream_t s);
+
+// ---- learned first-pass band (MLP 8 -> 64 -> 64 -> 1)
+// features of a candidate (i, j), n = min length, d0 = length difference,
+// c = matched partition pairs behind the candidate (its multiplicity before
+// dedup), pa/pb = partitions of the two strings:
+//   log2(1+n)/16, d0/K, c/(T+1), pa/(T+1), pb/(T+1), c/min(pa,pb),
+//   log2(1+c)/8, K/(K+100)
+constexpr int kBandFeatures = 8;
+constexpr int kBandHidden = 64;
+constexpr int kBandParams = kBandHidden * kBandFeatures + kBandHidden + kBandHidden * kBandHidden + kBandHidden +
+                            kBandHidden + 1;
+static_assert(kBandParams == MJ_BAND_PARAMS && kBandFeatures == MJ_BAND_FEATURES, "ABI constants");
+int launch_band_features(const uint32_t* ci, const uint32_t* cj, const uint32_t* mult, const uint32_t* parts,
+                         const int64_t* offsets, uint64_t m, uint32_t K, uint32_t T, float* X, cudaStream_t s);
+int launch_band_forward(const float* P, const float* X, uint64_t m, const uint32_t* gate, uint32_t min_gate,
+                        float* out, cudaStream_t s);
+size_t band_grad_smem();
+int launch_band_grad(const float* P, const float* X, const float* Y, const uint32_t* ed, uint32_t K, uint64_t m,
+                     uint64_t batch, uint64_t seed, float tau, float* grad, float* loss, cudaStream_t s);
+int launch_band_adam(float* P, const float* G, float* M, float* V, float lr, float b1, float b2, float eps, int step,
+                     cudaStream_t s);
+int launch_band_rule(const float* yhat, const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m,
+                     uint32_t K, uint32_t margin, uint32_t* kband, cudaStream_t s);
+
+// multiplicity of every candidate from the run starts written by the pair
+// compaction; partitions per string from the anchor list
+int launch_multiplicity(const uint32_t* run_start, uint64_t nc, uint64_t raw, uint32_t* mult, cudaStream_t s);
+int launch_partition_counts(const uint32_t* anchor_sid, uint64_t n_anchor, uint32_t* parts, cudaStream_t s);
+// subset lists for the two verification passes
+// (order nullable: flags[q] refer to candidate order[q]; the list holds candidate ids)
+int launch_bucket_flags(const uint32_t* kband, const uint32_t* order, uint64_t m, uint32_t K, uint32_t w,
+                        uint32_t* flags, cudaStream_t s);
+int launch_fallback_flags(const uint32_t* kband, const uint32_t* ed, const uint32_t* order, uint64_t m, uint32_t K,
+                          uint32_t* flags, cudaStream_t s);
+int launch_compact_index(const uint32_t* flags, const uint32_t* offs, const uint32_t* order, uint64_t m, uint32_t* out,
+                         cudaStream_t s);
+int launch_band_cells(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m, uint32_t K,
+                      unsigned long long* out, cudaStream_t s);
 
 // output compaction (ED <= K)
 int launch_ed_flags(const uint32_t* ed, uint64_t m, uint32_t K, uint32_t* flags, cudaStream_t s);
