@@ -198,9 +198,9 @@ def run_native(args):
     data = torch.from_numpy(s.bytes).to(dev)
     off = torch.from_numpy(s.offsets).to(dev)
     ctx = mj.Context(local)
-    p = mj.params(s.K, T=s.T)
+    plain = mj.params(s.K, T=s.T)
+    learned = mj.params(s.K, T=s.T, verify_mode=mj.MJ_VERIFY_LEARNED)
     stream = torch.cuda.Stream(dev)
-    L = s.lengths()
 
     def sync_all():
         torch.cuda.synchronize(dev)
@@ -208,22 +208,43 @@ def run_native(args):
             dist.barrier()
 
     with torch.cuda.stream(stream):
+        # the band network learns from a held-out instance of the workload
+        # (different seed, a quarter of the families), outside the timed region
+        t0 = time.perf_counter()
+        tr = synth.make_config(cfg, seed=100 + seed, n_roots=max(10, synth.CONFIGS[cfg][3] // 4))
+        tr_data = torch.from_numpy(tr.bytes).to(dev)
+        tr_off = torch.from_numpy(tr.offsets).to(dev)
+        ctx.join(tr_data, tr_off, mj.params(tr.K, T=tr.T, flags=mj.MJ_FLAG_FEATURES), stream=stream)
+        x, ed, _, _ = ctx.features(stream=stream)
+        ctx.band_init(seed=5)
+        train_loss = ctx.band_train(x, ed, K=tr.K, steps=args.band_steps, batch=1024, lr=2e-3, tau=0.9, seed=13,
+                                    stream=stream)
+        train_s = time.perf_counter() - t0
+        n_train = int(x.shape[0])
+        del x, ed, tr_data, tr_off
+
+        def timed(p, steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            st = []
+            e0.record(stream)
+            for _ in range(steps):
+                out = ctx.join(data, off, p, stream=stream)
+                st.append(ctx.stats())
+            e1.record(stream)
+            sync_all()
+            return e0.elapsed_time(e1) / steps, st, out
+
         for _ in range(args.warmup):
-            ctx.join(data, off, p, stream=stream)
+            ctx.join(data, off, learned, stream=stream)
+            ctx.join(data, off, plain, stream=stream)
         sync_all()
         clocks = Clocks(local)
         clocks.start()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        stats = []
-        e0.record(stream)
-        for _ in range(args.steps):
-            ctx.join(data, off, p, stream=stream)
-            stats.append(ctx.stats())
-        e1.record(stream)
-        sync_all()
+        ms, stats, out_l = timed(learned, args.steps)
+        ms_plain, stats_plain, out_p = timed(plain, args.steps)
         clk = clocks.stop()
-        ms = e0.elapsed_time(e1) / args.steps
+        identical = all(bool(torch.equal(a, b)) for a, b in zip(out_l, out_p))
 
         # end to end through host buffers: H2D of the inputs and D2H of the
         # output pairs inside every timed step
@@ -233,17 +254,40 @@ def run_native(args):
         h_out = [torch.empty(max(1, n_out) + 1024, dtype=torch.int32).pin_memory() for _ in range(3)]
         outs = tuple(o.numpy().view(np.uint32) for o in h_out)
         for _ in range(max(1, args.warmup // 2)):
-            ctx.join_host(h_data.numpy(), h_off.numpy(), p, stream=stream, out=outs)
+            ctx.join_host(h_data.numpy(), h_off.numpy(), learned, stream=stream, out=outs)
         sync_all()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for _ in range(args.steps):
-            ctx.join_host(h_data.numpy(), h_off.numpy(), p, stream=stream, out=outs)
+            ctx.join_host(h_data.numpy(), h_off.numpy(), learned, stream=stream, out=outs)
         f1.record(stream)
         sync_all()
         ms_e2e = f0.elapsed_time(f1) / args.steps
         e2e_stats = ctx.stats()
+
+        # batched verification: one persistent launch (default kernel) vs the
+        # autotuned per-length-bucket plan, as one persistent launch per run
+        # of buckets sharing a kernel (captured in a CUDA graph) or as one
+        # launch per bucket
+        batching = None
+        if args.batching:
+            ci, cj = ctx.candidates(data, off, plain, stream=stream)
+            tune = ctx.autotune_verify(data, off, ci, cj, s.K, sample=args.tune_sample, stream=stream)
+            batching = {"tuned": {str(b): {"pairs": v["pairs"], "kernel": v["kernel"], "lanes": v["lanes"],
+                                           "ms": v["ms"]} for b, v in tune["buckets"].items()}}
+            for name, cfgv in (("single_persistent", (mj.MJ_VERIFY_KERNEL_AUTO, 0, 0, 0)),
+                               ("tuned_persistent_graph", (mj.MJ_VERIFY_KERNEL_TUNED, 0, 0, 1)),
+                               ("tuned_per_bucket", (mj.MJ_VERIFY_KERNEL_TUNED, 0, 1, 0))):
+                ctx.set_verify_config(*cfgv)
+                for _ in range(2):
+                    ctx.join(data, off, plain, stream=stream)
+                sync_all()
+                tms, tst, tout = timed(plain, args.steps)
+                batching[name] = {"join_ms": tms,
+                                  "verify_ms": statistics.median([x["ms_section"]["verify_kernel"] for x in tst]),
+                                  "identical_output": all(bool(torch.equal(a, b)) for a, b in zip(tout, out_p))}
+            ctx.set_verify_config(0, 0, 0, 0)
 
     last = stats[-1]
     cells = int(last["band_cells"])
@@ -251,9 +295,9 @@ def run_native(args):
     launches = int(sum(st["n_launches"] for st in stats))
 
     if world > 1:
-        t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
+        t = torch.tensor([ms, ms_e2e, ms_plain], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0]), float(t[1])
+        ms, ms_e2e, ms_plain = float(t[0]), float(t[1]), float(t[2])
         c = torch.tensor([cells], dtype=torch.float64, device=dev)
         dist.all_reduce(c, op=dist.ReduceOp.SUM)
         cells_all = float(c[0])
@@ -275,9 +319,21 @@ def run_native(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": workload_name(cfg, s), "n_strings": s.n, "bytes": nbytes, "K": s.K, "T": s.T,
-                       "verify_mode": "plain", "parallelism": f"replicas x{world}",
+                       "verify_mode": "learned first-pass band, fallback to K", "parallelism": f"replicas x{world}",
                        "l2": f"inputs ({nbytes / 1e6:.0f} MB) larger than L2 (129 MB); no flush"},
             "join_ms": ms,
+            "learned_vs_plain": {
+                "learned_ms": ms, "plain_ms": ms_plain, "speedup": ms_plain / ms, "identical_output": identical,
+                "learned_verify_word_columns": int(stats[-1]["verify_word_columns"]),
+                "plain_verify_word_columns": int(stats_plain[-1]["verify_word_columns"]),
+                "first_pass_settled": int(stats[-1]["first_pass_settled"]),
+                "fallback_pairs": int(stats[-1]["fallback_pairs"]),
+                "plain_sections_ms": {k: round(statistics.median([st["ms_section"][k] for st in stats_plain]), 4)
+                                      for k in mj.SECTIONS},
+                "band_training": {"samples": n_train, "steps": args.band_steps, "seconds": round(train_s, 2),
+                                  "final_batch_loss": train_loss, "data": "held-out seed, a quarter of the families"},
+            },
+            "batching": batching,
             "cells_per_step": cells_all,
             "candidates": int(last["n_candidates"]), "raw_pairs": int(last["n_raw_pairs"]),
             "partitions": int(last["n_partitions"]), "output_pairs": int(last["n_output"]),
@@ -339,9 +395,14 @@ def main():
     ap.add_argument("--cpu-roots", type=int, default=400)
     ap.add_argument("--ref-roots", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--band-steps", type=int, default=2000)
+    ap.add_argument("--batching", type=int, default=-1, help="compare batched verification plans (default: config 3)")
+    ap.add_argument("--tune-sample", type=int, default=2048)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3
+    if args.batching < 0:
+        args.batching = 1 if args.config == 3 else 0
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -54,17 +54,45 @@ extern "C" {
 #define MJ_VERIFY_KERNEL_AUTO 0       /* diagonal for K <= 255, wavefront above */
 #define MJ_VERIFY_KERNEL_DIAGONAL 1   /* one thread per pair, band as ceil((K+1)/32) words */
 #define MJ_VERIFY_KERNEL_WAVEFRONT 2  /* G lanes per pair, 32-row blocks, skewed wavefront */
+#define MJ_VERIFY_KERNEL_TUNED 3      /* per length bucket, as chosen by mj_autotune_verify */
 
 typedef struct mj_ctx mj_ctx;
 
 /* Choice of verification kernel for a context (used by mj_verify and mj_join).
- *  kernel  MJ_VERIFY_KERNEL_*.
- *  lanes   wavefront only: lanes per pair (2, 4, 8, 16 or 32); 0 = the fewest
- *          that hold the band.  Too few lanes for a band is MJ_ERR_UNSUPPORTED. */
+ * Pairs are verified longest first; with MJ_VERIFY_KERNEL_TUNED each length
+ * bucket (floor(log2) of the shorter length) uses the kernel the autotuner
+ * picked for it.
+ *  kernel    MJ_VERIFY_KERNEL_*.
+ *  lanes     wavefront only: lanes per pair (2, 4, 8, 16 or 32); 0 = the fewest
+ *            that hold the band.  Too few lanes for a band is MJ_ERR_UNSUPPORTED.
+ *  batching  TUNED only: 0 = one persistent launch per run of consecutive
+ *            buckets that share a kernel; 1 = one launch per length bucket.
+ *  graph     1 = capture the plain verification stage (ordering, bucketing,
+ *            launches) in a CUDA graph and replay it on later calls with the
+ *            same inputs and sizes (the first call with new inputs runs
+ *            uncaptured, the second captures).  Needs a stream other than the
+ *            legacy or per-thread default stream; on those it runs uncaptured. */
 typedef struct {
   uint32_t kernel;
   uint32_t lanes;
+  uint32_t batching;
+  uint32_t graph;
 } mj_verify_config;
+
+/* Result of mj_autotune_verify, per length bucket b (shorter length in
+ * [2^b, 2^(b+1))): pairs seen, the kernel and lanes chosen, and the time of
+ * every candidate tried on the bucket's sample (candidates: diagonal when
+ * K <= 255, then the wavefront with 2^c times the fewest lanes). */
+#define MJ_TUNE_CANDIDATES 6
+typedef struct {
+  uint32_t count[32];
+  uint32_t kernel[32];
+  uint32_t lanes[32];
+  float ms[32][MJ_TUNE_CANDIDATES];   /* 0 = not tried */
+  uint32_t cand_kernel[MJ_TUNE_CANDIDATES];
+  uint32_t cand_lanes[MJ_TUNE_CANDIDATES];
+  uint32_t n_candidates;
+} mj_autotune_report;
 
 /* Parameters of one join.
  *  K       edit-distance threshold (Sec. 1).
@@ -72,7 +100,7 @@ typedef struct {
  *  q       q-gram length; 0 = the rule of Sec. 2.2, q = ceil(3 log_|Sigma|(N/T)),
  *          with Sigma the distinct byte values present and N the longest length;
  *          capped so that q * ceil(log2 |Sigma|) <= 64.
- *  r_min   lower bound applied to the neighbourhood radius of Alg. 2 line 2
+ *  r_min   lower bound applied to the neighbourhood radius of Alg. 2
  *          (default 1; the literal rule gives r <= 0 for short strings).
  *  seed    seed of the random q-gram function Pi and of the partition key.
  *  verify_mode  MJ_VERIFY_PLAIN or MJ_VERIFY_LEARNED.
@@ -89,7 +117,7 @@ typedef struct {
   uint32_t flags;
 } mj_params;
 
-/* Parameters as derived for an input (Sec. 2.2, Alg. 2 line 2). */
+/* Parameters as derived for an input (Sec. 2.2, Alg. 2). */
 typedef struct {
   uint32_t sigma;        /* distinct byte values present */
   uint32_t bits;         /* bits per rank code, max(1, ceil(log2 sigma)) */
@@ -104,7 +132,7 @@ typedef struct {
   uint64_t n_strings, n_bytes;
   uint64_t n_partitions;       /* records of Alg. 1 over all strings */
   uint64_t n_raw_pairs;        /* pairs passing both filters, before dedup */
-  uint64_t n_candidates;       /* |C| after dedup (Alg. 3 line 20) */
+  uint64_t n_candidates;       /* |C| after dedup (Alg. 3) */
   uint64_t n_output;           /* pairs with ED <= K */
   uint64_t key_collisions;     /* groups with equal keys but different bytes (flags bit 0) */
   uint64_t band_cells;         /* K-band cells of all candidates: sum over pairs of
@@ -134,14 +162,22 @@ int mj_get_stats(const mj_ctx* ctx, mj_stats* out);
 /* Sets the verification kernel of the context (default: MJ_VERIFY_KERNEL_AUTO). */
 int mj_set_verify_config(mj_ctx* ctx, const mj_verify_config* cfg);
 
-/* Step a1 (Sec. 2.2, Alg. 2 line 2): Sigma, rank codes, N, q, T, r_max. */
+/* Autotuner of the verifier's band tiling: times every candidate kernel on up
+ * to `sample` pairs of every length bucket of the given pairs (band K) and
+ * stores the fastest per bucket in the context, for MJ_VERIFY_KERNEL_TUNED.
+ * Synchronises.  rep (nullable) receives the measurements. */
+int mj_autotune_verify(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n,
+                       const uint32_t* d_i, const uint32_t* d_j, uint64_t m, uint32_t K, uint32_t sample,
+                       void* stream, mj_autotune_report* rep);
+
+/* Step a1 (Sec. 2.2, Alg. 2): Sigma, rank codes, N, q, T, r_max. */
 int mj_derive(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n,
               const mj_params* p, void* stream, mj_derived* out);
 
 /* Steps a2-a4 (Alg. 1-2): partitions of every string.  *count receives the
  * number of partitions; mj_partition_copy writes them in string order, each
  * (sid, pos, len, key) with key the 64-bit partition-substring hash
- * (Alg. 3 line 2's f).  `d_qgram_table` (nullable) replaces Pi by a table of
+ * (Alg. 3's partition hash f).  `d_qgram_table` (nullable) replaces Pi by a table of
  * 2^(q*bits) 64-bit values indexed by the packed rank code of a q-gram (first
  * symbol most significant) — the form of Table 2's worked example. */
 int mj_partition(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n,
@@ -149,7 +185,7 @@ int mj_partition(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_offsets, 
 int mj_partition_copy(mj_ctx* ctx, uint32_t* d_sid, uint32_t* d_pos, uint32_t* d_len,
                       uint64_t* d_key, void* stream);
 
-/* Steps a2-a7 (Alg. 3 lines 4-20): the deduplicated candidate set C.
+/* Steps a2-a7 (Alg. 3's hash join): the deduplicated candidate set C.
  * *count receives |C|; mj_candidates_copy writes the pairs (i < j) sorted. */
 int mj_candidates(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n,
                   const mj_params* p, const uint64_t* d_qgram_table, void* stream, uint64_t* count);
@@ -234,12 +270,15 @@ typedef struct {
 } mj_band_train_params;
 
 /* Features and band-K results of every candidate of the last mj_join run
- * with MJ_FLAG_FEATURES (or in learned mode): d_x gets m x MJ_BAND_FEATURES
+ * with MJ_FLAG_FEATURES: d_x gets m x MJ_BAND_FEATURES
  * floats (row-major), d_ed min(ED, K+1) per candidate (plain mode), d_i/d_j
  * the pairs (all nullable).  *count (nullable) receives m. */
 int mj_features_copy(mj_ctx* ctx, float* d_x, uint32_t* d_ed, uint32_t* d_i, uint32_t* d_j, uint64_t* count,
                      void* stream);
-/* Fresh model: He-normal weights from `seed`, zero biases; sets the band rule. */
+/* Fresh model: He-normal weights from `seed`, zero biases; sets the band rule.
+ * min_multiplicity = 0 lets mj_band_train set it to the 1st percentile of the
+ * multiplicity of the training samples whose band-K result fits a narrower
+ * first band (candidates below it always get band K). */
 int mj_band_init(mj_ctx* ctx, uint64_t seed, uint32_t margin, uint32_t min_multiplicity);
 /* Trains the model on m samples (features d_x, band-K results d_ed with
  * target min(ED, K+1)/K) with the project's forward, backward and Adam

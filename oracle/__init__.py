@@ -7,7 +7,7 @@ benchmark may import this package; the product path never does.
 
 Threading: partitioning (per string) and verification (per pair) are split
 into chunks run on a thread pool; ctypes releases the GIL during each call.
-The hash join itself (Alg. 3 lines 4-20) runs sequentially, as in the paper.
+The hash join of Alg. 3 runs sequentially, as in the paper.
 """
 from __future__ import annotations
 
@@ -234,7 +234,7 @@ def partition(data: np.ndarray, offsets: np.ndarray, p: Params, table: np.ndarra
 # ---------------------------------------------------------------- join
 
 def candidates(data: np.ndarray, offsets: np.ndarray, K: int, parts: Partitions) -> np.ndarray:
-    """Alg. 3 lines 4-20 (sequential hash join, both filters, eviction, dedup).
+    """Alg. 3's hash join (sort, both filters, eviction, dedup), sequential.
     Returns an (m, 2) int64 array of distinct pairs i < j, sorted."""
     lib = _load()
     data = _u8(data)

@@ -76,7 +76,7 @@ uint32_t mjo_q_rule(uint64_t N, uint32_t T, uint32_t sigma) {
     return q < 1 ? 1 : q;
 }
 
-// Alg. 2 line 2: r = floor((|s| - q + 1 - T) / (2T + 2)).  Reading: the
+// Alg. 2, neighbourhood radius: r = floor((|s| - q + 1 - T) / (2T + 2)).  Reading: the
 // division floors on signed integers, and r is raised to at least r_min
 // (r_min = 0 keeps the literal rule wherever it is non-negative).
 int64_t mjo_radius(int64_t slen, int64_t q, int64_t T, int64_t r_min) {
@@ -84,7 +84,7 @@ int64_t mjo_radius(int64_t slen, int64_t q, int64_t T, int64_t r_min) {
     return r < r_min ? r_min : r;
 }
 
-// Alg. 2 lines 3-6: h[i] = Pi(s[i .. i+q-1]) for every q-gram start i in
+// Alg. 2, q-gram values: h[i] = Pi(s[i .. i+q-1]) for every q-gram start i in
 // [0, |s| - q].  Pi (Table 1: a random function Sigma^q -> (0,1)) is realised
 // as: the q symbols, each replaced by its rank code of `bits` bits, packed
 // first-symbol-most-significant into one integer `code`; then
@@ -141,7 +141,7 @@ int64_t mjo_find_anchors(const uint64_t* h, int64_t m, int64_t slen, int64_t r, 
 }
 
 // Alg. 1 (Partition-String) applied to strings [lo, hi) of a concatenated set.
-// Reading of Alg. 1 line 3: the pair emitted for anchor index i is
+// Reading of Alg. 1's partition pair: the pair emitted for anchor index i is
 // (a_i, a_{i+1} - a_i) (the printed a_p is a typo).  Writes (sid, pos, len)
 // triples in string order; returns their number, or -1 if `cap` is too small.
 // `n_anchor` (optional) receives every string's anchor count.
@@ -173,13 +173,12 @@ int64_t mjo_partition_range(const uint8_t* bytes, const int64_t* offsets, int64_
     return cnt;
 }
 
-// Alg. 3 lines 4-20: sort the strings by (length, alphabetical order), then
+// Alg. 3, the hash join: sort the strings by (length, alphabetical order), then
 // for every string in that order and every partition (pos, len) of it, probe
 // the bucket of the partition's substring in table D: an entry (j, pos_j,
-// len_j) whose string length differs by more than K is evicted (line 14);
-// otherwise the pair is a candidate if the position filter of line 8 holds.
-// Then (i, pos, len) is stored in the bucket (line 17).  Duplicates are
-// removed (line 20).
+// len_j) whose string length differs by more than K is evicted; otherwise
+// the pair is a candidate if the position filter holds.  Then (i, pos, len)
+// is stored in the bucket.  Duplicates are removed at the end.
 // Readings: the bucket of f is the exact substring (no hash collisions can
 // merge different substrings), and a string never pairs with itself (the
 // output set of the algorithm requires i != j), which arises when one string
@@ -225,7 +224,7 @@ int64_t mjo_candidates(const uint8_t* bytes, const int64_t* offsets, int64_t n, 
                         C.emplace_back(std::min(i, e.j), std::max(i, e.j));
                     kept.push_back(e);
                 }
-                // else: evicted from D (line 14)
+                // else: evicted from D (length filter)
             }
             kept.push_back(Entry{i, pos, len});
             bucket.swap(kept);

@@ -8,7 +8,7 @@ raise.
 Functions mirror the C entry points:
     derive      mj_derive       step a1 (Sec. 2.2 parameters)
     partition   mj_partition    steps a2-a4 (Alg. 1-2)
-    candidates  mj_candidates   steps a2-a7 (Alg. 3 lines 4-20)
+    candidates  mj_candidates   steps a2-a7 (Alg. 3's hash join)
     verify      mj_verify       step a8 (Ukkonen band, Sec. 3)
     join        mj_join         the whole path (Alg. 3)
     join_host   mj_join_host    the whole path from/to host memory
@@ -57,12 +57,20 @@ BAND_PARAMS = 4801
 
 
 class VerifyConfig(ctypes.Structure):
-    _fields_ = [("kernel", ctypes.c_uint32), ("lanes", ctypes.c_uint32)]
+    _fields_ = [("kernel", ctypes.c_uint32), ("lanes", ctypes.c_uint32), ("batching", ctypes.c_uint32),
+                ("graph", ctypes.c_uint32)]
+
+
+class AutotuneReport(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint32 * 32), ("kernel", ctypes.c_uint32 * 32), ("lanes", ctypes.c_uint32 * 32),
+                ("ms", (ctypes.c_float * 6) * 32), ("cand_kernel", ctypes.c_uint32 * 6),
+                ("cand_lanes", ctypes.c_uint32 * 6), ("n_candidates", ctypes.c_uint32)]
 
 
 MJ_VERIFY_KERNEL_AUTO = 0
 MJ_VERIFY_KERNEL_DIAGONAL = 1
 MJ_VERIFY_KERNEL_WAVEFRONT = 2
+MJ_VERIFY_KERNEL_TUNED = 3
 
 
 class Stats(ctypes.Structure):
@@ -91,6 +99,7 @@ _SIGS = {
     "mj_destroy": (None, [VP]),
     "mj_get_stats": (ctypes.c_int, [VP, ctypes.POINTER(Stats)]),
     "mj_set_verify_config": (ctypes.c_int, [VP, ctypes.POINTER(VerifyConfig)]),
+    "mj_autotune_verify": (ctypes.c_int, [VP, VP, VP, U32, VP, VP, U64, U32, U32, VP, ctypes.POINTER(AutotuneReport)]),
     "mj_derive": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, ctypes.POINTER(Derived)]),
     "mj_partition": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, VP, ctypes.POINTER(U64)]),
     "mj_partition_copy": (ctypes.c_int, [VP, VP, VP, VP, VP, VP]),
@@ -208,9 +217,23 @@ class Context:
         out["ms_section"] = dict(zip(SECTIONS, list(s.ms_section)))
         return out
 
-    def set_verify_config(self, kernel: int = MJ_VERIFY_KERNEL_AUTO, lanes: int = 0):
-        cfg = VerifyConfig(kernel, lanes)
+    def set_verify_config(self, kernel: int = MJ_VERIFY_KERNEL_AUTO, lanes: int = 0, batching: int = 0,
+                          graph: int = 0):
+        cfg = VerifyConfig(kernel, lanes, batching, graph)
         _check(self._lib.mj_set_verify_config(self._h, ctypes.byref(cfg)), "mj_set_verify_config")
+
+    def autotune_verify(self, data, offsets, i, j, K: int, sample: int = 4096, stream=None) -> dict:
+        n = _check_inputs(data, offsets)
+        rep = AutotuneReport()
+        _check(self._lib.mj_autotune_verify(self._h, _ptr(data), _ptr(offsets), n, _ptr(i), _ptr(j), i.numel(), K,
+                                            sample, _stream(stream), ctypes.byref(rep)), "mj_autotune_verify")
+        cands = [(rep.cand_kernel[k], rep.cand_lanes[k]) for k in range(rep.n_candidates)]
+        buckets = {}
+        for b in range(32):
+            if rep.count[b]:
+                buckets[b] = {"pairs": rep.count[b], "kernel": rep.kernel[b], "lanes": rep.lanes[b],
+                              "ms": {f"{k}/{l}": round(rep.ms[b][c], 4) for c, (k, l) in enumerate(cands)}}
+        return {"candidates": cands, "buckets": buckets}
 
     def derive(self, data, offsets, p: Params, stream=None) -> dict:
         n = _check_inputs(data, offsets)
@@ -290,7 +313,7 @@ class Context:
                "mj_features_copy")
         return x, ed, ci, cj
 
-    def band_init(self, seed: int = 1, margin: int = 0, min_multiplicity: int = 2):
+    def band_init(self, seed: int = 1, margin: int = 0, min_multiplicity: int = 0):
         _check(self._lib.mj_band_init(self._h, seed, margin, min_multiplicity), "mj_band_init")
 
     def band_train(self, x, ed, K: int, steps: int = 2000, batch: int = 1024, lr: float = 1e-3, tau: float = 0.9,

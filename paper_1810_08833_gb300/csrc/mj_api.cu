@@ -67,7 +67,7 @@ static uint32_t q_rule(uint64_t N, uint32_t T, uint32_t sigma) {
   return q ? q : 1;
 }
 
-// Alg. 2 line 2, floor division, raised to r_min.
+// Alg. 2's neighbourhood radius, floor division, raised to r_min.
 static int32_t radius_rule(int64_t slen, int64_t q, int64_t T, int32_t r_min) {
   int64_t num = slen - q + 1 - T, den = 2 * T + 2;
   int64_t r = num >= 0 ? num / den : -((-num + den - 1) / den);
@@ -111,11 +111,22 @@ struct mj_ctx {
   Buf in_bytes, in_offsets;  // staging for mj_join_host
   uint64_t n_part = 0, n_cand = 0, n_out = 0;
   // bit-planes written by the partition kernel for the verifier
-  mj_verify_config vcfg{MJ_VERIFY_KERNEL_AUTO, 0};
+  mj_verify_config vcfg{MJ_VERIFY_KERNEL_AUTO, 0, 0, 0};
+  // autotuned kernel per length bucket
+  bool tuned = false;
+  uint32_t tuned_kernel[kLenBuckets] = {};
+  uint32_t tuned_lanes[kLenBuckets] = {};
+  Buf branges;   // bucket counts [32] then ranges [64]
+  // CUDA graph of the plain verification stage
+  cudaGraphExec_t graph_exec = nullptr;
+  uint64_t graph_sig[12] = {};
+  uint64_t last_sig[12] = {};
+  uint64_t graph_launches = 0;
   // learned first-pass band: parameters P, Adam moments M and V, gradient G, loss
   Buf band;
   bool band_ready = false;
   uint32_t band_margin = 0, band_min_mult = 2;
+  bool band_gate_auto = false;   // set band_min_mult from the training data
   int band_step = 0;
   Buf feat_x, mult, run_start, parts, yhat, kband, vlist, vflags, voffs;
   bool have_features = false;
@@ -154,8 +165,9 @@ int readback(mj_ctx* c, const void* d_src, size_t bytes, cudaStream_t s) {
   return MJ_OK;
 }
 
+// A section's interval runs from its first start to its last stop in a call.
 void tstart(mj_ctx* c, int i, cudaStream_t s) {
-  if (c->timing) {
+  if (c->timing && !c->sec_used[i]) {
     cudaEventRecord(c->sec_ev[2 * i], s);
     c->sec_used[i] = true;
   }
@@ -407,7 +419,8 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
 // a8 on arbitrary pairs (rank codes from c->d).
 int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const uint32_t* d_i, const uint32_t* d_j,
            const uint32_t* d_k, uint64_t m, uint32_t K, uint32_t kmax, uint32_t* d_ed, bool count_cells,
-           cudaStream_t s, const uint32_t* order = nullptr) {
+           cudaStream_t s, const uint32_t* order = nullptr, const uint32_t* skip_kband = nullptr,
+           const uint32_t* range_lo = nullptr, const uint32_t* range_hi = nullptr, int kernel = -1, int lanes = -1) {
   const Derived& d = c->d;
   if (m == 0) return MJ_OK;
   if (kmax >= (1u << 16)) return MJ_ERR_UNSUPPORTED;
@@ -429,7 +442,7 @@ int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const ui
   MJ_CUDA_TRY(cudaMemsetAsync(c->dev_flags.p, 0, 64, s));
   MJ_TRY(c->small.reserve(64, s));
   if (!c->work_started) {
-    MJ_CUDA_TRY(cudaMemsetAsync(c->small.p, 0, 32, s));
+    MJ_CUDA_TRY(cudaMemsetAsync(c->small.p, 0, 48, s));
     c->work_started = true;
   }
   VerifyArgs a;
@@ -442,6 +455,10 @@ int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const ui
   a.pj = d_j;
   a.pk = d_k;
   a.order = order;
+  a.skip_kband = skip_kband;
+  a.range_lo = range_lo;
+  a.range_hi = range_hi;
+  a.skipped = skip_kband ? c->small.as<unsigned long long>() + 4 : nullptr;
   a.K = K;
   a.m = m;
   a.ed = d_ed;
@@ -449,8 +466,122 @@ int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const ui
   a.work = c->small.as<unsigned long long>() + 2;
   a.dev_flags = c->dev_flags.as<uint32_t>();
   tstart(c, 6, s);
-  MJ_TRY(launch_verify(a, PW, GW, kmax, c->small.as<unsigned long long>() + 1, s, (int)c->vcfg.kernel,
-                       (int)c->vcfg.lanes));
+  int kk = kernel >= 0 ? kernel : (int)c->vcfg.kernel;
+  int ll = lanes >= 0 ? lanes : (int)c->vcfg.lanes;
+  if (kk == MJ_VERIFY_KERNEL_TUNED) {
+    kk = MJ_VERIFY_KERNEL_AUTO;
+    ll = 0;
+  }
+  MJ_TRY(launch_verify(a, PW, GW, kmax, c->small.as<unsigned long long>() + 1, s, kk, ll));
+  tstop(c, 6, s);
+  return MJ_OK;
+}
+
+// Longest-first order of pairs (d_i, d_j): sorted work keys and the order.
+int pair_order(mj_ctx* c, const uint32_t* ci, const uint32_t* cj, const int64_t* d_offsets, uint64_t m,
+               const uint64_t** skeys, const uint32_t** order, cudaStream_t s) {
+  MJ_TRY(launch_work_keys(ci, cj, d_offsets, m, c->d.N, c->keys.as<uint64_t>(), c->idx.as<uint32_t>(), s));
+  bool oalt = false;
+  MJ_TRY(radix_sort_u64(c->keys.as<uint64_t>(), c->keys_alt.as<uint64_t>(), c->idx.as<uint32_t>(),
+                        c->idx_alt.as<uint32_t>(), m, 0, bits_for(c->d.N), c->sort_tmp.p, &oalt, s));
+  *skeys = oalt ? c->keys_alt.as<uint64_t>() : c->keys.as<uint64_t>();
+  *order = oalt ? c->idx_alt.as<uint32_t>() : c->idx.as<uint32_t>();
+  return MJ_OK;
+}
+
+int order_buffers(mj_ctx* c, uint64_t m, cudaStream_t s) {
+  MJ_TRY(c->keys.reserve(m * 8, s));
+  MJ_TRY(c->keys_alt.reserve(m * 8, s));
+  MJ_TRY(c->idx.reserve(m * 4, s));
+  MJ_TRY(c->idx_alt.reserve(m * 4, s));
+  MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(m), s));
+  MJ_TRY(c->branges.reserve(4 * (kLenBuckets + 2 * kLenBuckets) + 64, s));
+  return MJ_OK;
+}
+
+// Band-K verification of pairs (ci, cj) in longest-first order, as the
+// context's kernel choice says (TUNED: per length bucket, batched).
+int verify_ordered(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const uint32_t* ci,
+                   const uint32_t* cj, uint64_t m, uint32_t K, uint32_t* ed, cudaStream_t s) {
+  const uint64_t* skeys;
+  const uint32_t* order;
+  MJ_TRY(pair_order(c, ci, cj, d_offsets, m, &skeys, &order, s));
+  if (c->vcfg.kernel != MJ_VERIFY_KERNEL_TUNED || !c->tuned)
+    return verify(c, d_bytes, d_offsets, ci, cj, nullptr, m, K, K, ed, false, s, order);
+  uint32_t* counts = c->branges.as<uint32_t>();
+  uint32_t* ranges = counts + kLenBuckets;
+  MJ_TRY(launch_bucket_ranges(skeys, m, c->d.N, counts, ranges, s));
+  if (c->vcfg.batching == 1) {
+    for (int b = kLenBuckets - 1; b >= 0; --b)
+      MJ_TRY(verify(c, d_bytes, d_offsets, ci, cj, nullptr, m, K, K, ed, false, s, order, nullptr, ranges + 2 * b,
+                    ranges + 2 * b + 1, (int)c->tuned_kernel[b], (int)c->tuned_lanes[b]));
+    return MJ_OK;
+  }
+  // one launch per run of consecutive buckets (longest first) sharing a kernel
+  int b = kLenBuckets - 1;
+  while (b >= 0) {
+    int e = b;
+    while (e - 1 >= 0 && c->tuned_kernel[e - 1] == c->tuned_kernel[b] && c->tuned_lanes[e - 1] == c->tuned_lanes[b]) --e;
+    MJ_TRY(verify(c, d_bytes, d_offsets, ci, cj, nullptr, m, K, K, ed, false, s, order, nullptr, ranges + 2 * b,
+                  ranges + 2 * e + 1, (int)c->tuned_kernel[b], (int)c->tuned_lanes[b]));
+    b = e - 1;
+  }
+  return MJ_OK;
+}
+
+// verify_ordered, captured into a CUDA graph when the context asks for it and
+// replayed while its inputs (pointers, sizes, kernel plan) stay the same.  The
+// first call with new inputs runs uncaptured (it sizes every buffer), the
+// second captures, later ones replay.
+int verify_ordered_graph(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const uint32_t* ci,
+                         const uint32_t* cj, uint64_t m, uint32_t K, uint32_t* ed, cudaStream_t s) {
+  MJ_TRY(order_buffers(c, m, s));
+  // capture needs a stream of its own: the legacy and per-thread default
+  // streams run the stage uncaptured
+  const bool capturable = s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+  if (!c->vcfg.graph || !capturable) return verify_ordered(c, d_bytes, d_offsets, ci, cj, m, K, ed, s);
+  uint64_t plan = c->vcfg.kernel * 131u + c->vcfg.lanes * 7u + c->vcfg.batching;
+  if (c->tuned) {
+    for (int b = 0; b < kLenBuckets; ++b) plan = plan * 1000003u + c->tuned_kernel[b] * 64u + c->tuned_lanes[b];
+  }
+  const uint64_t sig[12] = {(uint64_t)d_bytes, (uint64_t)d_offsets, (uint64_t)ci, (uint64_t)cj, m, K,
+                            (uint64_t)ed, (uint64_t)c->planes.p, c->planes_pw, c->d.bits, plan,
+                            (uint64_t)c->small.p ^ (uint64_t)c->keys.p ^ (uint64_t)c->sort_tmp.p};
+  if (c->graph_exec && memcmp(sig, c->graph_sig, sizeof(sig)) == 0) {
+    tstart(c, 6, s);   // the verify section spans the replay
+    MJ_CUDA_TRY(cudaGraphLaunch(c->graph_exec, s));
+    tstop(c, 6, s);
+    c->launches_at_start -= c->graph_launches;   // kernels replayed by the graph
+    return MJ_OK;
+  }
+  if (memcmp(sig, c->last_sig, sizeof(sig)) != 0) {
+    memcpy(c->last_sig, sig, sizeof(sig));
+    return verify_ordered(c, d_bytes, d_offsets, ci, cj, m, K, ed, s);
+  }
+  if (c->graph_exec) {
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+  }
+  const bool timing = c->timing;
+  c->timing = false;   // no section events inside the graph
+  const uint64_t before = launch_count();
+  MJ_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+  const int st = verify_ordered(c, d_bytes, d_offsets, ci, cj, m, K, ed, s);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+  c->timing = timing;
+  if (st != MJ_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  MJ_CUDA_TRY(ce);
+  const cudaError_t ie = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  MJ_CUDA_TRY(ie);
+  c->graph_launches = launch_count() - before;
+  memcpy(c->graph_sig, sig, sizeof(sig));
+  tstart(c, 6, s);
+  MJ_CUDA_TRY(cudaGraphLaunch(c->graph_exec, s));
   tstop(c, 6, s);
   return MJ_OK;
 }
@@ -474,72 +605,67 @@ int verify_stage(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, ui
   const uint32_t* cj = c->cand_j.as<uint32_t>();
   MJ_TRY(c->ed.reserve(m * 4, s));
   MJ_TRY(c->small.reserve(64, s));
+  const bool want_x = (p->flags & MJ_FLAG_FEATURES) != 0;
   if (want_feat) {
-    MJ_TRY(c->mult.reserve(m * 4, s));
     MJ_TRY(c->parts.reserve((size_t)n * 4 + 16, s));
-    MJ_TRY(c->feat_x.reserve(m * 4 * kBandFeatures, s));
-    MJ_TRY(launch_multiplicity(c->run_start.as<uint32_t>(), m, c->stats.n_raw_pairs, c->mult.as<uint32_t>(), s));
     MJ_CUDA_TRY(cudaMemsetAsync(c->parts.p, 0, (size_t)n * 4, s));
     MJ_TRY(launch_partition_counts(c->anchor_sid.as<uint32_t>(), c->n_part, c->parts.as<uint32_t>(), s));
+  }
+  if (want_x) {
+    MJ_TRY(c->mult.reserve(m * 4, s));
+    MJ_TRY(c->feat_x.reserve(m * 4 * kBandFeatures, s));
+    MJ_TRY(launch_multiplicity(c->run_start.as<uint32_t>(), m, c->stats.n_raw_pairs, c->mult.as<uint32_t>(), s));
     MJ_TRY(launch_band_features(ci, cj, c->mult.as<uint32_t>(), c->parts.as<uint32_t>(), d_offsets, m, K, c->d.T,
                                 c->feat_x.as<float>(), s));
   }
-  // longest pairs first, so that the persistent verifier does not end on a
-  // tail of long pairs
-  MJ_TRY(c->keys.reserve(m * 8, s));
-  MJ_TRY(c->keys_alt.reserve(m * 8, s));
-  MJ_TRY(c->idx.reserve(m * 4, s));
-  MJ_TRY(c->idx_alt.reserve(m * 4, s));
-  MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(m), s));
-  MJ_TRY(launch_work_keys(ci, cj, d_offsets, m, c->d.N, c->keys.as<uint64_t>(), c->idx.as<uint32_t>(), s));
-  bool oalt = false;
-  MJ_TRY(radix_sort_u64(c->keys.as<uint64_t>(), c->keys_alt.as<uint64_t>(), c->idx.as<uint32_t>(),
-                        c->idx_alt.as<uint32_t>(), m, 0, bits_for(c->d.N), c->sort_tmp.p, &oalt, s));
-  const uint32_t* order = oalt ? c->idx_alt.as<uint32_t>() : c->idx.as<uint32_t>();
   uint32_t* ed = c->ed.as<uint32_t>();
   if (!learned) {
-    MJ_TRY(verify(c, d_bytes, d_offsets, ci, cj, nullptr, m, K, K, ed, false, s, order));
+    // longest pairs first, so that the persistent verifier does not end on a
+    // tail of long pairs
+    MJ_TRY(verify_ordered_graph(c, d_bytes, d_offsets, ci, cj, m, K, ed, s));
   } else {
     if (!c->band_ready) return MJ_ERR_STATE;
-    MJ_TRY(c->yhat.reserve(m * 4, s));
+    MJ_TRY(order_buffers(c, m, s));
+    const uint64_t* skeys;
+    const uint32_t* order;
+    MJ_TRY(pair_order(c, ci, cj, d_offsets, m, &skeys, &order, s));
     MJ_TRY(c->kband.reserve(m * 4, s));
     MJ_TRY(c->vflags.reserve(m * 4, s));
     MJ_TRY(c->voffs.reserve(m * 4 + 16, s));
     MJ_TRY(c->vlist.reserve(m * 4 + 16, s));
     MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(m), s));
-    MJ_TRY(launch_band_forward(c->band.as<float>(), c->feat_x.as<float>(), m, c->mult.as<uint32_t>(),
-                               c->band_min_mult, c->yhat.as<float>(), s));
-    MJ_TRY(launch_band_rule(c->yhat.as<float>(), ci, cj, d_offsets, m, K, c->band_margin, c->kband.as<uint32_t>(), s));
+    MJ_TRY(launch_band_fused(c->band.as<float>(), ci, cj, c->run_start.as<uint32_t>(), c->stats.n_raw_pairs,
+                             c->parts.as<uint32_t>(), d_offsets, m, K, c->d.T, c->band_margin, c->band_min_mult,
+                             c->kband.as<uint32_t>(), s));
     uint32_t* tot = c->voffs.as<uint32_t>() + m;
     uint64_t first = 0;
     int st = MJ_OK;
     const uint32_t wK = (K + 1 + 31) / 32;
-    for (uint32_t w = 1; w < wK; ++w) {
-      MJ_TRY(launch_bucket_flags(c->kband.as<uint32_t>(), order, m, K, w, c->vflags.as<uint32_t>(), s));
+    // first passes: one launch per group of band widths (exact word counts up
+    // to 8 words, power-of-two ranges beyond)
+    for (uint32_t wlo = 1; wlo < wK;) {
+      const uint32_t whi = std::min(wK, wK <= 8 ? wlo + 1 : 2 * wlo);
+      MJ_TRY(launch_bucket_flags(c->kband.as<uint32_t>(), order, m, K, wlo, whi, c->vflags.as<uint32_t>(), s));
       MJ_TRY(launch_exclusive_scan_u32(c->vflags.as<uint32_t>(), c->voffs.as<uint32_t>(), m, c->scan_tmp.p, tot, s));
       const uint64_t cnt = readback_u32(c, tot, s, &st);
       MJ_TRY(st);
-      if (!cnt) continue;
-      MJ_TRY(launch_compact_index(c->vflags.as<uint32_t>(), c->voffs.as<uint32_t>(), order, m,
-                                  c->vlist.as<uint32_t>(), s));
-      MJ_TRY(verify(c, d_bytes, d_offsets, ci, cj, c->kband.as<uint32_t>(), cnt, K, 32 * w - 1, ed, false, s,
-                    c->vlist.as<uint32_t>()));
-      first += cnt;
+      if (cnt) {
+        MJ_TRY(launch_compact_index(c->vflags.as<uint32_t>(), c->voffs.as<uint32_t>(), order, m,
+                                    c->vlist.as<uint32_t>(), s));
+        MJ_TRY(verify(c, d_bytes, d_offsets, ci, cj, c->kband.as<uint32_t>(), cnt, K, 32 * (whi - 1) - 1, ed, false,
+                      s, c->vlist.as<uint32_t>()));
+        first += cnt;
+      }
+      wlo = whi;
     }
-    MJ_TRY(launch_fallback_flags(c->kband.as<uint32_t>(), ed, order, m, K, c->vflags.as<uint32_t>(), s));
-    MJ_TRY(launch_exclusive_scan_u32(c->vflags.as<uint32_t>(), c->voffs.as<uint32_t>(), m, c->scan_tmp.p, tot, s));
-    const uint64_t cnt2 = readback_u32(c, tot, s, &st);
-    MJ_TRY(st);
-    if (cnt2) {
-      MJ_TRY(launch_compact_index(c->vflags.as<uint32_t>(), c->voffs.as<uint32_t>(), order, m,
-                                  c->vlist.as<uint32_t>(), s));
-      MJ_TRY(verify(c, d_bytes, d_offsets, ci, cj, nullptr, cnt2, K, K, ed, false, s, c->vlist.as<uint32_t>()));
-    }
-    const uint64_t rerun = cnt2 - (m - first);
-    c->stats.first_pass_settled = first - rerun;
-    c->stats.fallback_pairs = rerun;
+    // band K for every pair the first passes did not settle
+    MJ_TRY(verify(c, d_bytes, d_offsets, ci, cj, nullptr, m, K, K, ed, false, s, order, c->kband.as<uint32_t>()));
+    MJ_TRY(readback(c, c->small.as<unsigned long long>() + 4, 8, s));
+    const uint64_t settled = c->h_small[0];
+    c->stats.first_pass_settled = settled;
+    c->stats.fallback_pairs = first - settled;
   }
-  c->have_features = want_feat;
+  c->have_features = want_x;
   return launch_band_cells(ci, cj, d_offsets, m, K, c->small.as<unsigned long long>() + 3, s);
 }
 
@@ -640,19 +766,22 @@ void mj_destroy(mj_ctx* c) {
                  &c->rec_h61, &c->keys, &c->keys_alt, &c->idx, &c->idx_alt, &c->sort_tmp, &c->s_sid, &c->s_pos,
                  &c->s_slen, &c->s_len, &c->s_h61, &c->pair_count, &c->pair_off, &c->pairs, &c->pairs_alt,
                  &c->uflags, &c->uoffs, &c->cand_i, &c->cand_j, &c->planes, &c->ed, &c->eflags, &c->eoffs,
-                 &c->out_i, &c->out_j, &c->out_ed, &c->in_bytes, &c->in_offsets};
+                 &c->out_i, &c->out_j, &c->out_ed, &c->in_bytes, &c->in_offsets, &c->branges,
+                 &c->band, &c->feat_x, &c->mult, &c->run_start, &c->parts, &c->yhat, &c->kband, &c->vlist,
+                 &c->vflags, &c->voffs};
   for (Buf* b : bufs) b->release();
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : c->sec_ev)
     if (e) cudaEventDestroy(e);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->h_small) cudaFreeHost(c->h_small);
   delete c;
 }
 
 int mj_set_verify_config(mj_ctx* c, const mj_verify_config* cfg) {
   if (!c || !cfg) return MJ_ERR_ARG;
-  if (cfg->kernel > MJ_VERIFY_KERNEL_WAVEFRONT) return MJ_ERR_ARG;
+  if (cfg->kernel > MJ_VERIFY_KERNEL_TUNED || cfg->batching > 1 || cfg->graph > 1) return MJ_ERR_ARG;
   if (cfg->lanes && (cfg->lanes > 32 || (cfg->lanes & (cfg->lanes - 1)) || cfg->lanes < 2)) return MJ_ERR_ARG;
   c->vcfg = *cfg;
   return MJ_OK;
@@ -756,16 +885,100 @@ int mj_verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
   mj_params_default(&p, K);
   begin_call(c, false);
   MJ_TRY(derive(c, d_bytes, d_offsets, n, &p, s));
-  uint32_t kmax = K;
-  if (d_k) {
+  if (!d_k) {
+    // one band for every pair: longest first, with the context's kernel plan
+    if (m) MJ_TRY(verify_ordered_graph(c, d_bytes, d_offsets, d_i, d_j, m, K, d_ed, s));
+  } else {
     // the widest per-pair band sizes the kernel
     std::vector<uint32_t> hk(m);
     MJ_CUDA_TRY(cudaMemcpyAsync(hk.data(), d_k, m * 4, cudaMemcpyDeviceToHost, s));
     MJ_CUDA_TRY(cudaStreamSynchronize(s));
-    kmax = 0;
+    uint32_t kmax = 0;
     for (uint32_t v : hk) kmax = std::max(kmax, v);
+    MJ_TRY(verify(c, d_bytes, d_offsets, d_i, d_j, d_k, m, K, kmax, d_ed, true, s));
   }
-  MJ_TRY(verify(c, d_bytes, d_offsets, d_i, d_j, d_k, m, K, kmax, d_ed, true, s));
+  c->stats.n_launches = launch_count() - c->launches_at_start;
+  return MJ_OK;
+}
+
+int mj_autotune_verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const uint32_t* d_i,
+                       const uint32_t* d_j, uint64_t m, uint32_t K, uint32_t sample, void* stream,
+                       mj_autotune_report* rep) {
+  if (!c || !d_offsets || (m && (!d_i || !d_j))) return MJ_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = S(stream);
+  mj_params p;
+  mj_params_default(&p, K);
+  begin_call(c, false);
+  MJ_TRY(derive(c, d_bytes, d_offsets, n, &p, s));
+  if (rep) memset(rep, 0, sizeof(*rep));
+  // candidates: the diagonal kernel when its band fits 8 words, then the
+  // wavefront with 1x, 2x, 4x ... the fewest lanes
+  uint32_t ck[MJ_TUNE_CANDIDATES], cl[MJ_TUNE_CANDIDATES], nc = 0;
+  if (verify_words_for(K) <= 8) {
+    ck[nc] = MJ_VERIFY_KERNEL_DIAGONAL;
+    cl[nc++] = 0;
+  }
+  for (int lanes = wave_lanes_for(K); lanes <= 32 && nc < MJ_TUNE_CANDIDATES; lanes *= 2) {
+    ck[nc] = MJ_VERIFY_KERNEL_WAVEFRONT;
+    cl[nc++] = (uint32_t)lanes;
+  }
+  if (rep) {
+    rep->n_candidates = nc;
+    for (uint32_t k = 0; k < nc; ++k) {
+      rep->cand_kernel[k] = ck[k];
+      rep->cand_lanes[k] = cl[k];
+    }
+  }
+  for (int b = 0; b < kLenBuckets; ++b) {
+    c->tuned_kernel[b] = MJ_VERIFY_KERNEL_AUTO;
+    c->tuned_lanes[b] = 0;
+  }
+  c->tuned = true;
+  if (!m) return MJ_OK;
+  MJ_TRY(order_buffers(c, m, s));
+  MJ_TRY(c->ed.reserve(m * 4, s));
+  const uint64_t* skeys;
+  const uint32_t* order;
+  MJ_TRY(pair_order(c, d_i, d_j, d_offsets, m, &skeys, &order, s));
+  uint32_t* counts = c->branges.as<uint32_t>();
+  uint32_t* ranges = counts + kLenBuckets;
+  uint32_t* trial = ranges + 2 * kLenBuckets;   // [lo, hi) of the sample being timed
+  MJ_TRY(launch_bucket_ranges(skeys, m, c->d.N, counts, ranges, s));
+  uint32_t h[3 * kLenBuckets];
+  MJ_CUDA_TRY(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, s));
+  MJ_CUDA_TRY(cudaStreamSynchronize(s));
+  const uint32_t smp = sample ? sample : 4096;
+  for (int b = 0; b < kLenBuckets; ++b) {
+    const uint32_t cnt = h[b];
+    if (rep) rep->count[b] = cnt;
+    if (!cnt) continue;
+    const uint32_t lo = h[kLenBuckets + 2 * b];
+    const uint32_t hi = std::min(h[kLenBuckets + 2 * b + 1], lo + smp);
+    const uint32_t r[2] = {lo, hi};
+    MJ_CUDA_TRY(cudaMemcpyAsync(trial, r, sizeof(r), cudaMemcpyHostToDevice, s));
+    float best = 0.f;
+    for (uint32_t k = 0; k < nc; ++k) {
+      for (int rep_i = 0; rep_i < 2; ++rep_i) {   // the first run warms the caches
+        MJ_CUDA_TRY(cudaEventRecord(c->ev[0], s));
+        MJ_TRY(verify(c, d_bytes, d_offsets, d_i, d_j, nullptr, m, K, K, c->ed.as<uint32_t>(), false, s, order,
+                      nullptr, trial, trial + 1, (int)ck[k], (int)cl[k]));
+        MJ_CUDA_TRY(cudaEventRecord(c->ev[1], s));
+      }
+      MJ_CUDA_TRY(cudaEventSynchronize(c->ev[1]));
+      const float ms = elapsed(c->ev[0], c->ev[1]);
+      if (rep) rep->ms[b][k] = ms;
+      if (k == 0 || ms < best) {
+        best = ms;
+        c->tuned_kernel[b] = ck[k];
+        c->tuned_lanes[b] = cl[k];
+      }
+    }
+    if (rep) {
+      rep->kernel[b] = c->tuned_kernel[b];
+      rep->lanes[b] = c->tuned_lanes[b];
+    }
+  }
   c->stats.n_launches = launch_count() - c->launches_at_start;
   return MJ_OK;
 }
@@ -865,7 +1078,8 @@ int mj_band_init(mj_ctx* c, uint64_t seed, uint32_t margin, uint32_t min_multipl
   MJ_CUDA_TRY(cudaMemcpy(c->band.p, w.data(), sizeof(float) * kBandParams, cudaMemcpyHostToDevice));
   MJ_CUDA_TRY(cudaMemset(c->band.as<float>() + kBandParams, 0, sizeof(float) * 2 * kBandParams));
   c->band_margin = margin;
-  c->band_min_mult = min_multiplicity;
+  c->band_min_mult = min_multiplicity ? min_multiplicity : 1;
+  c->band_gate_auto = min_multiplicity == 0;
   c->band_step = 0;
   c->band_ready = true;
   return MJ_OK;
@@ -895,6 +1109,29 @@ int mj_band_train(mj_ctx* c, const float* d_x, const uint32_t* d_ed, uint64_t m,
   MJ_CUDA_TRY(cudaMemcpyAsync(&loss, L, sizeof(float), cudaMemcpyDeviceToHost, s));
   MJ_CUDA_TRY(cudaStreamSynchronize(s));
   if (final_loss) *final_loss = loss;
+  if (c->band_gate_auto) {
+    // gate = 1st percentile of the multiplicity of the samples a narrower
+    // first band could settle
+    unsigned int* hist = reinterpret_cast<unsigned int*>(G);   // gradient scratch, free after training
+    MJ_TRY(launch_gate_hist(d_x, d_ed, m, K, hist, s));
+    unsigned int h[256];
+    MJ_CUDA_TRY(cudaMemcpyAsync(h, hist, sizeof(h), cudaMemcpyDeviceToHost, s));
+    MJ_CUDA_TRY(cudaStreamSynchronize(s));
+    uint64_t tot = 0;
+    for (unsigned int v : h) tot += v;
+    uint32_t gate = 1;
+    if (tot) {
+      uint64_t acc = 0;
+      for (int b = 0; b < 256; ++b) {
+        acc += h[b];
+        if (acc * 100 >= tot) {
+          gate = b < 1 ? 1 : (uint32_t)b;
+          break;
+        }
+      }
+    }
+    c->band_min_mult = gate;
+  }
   c->stats.n_launches = launch_count() - c->launches_at_start;
   return MJ_OK;
 }

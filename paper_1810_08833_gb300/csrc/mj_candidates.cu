@@ -1,6 +1,6 @@
 // Steps a1 and a5-a7: parameter statistics, grouping of equal partitions,
-// pair emission under the length and position filters of Alg. 3 (lines 7-8),
-// and deduplication of the candidate pairs (Alg. 3 line 20).
+// pair emission under the length and position filters of Alg. 3,
+// and deduplication of the candidate pairs (the last step of Alg. 3's join).
 //
 // The paper's sequential hash join visits strings in length order and evicts
 // bucket entries whose length differs by more than K.  Its result is the set
@@ -216,11 +216,12 @@ __global__ void partition_counts_kernel(const uint32_t* __restrict__ sid, uint64
 }
 
 __global__ void bucket_flags_kernel(const uint32_t* __restrict__ kband, const uint32_t* __restrict__ order, uint64_t m,
-                                    uint32_t K, uint32_t w, uint32_t* __restrict__ flags) {
+                                    uint32_t K, uint32_t wlo, uint32_t whi, uint32_t* __restrict__ flags) {
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t u = order ? order[q] : q;
     const uint32_t k = kband[u];
-    flags[q] = (k < K && (k + 1 + 31) / 32 == w) ? 1u : 0u;
+    const uint32_t kw = (k + 1 + 31) / 32;
+    flags[q] = (k < K && kw >= wlo && kw < whi) ? 1u : 0u;
   }
 }
 
@@ -258,6 +259,31 @@ __global__ void band_cells_kernel(const uint32_t* __restrict__ ci, const uint32_
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
+__device__ __forceinline__ uint32_t len_bucket(uint64_t n) { return n <= 1 ? 0u : 63u - (uint32_t)__clzll(n); }
+
+__global__ void bucket_hist_kernel(const uint64_t* __restrict__ keys, uint64_t m, uint64_t N,
+                                   uint32_t* __restrict__ counts) {
+  __shared__ uint32_t h[kLenBuckets];
+  if (threadIdx.x < kLenBuckets) h[threadIdx.x] = 0;
+  __syncthreads();
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t b = len_bucket(N - keys[q]);
+    atomicAdd(&h[b < kLenBuckets ? b : kLenBuckets - 1], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < kLenBuckets && h[threadIdx.x]) atomicAdd(&counts[threadIdx.x], h[threadIdx.x]);
+}
+
+// longest first: bucket b starts after all pairs of the buckets above it
+__global__ void bucket_scan_kernel(const uint32_t* __restrict__ counts, uint32_t* __restrict__ ranges) {
+  uint32_t run = 0;
+  for (int b = kLenBuckets - 1; b >= 0; --b) {
+    ranges[2 * b] = run;
+    run += counts[b];
+    ranges[2 * b + 1] = run;
+  }
 }
 
 unsigned grid_for(uint64_t n, int threads = 256) {
@@ -340,6 +366,18 @@ int launch_compact_pairs(const uint64_t* sorted, const uint32_t* flags, const ui
   return MJ_OK;
 }
 
+int launch_bucket_ranges(const uint64_t* sorted_keys, uint64_t m, uint64_t N, uint32_t* counts, uint32_t* ranges,
+                         cudaStream_t s) {
+  MJ_CUDA_TRY(cudaMemsetAsync(counts, 0, kLenBuckets * sizeof(uint32_t), s));
+  if (m) {
+    bucket_hist_kernel<<<grid_for(m), 256, 0, s>>>(sorted_keys, m, N, counts);
+    MJ_KERNEL_DONE();
+  }
+  bucket_scan_kernel<<<1, 1, 0, s>>>(counts, ranges);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
 int launch_work_keys(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m, uint64_t N,
                      uint64_t* keys, uint32_t* vals, cudaStream_t s) {
   if (!m) return MJ_OK;
@@ -362,10 +400,10 @@ int launch_partition_counts(const uint32_t* anchor_sid, uint64_t n_anchor, uint3
   return MJ_OK;
 }
 
-int launch_bucket_flags(const uint32_t* kband, const uint32_t* order, uint64_t m, uint32_t K, uint32_t w,
-                        uint32_t* flags, cudaStream_t s) {
+int launch_bucket_flags(const uint32_t* kband, const uint32_t* order, uint64_t m, uint32_t K, uint32_t wlo,
+                        uint32_t whi, uint32_t* flags, cudaStream_t s) {
   if (!m) return MJ_OK;
-  bucket_flags_kernel<<<grid_for(m), 256, 0, s>>>(kband, order, m, K, w, flags);
+  bucket_flags_kernel<<<grid_for(m), 256, 0, s>>>(kband, order, m, K, wlo, whi, flags);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }

@@ -41,6 +41,7 @@ enum : uint32_t {
   FLAG_BOUNDS = 1u << 0,       // an index left its buffer (access skipped)
   FLAG_TIMEOUT = 1u << 1,      // a bounded wait gave up
   FLAG_CAPACITY = 1u << 2,     // an output buffer was too small (write skipped)
+  FLAG_LENGTH = 1u << 3,       // a string too long for 32-bit column indexing (pair rejected)
 };
 
 void set_last_cuda_error(cudaError_t e, const char* expr, const char* file, int line);
@@ -162,6 +163,10 @@ struct VerifyArgs {
   const uint32_t* pj;
   const uint32_t* pk;        // nullable per-pair band
   const uint32_t* order;     // nullable: pair indices in the order to verify them
+  const uint32_t* skip_kband; // nullable: skip pair t when ed[t] <= skip_kband[t] < K (already settled)
+  const uint32_t* range_lo;  // nullable: with range_hi, process order positions [*range_lo, *range_hi) only
+  const uint32_t* range_hi;
+  unsigned long long* skipped; // nullable: number of pairs skipped that way
   uint32_t K;
   uint64_t m;
   uint32_t* ed;
@@ -179,6 +184,13 @@ int launch_verify(const VerifyArgs& a, uint64_t plane_words, uint32_t guard_word
                   unsigned long long* next, cudaStream_t s, int kernel = MJ_VERIFY_KERNEL_AUTO, int lanes = 0);
 int wave_lanes_for(uint32_t kmax);
 
+// length buckets of the verification order (bucket of a pair: floor(log2 of
+// its shorter length), 0..31); keys are the sorted work keys N - n, so the
+// buckets are contiguous, longest first.  ranges[2b], ranges[2b+1] = [start,
+// end) of bucket b.
+constexpr int kLenBuckets = 32;
+int launch_bucket_ranges(const uint64_t* sorted_keys, uint64_t m, uint64_t N, uint32_t* counts, uint32_t* ranges,
+                         cudaStream_t s);
 // verification order: candidate indices sorted by key = N - min length
 int launch_work_keys(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m, uint64_t N,
                      uint64_t* keys, uint32_t* vals, cudaStream_t s);
@@ -203,6 +215,10 @@ int launch_band_grad(const float* P, const float* X, const float* Y, const uint3
                      uint64_t batch, uint64_t seed, float tau, float* grad, float* loss, cudaStream_t s);
 int launch_band_adam(float* P, const float* G, float* M, float* V, float lr, float b1, float b2, float eps, int step,
                      cudaStream_t s);
+int launch_band_fused(const float* P, const uint32_t* ci, const uint32_t* cj, const uint32_t* run_start, uint64_t raw,
+                      const uint32_t* parts, const int64_t* offsets, uint64_t m, uint32_t K, uint32_t T, uint32_t margin,
+                      uint32_t min_mult, uint32_t* kband, cudaStream_t s);
+int launch_gate_hist(const float* X, const uint32_t* ed, uint64_t m, uint32_t K, unsigned int* hist, cudaStream_t s);
 int launch_band_rule(const float* yhat, const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m,
                      uint32_t K, uint32_t margin, uint32_t* kband, cudaStream_t s);
 
@@ -212,8 +228,8 @@ int launch_multiplicity(const uint32_t* run_start, uint64_t nc, uint64_t raw, ui
 int launch_partition_counts(const uint32_t* anchor_sid, uint64_t n_anchor, uint32_t* parts, cudaStream_t s);
 // subset lists for the two verification passes
 // (order nullable: flags[q] refer to candidate order[q]; the list holds candidate ids)
-int launch_bucket_flags(const uint32_t* kband, const uint32_t* order, uint64_t m, uint32_t K, uint32_t w,
-                        uint32_t* flags, cudaStream_t s);
+int launch_bucket_flags(const uint32_t* kband, const uint32_t* order, uint64_t m, uint32_t K, uint32_t wlo,
+                        uint32_t whi, uint32_t* flags, cudaStream_t s);
 int launch_fallback_flags(const uint32_t* kband, const uint32_t* ed, const uint32_t* order, uint64_t m, uint32_t K,
                           uint32_t* flags, cudaStream_t s);
 int launch_compact_index(const uint32_t* flags, const uint32_t* offs, const uint32_t* order, uint64_t m, uint32_t* out,

@@ -238,6 +238,131 @@ __global__ void band_rule_kernel(const float* __restrict__ yhat, const uint32_t*
   }
 }
 
+// Network output for one feature row (weights in shared memory).
+__device__ __forceinline__ float mlp_eval(const float* s, const float* xf) {
+  float h1[H];
+#pragma unroll
+  for (int a = 0; a < H; ++a) {
+    float zz = s[OFF_B1 + a];
+#pragma unroll
+    for (int f = 0; f < F; ++f) zz = fmaf(s[OFF_W1 + a * F + f], xf[f], zz);
+    h1[a] = relu(zz);
+  }
+  float y = s[OFF_B3];
+#pragma unroll 4
+  for (int cc = 0; cc < H; ++cc) {
+    float zz = s[OFF_B2 + cc];
+#pragma unroll
+    for (int a = 0; a < H; ++a) zz = fmaf(s[OFF_W2 + cc * H + a], h1[a], zz);
+    y = fmaf(s[OFF_W3 + cc], relu(zz), y);
+  }
+  return y;
+}
+
+constexpr int kQueue = 128;   // threads per block of the fused band kernel
+
+// Features, network and band rule in one pass over the candidates (learned
+// joins).  Candidates from fewer than min_mult matched partition pairs keep
+// band K without running the network; the others are gathered in a block
+// queue and evaluated 128 at a time, so a sparse gate does not leave lanes
+// idle during the network.
+__global__ void __launch_bounds__(kQueue) band_fused_kernel(const float* __restrict__ P, const uint32_t* __restrict__ ci,
+                                                            const uint32_t* __restrict__ cj,
+                                                            const uint32_t* __restrict__ run_start, uint64_t raw,
+                                                            const uint32_t* __restrict__ parts,
+                                                            const int64_t* __restrict__ offsets, uint64_t m, uint32_t K,
+                                                            uint32_t T, uint32_t margin, uint32_t min_mult,
+                                                            uint32_t* __restrict__ kband) {
+  __shared__ float s[kBandParams];
+  __shared__ uint32_t q_u[2 * kQueue];
+  __shared__ uint32_t q_c[2 * kQueue];
+  __shared__ uint32_t qn;
+  for (int i = threadIdx.x; i < kBandParams; i += blockDim.x) s[i] = P[i];
+  if (threadIdx.x == 0) qn = 0;
+  __syncthreads();
+  const uint32_t wK = (K + 1 + 31) / 32;
+  auto evaluate = [&](uint64_t u, uint32_t c) {
+    const uint32_t x = ci[u], z = cj[u];
+    const int64_t lx = offsets[x + 1] - offsets[x], lz = offsets[z + 1] - offsets[z];
+    const uint32_t d0 = (uint32_t)(lx > lz ? lx - lz : lz - lx);
+    const float n = (float)(lx < lz ? lx : lz);
+    const float pa = (float)parts[x], pb = (float)parts[z];
+    const float pmin = fminf(pa, pb) > 1.f ? fminf(pa, pb) : 1.f;
+    const float t1 = (float)T + 1.f;
+    const float xf[F] = {log2f(1.f + n) / 16.f, (float)d0 / (float)(K ? K : 1), (float)c / t1, pa / t1, pb / t1,
+                         (float)c / pmin, log2f(1.f + (float)c) / 8.f, (float)K / (float)(K + 100)};
+    const float y = mlp_eval(s, xf);
+    uint32_t kb = K;
+    if (y == y && y < 1.f) {
+      const float want = ceilf(fmaxf(y, 0.f) * (float)K) + (float)margin;
+      uint32_t kw = want > (float)K ? K : (uint32_t)want;
+      if (kw < d0) kw = d0;
+      const uint32_t w = (kw + 1 + 31) / 32;
+      if (w < wK) kb = 32 * w - 1;
+    }
+    kband[u] = kb;
+  };
+  const uint64_t stride = (uint64_t)gridDim.x * kQueue;
+  for (uint64_t base = (uint64_t)blockIdx.x * kQueue; base < m; base += stride) {
+    const uint64_t u = base + threadIdx.x;
+    if (u < m) {
+      const uint64_t e = u + 1 < m ? run_start[u + 1] : raw;
+      const uint32_t c = (uint32_t)(e - run_start[u]);
+      kband[u] = K;
+      if (c >= min_mult) {
+        const uint32_t slot = atomicAdd(&qn, 1u);
+        q_u[slot] = (uint32_t)u;
+        q_c[slot] = c;
+      }
+    }
+    __syncthreads();
+    const uint32_t n_q = qn;
+    const bool last = base + stride >= m;
+    if (n_q >= kQueue || (last && n_q > 0)) {
+      // evaluate the first min(n_q, kQueue) entries, keep the rest queued
+      const uint32_t take = n_q < kQueue ? n_q : kQueue;
+      if (threadIdx.x < take) evaluate(q_u[threadIdx.x], q_c[threadIdx.x]);
+      __syncthreads();
+      const uint32_t left = n_q - take;
+      const bool mv = threadIdx.x < left;
+      uint32_t qa = 0, qb = 0;
+      if (mv) {
+        qa = q_u[take + threadIdx.x];
+        qb = q_c[take + threadIdx.x];
+      }
+      __syncthreads();
+      if (mv) {
+        q_u[threadIdx.x] = qa;
+        q_c[threadIdx.x] = qb;
+      }
+      if (threadIdx.x == 0) qn = left;
+      __syncthreads();
+      if (last && left > 0) {
+        if (threadIdx.x < left) evaluate(q_u[threadIdx.x], q_c[threadIdx.x]);
+        __syncthreads();
+        if (threadIdx.x == 0) qn = 0;
+        __syncthreads();
+      }
+    }
+  }
+}
+
+// Gate for the learned band from training samples: the 1st percentile of the
+// multiplicity c (recovered from feature 6 = log2(1+c)/8) among samples whose
+// band-K result fits a band narrower than K's word count, written to *out.
+__global__ void gate_hist_kernel(const float* __restrict__ X, const uint32_t* __restrict__ ed, uint64_t m, uint32_t K,
+                                 unsigned int* __restrict__ hist) {
+  const uint32_t wK = (K + 1 + 31) / 32;
+  const uint32_t kmax1 = wK > 1 ? 32 * (wK - 1) - 1 : 0;
+  for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < m; u += (uint64_t)gridDim.x * blockDim.x) {
+    if (wK <= 1 || ed[u] > kmax1) continue;
+    const float c = exp2f(8.f * X[u * F + 6]) - 1.f;
+    uint32_t ci = (uint32_t)(c + 0.5f);
+    if (ci > 255) ci = 255;
+    atomicAdd(hist + ci, 1u);
+  }
+}
+
 unsigned grid1(uint64_t n, int threads) {
   uint64_t g = (n + threads - 1) / threads;
   uint64_t cap = (uint64_t)kNumSMsHint * 16;
@@ -280,6 +405,24 @@ int launch_band_adam(float* P, const float* G, float* M, float* V, float lr, flo
                      cudaStream_t s) {
   const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
   adam_kernel<<<(kBandParams + 255) / 256, 256, 0, s>>>(P, G, M, V, lr, b1, b2, eps, c1, c2);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
+int launch_band_fused(const float* P, const uint32_t* ci, const uint32_t* cj, const uint32_t* run_start, uint64_t raw,
+                      const uint32_t* parts, const int64_t* offsets, uint64_t m, uint32_t K, uint32_t T, uint32_t margin,
+                      uint32_t min_mult, uint32_t* kband, cudaStream_t s) {
+  if (!m) return MJ_OK;
+  band_fused_kernel<<<grid1(m, kQueue), kQueue, 0, s>>>(P, ci, cj, run_start, raw, parts, offsets, m, K, T, margin,
+                                                       min_mult, kband);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
+int launch_gate_hist(const float* X, const uint32_t* ed, uint64_t m, uint32_t K, unsigned int* hist, cudaStream_t s) {
+  MJ_CUDA_TRY(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned int), s));
+  if (!m) return MJ_OK;
+  gate_hist_kernel<<<grid1(m, 256), 256, 0, s>>>(X, ed, m, K, hist);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }

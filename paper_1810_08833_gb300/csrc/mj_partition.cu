@@ -48,7 +48,7 @@ __device__ __forceinline__ uint32_t string_of(const int64_t* __restrict__ off, u
   return lo;
 }
 
-// Alg. 2 line 2 with floor division and the r_min clamp.
+// Alg. 2's neighbourhood radius with floor division and the r_min clamp.
 __device__ __forceinline__ int32_t radius_of(int64_t slen, int32_t q, int32_t T, int32_t r_min) {
   int64_t num = slen - q + 1 - T, den = 2 * (int64_t)T + 2;
   int64_t r = num >= 0 ? num / den : -((-num + den - 1) / den);

@@ -1,7 +1,7 @@
 // Device-wide exclusive scans and an LSD radix sort of 64-bit keys with
 // optional 32-bit values: the sorting primitives behind grouping the
 // partition records (Alg. 3's hash join) and deduplicating candidate pairs
-// (Alg. 3 line 20).
+// (the last step of Alg. 3's join).
 #include "mj_internal.cuh"
 
 namespace mj {

@@ -91,6 +91,10 @@ extern "C" int mj_verify_static(const uint8_t* d_bytes, const int64_t* d_offsets
   a.pj = d_j;
   a.pk = nullptr;
   a.order = nullptr;
+  a.skip_kband = nullptr;
+  a.range_lo = nullptr;
+  a.range_hi = nullptr;
+  a.skipped = nullptr;
   a.K = K;
   a.m = m;
   a.ed = d_ed;

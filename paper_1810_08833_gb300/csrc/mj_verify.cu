@@ -283,10 +283,12 @@ template <int W, int P>
 __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t PW, uint32_t GW,
                                                           unsigned long long* __restrict__ next) {
   const int lane = threadIdx.x & 31;
+  const uint64_t q_lo = a.range_lo ? *a.range_lo : 0;
+  const uint64_t q_hi = a.range_hi ? *a.range_hi : a.m;
   PairState<W, P> st;
   bool active = false;
   bool more = true;
-  uint64_t cells = 0, work = 0;
+  uint64_t cells = 0, work = 0, nskip = 0;
   while (true) {
     // lanes without a pair fetch the next indices
     const bool need = !active && more;
@@ -297,24 +299,30 @@ __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t
       if (lane == leader) base = atomicAdd(next, (unsigned long long)__popc(nmask));
       base = __shfl_sync(0xffffffffu, base, leader);
       if (need) {
-        const uint64_t q = base + __popc(nmask & ((1u << lane) - 1u));
-        if (q >= a.m) {
+        const uint64_t q = q_lo + base + __popc(nmask & ((1u << lane) - 1u));
+        if (q >= q_hi) {
           more = false;
         } else {
           const uint64_t t = a.order ? a.order[q] : q;
-          uint32_t res;
-          if (a.cells) {
-            const uint32_t x = a.pi[t], y = a.pj[t];
-            if (x < a.n_strings && y < a.n_strings) {
-              const int64_t lx = __ldg(a.offsets + x + 1) - __ldg(a.offsets + x);
-              const int64_t ly = __ldg(a.offsets + y + 1) - __ldg(a.offsets + y);
-              cells += band_cells(lx > ly ? lx : ly, lx > ly ? ly : lx, a.K);
+          // a pair the first pass already decided needs nothing: the lane
+          // stays idle and fetches again at the next iteration
+          const bool settled = a.skip_kband && a.skip_kband[t] < a.K && a.ed[t] <= a.skip_kband[t];
+          nskip += settled ? 1 : 0;
+          if (!settled) {
+            if (a.cells) {
+              const uint32_t x = a.pi[t], y = a.pj[t];
+              if (x < a.n_strings && y < a.n_strings) {
+                const int64_t lx = __ldg(a.offsets + x + 1) - __ldg(a.offsets + x);
+                const int64_t ly = __ldg(a.offsets + y + 1) - __ldg(a.offsets + y);
+                cells += band_cells(lx > ly ? lx : ly, lx > ly ? ly : lx, a.K);
+              }
             }
-          }
-          if (pair_init<W, P>(st, a, PW, GW, t, &res)) {
-            active = true;
-          } else {
-            a.ed[t] = res;
+            uint32_t res;
+            if (pair_init<W, P>(st, a, PW, GW, t, &res)) {
+              active = true;
+            } else {
+              a.ed[t] = res;
+            }
           }
         }
       }
@@ -339,6 +347,10 @@ __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t
     for (int o = 16; o > 0; o >>= 1) work += __shfl_down_sync(0xffffffffu, work, o);
     if (lane == 0 && work) atomicAdd(a.work, (unsigned long long)work);
   }
+  if (a.skipped) {
+    for (int o = 16; o > 0; o >>= 1) nskip += __shfl_down_sync(0xffffffffu, nskip, o);
+    if (lane == 0 && nskip) atomicAdd(a.skipped, (unsigned long long)nskip);
+  }
 }
 
 // ---------------------------------------------------------------- wide bands
@@ -359,182 +371,260 @@ __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t
 // D of its bottom row; the bottom row of the block holding row m at column n
 // gives D[m][n], and the block holding row j + d0 at column j gives the
 // diagonal lower bound used for the early exit.
-constexpr int kWaveCheck = 8;   // steps between early-exit votes
+constexpr int kWaveSteps = 16;   // wavefront steps between refills and votes (unrolled)
+
+// Each lane publishes one word per wavefront step for the lane holding the
+// next block of rows:
+//   bit 31      the block's bottom row gained +1 in this column (hout = +1)
+//   bits 1..30  D at the block's bottom row in this column (the score)
+//   bit 0       hout = -1
+// The next lane reads it only in the columns that block b - 1 shares with
+// block b; elsewhere the top row's delta is kIdle, +1 (the band's edge).
+constexpr uint32_t kIdle = 0x80000000u;
+constexpr int32_t kDeadU = -0x40000000;   // step offset of a lane without a block
+constexpr uint32_t kMaxLen = 1u << 27;     // scores must fit bits 1..30
+
+template <int P>
+__device__ __forceinline__ void wave_load_bits(const VerifyArgs& a, uint64_t PW, uint64_t pos, uint32_t (&v)[P],
+                                               bool reverse) {
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const uint32_t lo = p < (int)a.bits ? __ldg(a.planes + (uint64_t)p * PW + (pos >> 5)) : 0u;
+    const uint32_t hi = p < (int)a.bits ? __ldg(a.planes + (uint64_t)p * PW + (pos >> 5) + 1) : 0u;
+    const uint32_t x = __funnelshift_r(lo, hi, (uint32_t)(pos & 31));
+    v[p] = reverse ? __brev(x) : x;
+  }
+}
+
+// One column of a 32-row block (Myers' step in Hyyro's formulation).  wv
+// carries the horizontal delta entering the top row (bit 31: +1, bit 0: -1,
+// neither: 0); B's symbol is bit 31 of bw[] (consumed, shifted out); T's
+// score bits (1..30) follow the bottom row; Ph keeps the bottom row's +1 in
+// bit 31 and hn is its -1.  Bit extraction, shifts and disjoint ORs are
+// written as integer multiply-adds, which the FMA pipe can take: the logic
+// ops already fill the ALU pipe.
+template <int P>
+__device__ __forceinline__ void wave_column(const uint32_t (&pa)[P], uint32_t (&bw)[P], uint32_t wv, uint32_t& Pv,
+                                            uint32_t& Mv, uint32_t& T, uint32_t& Ph, uint32_t& hn) {
+  uint32_t Eq = 0xffffffffu;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const uint32_t xb = (uint32_t)__mulhi((int32_t)bw[p], 1);   // B's bit p broadcast (sign of bw)
+    Eq &= ~(pa[p] ^ xb);
+    bw[p] *= 2u;
+  }
+  const uint32_t hin_neg = wv & 1u;
+  const uint32_t hin_pos = __umulhi(wv, 2u);
+  const uint32_t Xv = Eq | Mv;
+  const uint32_t Eh = Eq | hin_neg;
+  const uint32_t Xh = (((Eh & Pv) + Pv) ^ Pv) | Eh;
+  Ph = Mv | ~(Xh | Pv);
+  const uint32_t Mh = Pv & Xh;
+  hn = __umulhi(Mh, 2u);
+  T = T + 2u * __umulhi(Ph, 2u) - 2u * hn;
+  const uint32_t Ph1 = Ph * 2u + hin_pos;   // (Ph << 1) | hin > 0
+  const uint32_t Mh1 = Mh * 2u + hin_neg;   // (Mh << 1) | hin < 0
+  Pv = Mh1 | ~(Xv | Ph1);
+  Mv = Ph1 & Xv;
+}
 
 template <int G, int P>
-__global__ void __launch_bounds__(128) verify_wave_kernel(VerifyArgs a, uint64_t PW, uint32_t GW,
+__global__ void __launch_bounds__(128, P <= 2 ? 8 : 1) verify_wave_kernel(VerifyArgs a, uint64_t PW, uint32_t GW,
                                                           unsigned long long* __restrict__ next) {
   const int lane = threadIdx.x & 31;
   const int gl = lane & (G - 1);
   const int gbase = lane - gl;
   const uint32_t gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
   const int prev_lane = gbase + ((gl + G - 1) & (G - 1));
+  const uint64_t q_lo = a.range_lo ? *a.range_lo : 0;
+  const uint64_t q_hi = a.range_hi ? *a.range_hi : a.m;
   // pair state (identical in the G lanes of a group)
   bool has = false, more = true;
   uint64_t t = 0;
   uint32_t k = 0;
-  int64_t oA = 0, oB = 0, m = 0, n = 0, d0 = 0, s = 0, s_end = 0;
-  int32_t dlo = 0, dhi = 0, bm = 0;
-  // block state (this lane)
-  int32_t b = 0;
+  int64_t oA = 0, oB = 0;
+  int32_t m = 0, n = 0, d0 = 0, dlo = 0, dhi = 0, bm = 0;
+  int32_t sbase = 0;   // wavefront steps done on the pair
+  // block state (this lane): block b runs at the steps where 0 <= u <= span
+  // (u counts up by one per step); block b - 1 computed the same column one
+  // step earlier while u <= u_valid; diagonal d0 crosses it where
+  // 0 <= u + dg < 32
+  int32_t b = 0, u = kDeadU, span = 0, u_valid = -1, dg = 0x40000000;
+  uint32_t T = 0;   // score << 1
   uint32_t Pv = 0, Mv = 0;
   uint32_t pa[P], bw[P];
-  int64_t bw_col = 0;
-  int32_t score = 0;
-  // what this lane produced at the previous step: tag = block << 2 | (hout + 1)
-  int32_t pub_tag = -1, pub_score = 0;
-  uint64_t work = 0, cells = 0;
+  uint32_t pub = kIdle;
+  bool done = false, reject = false;
+  int32_t result = 0;
+  uint64_t work = 0, cells = 0, nskip = 0;
+#pragma unroll
+  for (int p = 0; p < P; ++p) pa[p] = bw[p] = 0u;
+
+  // Take block nb after step s.  Its columns are [jf, jl]; block nb computes
+  // column j at step j + nb.  Blocks past row m never run.
+  auto take_block = [&](int32_t nb, int32_t s) {
+    b = nb;
+    if (b <= bm) {
+      const int32_t jf = max(1, 32 * b + 1 - dhi);
+      const int32_t jl = min(n, 32 * b + 32 - dlo);
+      u = s - (jf + b);
+      span = jl - jf;
+      u_valid = b == 0 ? -1 : min(n, 32 * b - dlo) - jf;   // last column of block b - 1
+      dg = jf - 32 * b - 1 + d0;   // row j + d0 is row 32 b + 1 + (u + dg)
+    } else {
+      u = kDeadU;
+      span = 0;
+      u_valid = -1;
+      dg = 0x40000000;
+    }
+  };
 
   while (true) {
-    // ---- groups without a pair take the next one
-    const bool need = !has && more;
-    const uint32_t leaders = __ballot_sync(0xffffffffu, need && gl == 0);
-    unsigned long long base = 0;
-    if (leaders) {
+    // ---- groups without a pair take pairs until they hold one that needs
+    // the wavefront (one vote while all groups are busy)
+    while (true) {
+      const bool need = !has && more;
+      const uint32_t leaders = __ballot_sync(0xffffffffu, need && gl == 0);
+      if (!leaders) break;
       const int first = __ffs(leaders) - 1;
+      unsigned long long base = 0;
       if (lane == first) base = atomicAdd(next, (unsigned long long)__popc(leaders));
       base = __shfl_sync(0xffffffffu, base, first);
-    }
-    const uint64_t q = base + __popc(leaders & ((1u << gbase) - 1u));
-    if (need) {
-      if (q >= a.m) {
-        more = false;
-      } else {
-        t = a.order ? a.order[q] : q;
-        const uint32_t x = a.pi[t], y = a.pj[t];
-        k = a.pk ? a.pk[t] : a.K;
-        uint32_t res = 0xffffffffu;
-        if (x >= a.n_strings || y >= a.n_strings) {
-          if (gl == 0) atomicOr(a.dev_flags, FLAG_BOUNDS);
-          res = k + 1;
+      const uint64_t q = q_lo + base + __popc(leaders & ((1u << gbase) - 1u));
+      if (need) {
+        if (q >= q_hi) {
+          more = false;
         } else {
-          const int64_t ox = __ldg(a.offsets + x), lx = __ldg(a.offsets + x + 1) - ox;
-          const int64_t oy = __ldg(a.offsets + y), ly = __ldg(a.offsets + y + 1) - oy;
-          const bool xa = lx >= ly;
-          if (a.cells && gl == 0) cells += band_cells(xa ? lx : ly, xa ? ly : lx, a.K);
-          oA = xa ? ox : oy;
-          m = xa ? lx : ly;
-          oB = xa ? oy : ox;
-          n = xa ? ly : lx;
-          d0 = m - n;
-          if (d0 > (int64_t)k) {
+          t = a.order ? a.order[q] : q;
+          const uint32_t x = a.pi[t], y = a.pj[t];
+          k = a.pk ? a.pk[t] : a.K;
+          uint32_t res = 0xffffffffu;
+          const bool skip = a.skip_kband && a.skip_kband[t] < a.K && a.ed[t] <= a.skip_kband[t];
+          if (skip) {
+            res = 0xfffffffeu;   // settled by the first pass: nothing to do
+          } else if (x >= a.n_strings || y >= a.n_strings) {
+            if (gl == 0) atomicOr(a.dev_flags, FLAG_BOUNDS);
             res = k + 1;
-          } else if (n == 0) {
-            res = (uint32_t)d0;
           } else {
-            dlo = -(int32_t)(((int64_t)k - d0) >> 1);
-            dhi = (int32_t)d0 + (int32_t)(((int64_t)k - d0) >> 1);
-            if (dhi - dlo < 63) dlo = dhi - 63;        // at least 64 band rows (any wider band is exact)
-            bm = (int32_t)((m - 1) >> 5);
-            s = 0;
-            s_end = n + bm;
-            b = gl;
-            pub_tag = -1;
+            const int64_t ox = __ldg(a.offsets + x), lx = __ldg(a.offsets + x + 1) - ox;
+            const int64_t oy = __ldg(a.offsets + y), ly = __ldg(a.offsets + y + 1) - oy;
+            const bool xa = lx >= ly;
+            if (a.cells && gl == 0) cells += band_cells(xa ? lx : ly, xa ? ly : lx, a.K);
+            const int64_t mm = xa ? lx : ly, nn = xa ? ly : lx;
+            oA = xa ? ox : oy;
+            oB = xa ? oy : ox;
+            if (mm >= (int64_t)kMaxLen) {
+              if (gl == 0) atomicOr(a.dev_flags, FLAG_LENGTH);
+              res = k + 1;
+            } else if (mm - nn > (int64_t)k) {
+              res = k + 1;
+            } else if (nn == 0) {
+              res = (uint32_t)mm;
+            } else {
+              m = (int32_t)mm;
+              n = (int32_t)nn;
+              d0 = m - n;
+              dlo = -(int32_t)((k - (uint32_t)d0) >> 1);
+              dhi = d0 + (int32_t)((k - (uint32_t)d0) >> 1);
+              if (dhi - dlo < 63) dlo = dhi - 63;   // at least 64 band rows (any wider band is exact)
+              bm = (m - 1) >> 5;
+              sbase = 0;
+              take_block(gl, 0);
+              pub = kIdle;
+              done = reject = false;
+            }
           }
-        }
-        if (res != 0xffffffffu) {
-          if (gl == 0) a.ed[t] = res;
-        } else {
-          has = true;
+          if (res == 0xfffffffeu) {
+            if (gl == 0) ++nskip;
+          } else if (res != 0xffffffffu) {
+            if (gl == 0) a.ed[t] = res;
+          } else {
+            has = true;
+          }
         }
       }
     }
     if (!__any_sync(0xffffffffu, has || more)) break;
 
-    // ---- one wavefront step for groups holding a pair
-    const int32_t in_tag = __shfl_sync(0xffffffffu, pub_tag, prev_lane);
-    const int32_t in_score = __shfl_sync(0xffffffffu, pub_score, prev_lane);
-    bool done = false, reject = false;
-    int32_t result = 0;
-    pub_tag = -1;
-    if (has) {
-      ++s;
-      const int64_t j = s - b;
-      const int64_t jf = (32 * (int64_t)b + 1 - dhi) > 1 ? (32 * (int64_t)b + 1 - dhi) : 1;
-      const int64_t jl = (32 * (int64_t)b + 32 - dlo) < n ? (32 * (int64_t)b + 32 - dlo) : n;
-      if (b <= bm && j >= jf && j <= jl) {
-        const bool first_col = (j == jf);
-        if (first_col) {
+    // ---- kWaveSteps wavefront steps.  Every lane runs the column step; a lane
+    // outside its block's steps computes on stale state (rebuilt at the
+    // block's first column) that no other lane reads.  First and last
+    // columns and the diagonal test take one rarely divergent branch.
+#pragma unroll
+    for (int it = 0; it < kWaveSteps; ++it) {
+      const uint32_t w_in = __shfl_sync(0xffffffffu, pub, prev_lane);
+      ++u;
+      const uint32_t wv = u <= u_valid ? w_in : kIdle;
+      uint32_t Ph, hn;
+      wave_column<P>(pa, bw, wv, Pv, Mv, T, Ph, hn);
+      pub = ((Ph & 0x80000000u) | T) + hn;
+      const bool diag_here = it == kWaveSteps - 1 && (uint32_t)(u + dg) < 32u;
+      if (u == 0 || u == span || diag_here) {
+        if (u == 0) {   // first column: load the block's symbols, rows start from +1 deltas
+          const int32_t jf = sbase + it + 1 - b;
+          wave_load_bits<P>(a, PW, (uint64_t)(oA + 32 * (int64_t)b + 32 * (int64_t)GW), pa, false);
+          wave_load_bits<P>(a, PW, (uint64_t)(oB + jf - 1 + 32 * (int64_t)GW), bw, true);
           Pv = 0xffffffffu;
           Mv = 0u;
-          const uint64_t pos = (uint64_t)(oA + 32 * (int64_t)b + 32 * (int64_t)GW);
-#pragma unroll
-          for (int p = 0; p < P; ++p) {
-            const uint32_t lo = p < (int)a.bits ? __ldg(a.planes + (uint64_t)p * PW + (pos >> 5)) : 0u;
-            const uint32_t hi = p < (int)a.bits ? __ldg(a.planes + (uint64_t)p * PW + (pos >> 5) + 1) : 0u;
-            pa[p] = __funnelshift_r(lo, hi, (uint32_t)(pos & 31));
-          }
+          wave_column<P>(pa, bw, wv, Pv, Mv, T, Ph, hn);
+          // D of the row above the block in this column, plus the block's deltas
+          const int32_t above = b == 0 ? 1 : (int32_t)((w_in >> 1) & 0x3fffffffu);
+          const int32_t score = above + (int32_t)__popc(Pv) - (int32_t)__popc(Mv);
+          T = (uint32_t)score << 1;
+          pub = ((Ph & 0x80000000u) | T) + hn;
         }
-        if (first_col || j - bw_col >= 32) {
-          bw_col = j;
-          const uint64_t pos = (uint64_t)(oB + j - 1 + 32 * (int64_t)GW);
-#pragma unroll
-          for (int p = 0; p < P; ++p) {
-            const uint32_t lo = p < (int)a.bits ? __ldg(a.planes + (uint64_t)p * PW + (pos >> 5)) : 0u;
-            const uint32_t hi = p < (int)a.bits ? __ldg(a.planes + (uint64_t)p * PW + (pos >> 5) + 1) : 0u;
-            bw[p] = __funnelshift_r(lo, hi, (uint32_t)(pos & 31));
-          }
-        }
-        const uint32_t c = (uint32_t)(j - bw_col);
-        uint32_t Eq = 0xffffffffu;
-#pragma unroll
-        for (int p = 0; p < P; ++p)
-          if (p < (int)a.bits) Eq &= pa[p] ^ (((bw[p] >> c) & 1u) - 1u);
-        // horizontal delta entering the block's top row in column j
-        const bool from_prev = b > 0 && in_tag >= 0 && (in_tag >> 2) == b - 1;
-        const int hin = from_prev ? ((in_tag & 3) - 1) : 1;
-        const uint32_t hneg = hin < 0 ? 1u : 0u;
-        const uint32_t Xv = Eq | Mv;
-        const uint32_t Eh = Eq | hneg;
-        const uint32_t Xh = (((Eh & Pv) + Pv) ^ Pv) | Eh;
-        uint32_t Ph = Mv | ~(Xh | Pv);
-        uint32_t Mh = Pv & Xh;
-        const int hout = (int)(Ph >> 31) - (int)(Mh >> 31);
-        Ph = (Ph << 1) | (hin > 0 ? 1u : 0u);
-        Mh = (Mh << 1) | hneg;
-        Pv = Mh | ~(Xv | Ph);
-        Mv = Ph & Xv;
-        if (first_col) {
-          // D of the row above the block in column j, plus the block's deltas
-          const int32_t above = (b == 0) ? (int32_t)j : in_score;
-          score = above + (int32_t)__popc(Pv) - (int32_t)__popc(Mv);
-        } else {
-          score += hout;
-        }
-        pub_tag = (b << 2) | (hout + 1);
-        pub_score = score;
-        work += 1;
         // D at row r of this block = score minus the deltas of the rows below r
-        if (b == bm && j == n) {
-          const int tm = (int)((m - 1) & 31);
-          const uint32_t below = tm == 31 ? 0u : (0xffffffffu << (tm + 1));
-          result = score - (int32_t)__popc(Pv & below) + (int32_t)__popc(Mv & below);
-          done = true;
-        } else if ((s & (kWaveCheck - 1)) == 0) {
-          const int64_t rd = j + d0;   // row of diagonal d0 in column j
-          if (rd >= 32 * (int64_t)b + 1 && rd <= 32 * (int64_t)b + 32) {
-            const int tr = (int)((rd - 1) & 31);
-            const uint32_t below = tr == 31 ? 0u : (0xffffffffu << (tr + 1));
-            const int32_t diag = score - (int32_t)__popc(Pv & below) + (int32_t)__popc(Mv & below);
-            if (diag > (int32_t)k) reject = true;
-          }
+        if (diag_here && (uint32_t)u <= (uint32_t)span) {   // row j + d0 of diagonal d0
+          const int tr = u + dg;
+          const uint32_t below = tr == 31 ? 0u : (0xffffffffu << (tr + 1));
+          const int32_t diag = (int32_t)(T >> 1) - (int32_t)__popc(Pv & below) + (int32_t)__popc(Mv & below);
+          if (diag > (int32_t)k) reject = true;
         }
-        if (j == jl) b += G;   // this block left the band: take the next one of this lane
+        if (u == span) {   // the block leaves the band
+          if (b == bm) {
+            const int tm = (m - 1) & 31;
+            const uint32_t below = tm == 31 ? 0u : (0xffffffffu << (tm + 1));
+            result = (int32_t)(T >> 1) - (int32_t)__popc(Pv & below) + (int32_t)__popc(Mv & below);
+            done = true;
+          }
+          work += (uint64_t)(span + 1);
+          take_block(b + G, sbase + it + 1);
+        }
       }
     }
-    const uint32_t dmask = __ballot_sync(0xffffffffu, done) & gmask;
-    const uint32_t rmask = __ballot_sync(0xffffffffu, reject) & gmask;
-    const int src = dmask ? __ffs(dmask) - 1 : lane;
-    const int32_t fin = __shfl_sync(0xffffffffu, result, src);
-    if (has && (dmask || rmask)) {
-      if (gl == 0) a.ed[t] = rmask ? k + 1 : (fin > (int32_t)k ? k + 1 : (uint32_t)fin);
-      has = false;
-    } else if (has && s >= s_end) {   // cannot happen: the last block ends at step s_end
-      if (gl == 0) {
-        atomicOr(a.dev_flags, FLAG_BOUNDS);
-        a.ed[t] = k + 1;
+    sbase += kWaveSteps;
+    if ((sbase & 31) == 0 && u >= 0 && u <= span) {   // B's symbols of the next 32 columns, all lanes at once
+      wave_load_bits<P>(a, PW, (uint64_t)(oB + (sbase - b) + 32 * (int64_t)GW), bw, true);
+    }
+    // ---- a group whose pair finished (or was rejected) writes it and frees
+    // its lanes; one vote in the common case where none did
+    const bool overrun = has && sbase >= n + bm;   // cannot happen: the last block ends at step n + bm
+    if (__ballot_sync(0xffffffffu, done || reject || overrun)) {
+      const uint32_t dmask = __ballot_sync(0xffffffffu, done) & gmask;
+      const uint32_t rmask = __ballot_sync(0xffffffffu, reject) & gmask;
+      const int src = dmask ? __ffs(dmask) - 1 : lane;
+      const int32_t fin = __shfl_sync(0xffffffffu, result, src);
+      bool end = false;
+      if (has && (dmask || rmask)) {
+        if (gl == 0) a.ed[t] = rmask ? k + 1 : (fin > (int32_t)k ? k + 1 : (uint32_t)fin);
+        end = true;
+      } else if (overrun) {
+        if (gl == 0) {
+          atomicOr(a.dev_flags, FLAG_BOUNDS);
+          a.ed[t] = k + 1;
+        }
+        end = true;
       }
-      has = false;
+      if (end) {
+        if (u >= 0 && u <= span) work += (uint64_t)(u + 1);   // block cut short by the exit
+        has = false;
+        u = kDeadU;
+        span = 0;
+        u_valid = -1;
+        dg = 0x40000000;
+        pub = kIdle;
+        done = reject = false;
+      }
     }
   }
   if (a.work) {
@@ -544,6 +634,10 @@ __global__ void __launch_bounds__(128) verify_wave_kernel(VerifyArgs a, uint64_t
   if (a.cells) {
     for (int o = 16; o > 0; o >>= 1) cells += __shfl_down_sync(0xffffffffu, cells, o);
     if (lane == 0 && cells) atomicAdd(a.cells, (unsigned long long)cells);
+  }
+  if (a.skipped) {
+    for (int o = 16; o > 0; o >>= 1) nskip += __shfl_down_sync(0xffffffffu, nskip, o);
+    if (lane == 0 && nskip) atomicAdd(a.skipped, (unsigned long long)nskip);
   }
 }
 

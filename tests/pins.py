@@ -162,7 +162,7 @@ def pin_q_rule():
 
 
 def pin_radius():
-    """r = floor((|s| - q + 1 - T) / (2T + 2)) (Alg. 2 line 2), floored."""
+    """r = floor((|s| - q + 1 - T) / (2T + 2)) (Alg. 2, neighbourhood radius), floored."""
     assert oracle.radius(21, 3, 3, 0) == 2         # Table 4: s1
     assert oracle.radius(22, 3, 3, 0) == 2         # Table 4: s2
     assert oracle.radius(500, 9, 10, 0) == 21      # (500-9+1-10)/22 = 21.9
@@ -269,7 +269,7 @@ def pin_hash_is_injective(seed: int = 5):
 
 def set_definition_candidates(s: synth.StringSet, K: int, parts: oracle.Partitions) -> set:
     """Candidates by their order-free definition: i != j share a partition
-    substring, |len_i - len_j| <= K, and the position filter of Alg. 3 line 8
+    substring, |len_i - len_j| <= K, and the position filter of Alg. 3
     holds for that matched partition pair."""
     L = s.lengths()
     groups = {}
