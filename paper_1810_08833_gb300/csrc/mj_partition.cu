@@ -11,6 +11,8 @@
 // own string (positions i in [r, m-1-r] of a string have all their 2r
 // neighbours inside the string's q-gram range), so halos that run into a
 // neighbouring string are harmless.
+#include <type_traits>
+
 #include "mj_internal.cuh"
 
 namespace mj {
@@ -48,33 +50,26 @@ __device__ __forceinline__ uint32_t string_of(const int64_t* __restrict__ off, u
   return lo;
 }
 
-// Alg. 2's neighbourhood radius with floor division and the r_min clamp.
-__device__ __forceinline__ int32_t radius_of(int64_t slen, int32_t q, int32_t T, int32_t r_min) {
-  int64_t num = slen - q + 1 - T, den = 2 * (int64_t)T + 2;
-  int64_t r = num >= 0 ? num / den : -((-num + den - 1) / den);
-  return r < r_min ? r_min : (int32_t)r;
-}
-
 constexpr int kThreads = 256;
 constexpr int kPerThread = kPartTile / kThreads;  // positions per thread in the emit kernel
-constexpr int kWarpPositions = kPartTile / (kThreads / 32);
-constexpr int kMaxTileStrings = 1024;             // string offsets cached per tile
+
+// The anchor kernel: one CTA per kATile positions (two kPartTile tiles).
+constexpr int kATile = 2 * kPartTile;
+constexpr int kAPer = kATile / kThreads;           // 16 positions per thread
+constexpr int kAWarpSpan = kATile / (kThreads / 32);   // 512 positions per warp
+constexpr int kAMaxStrings = 256;                  // string offsets cached per CTA
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline int floor_log2(int x) {
-  int t = 0;
-  while ((2 << t) <= x) ++t;
-  return t;
-}
+// Halo of the anchor kernel: r_max positions rounded up to 16.
+__host__ __device__ inline int anchor_halo(int r_max) { return (int)align16((size_t)(r_max < 1 ? 1 : r_max)); }
 
-// Shared memory of the anchor kernel: staged rank codes, then the range-minimum
-// table of Pi values: level t holds min(h[x .. x + 2^t - 1]) for every x.
+// Shared memory of the anchor kernel: rank table, staged rank codes of the
+// tile, its halo and q-gram tail, then two range-minimum levels (ping-pong).
 template <class HT>
-__host__ __device__ inline size_t anchor_smem_bytes(int r_max, int q) {
-  size_t span = kPartTile + 2 * (size_t)r_max;
-  int levels = floor_log2(r_max < 1 ? 1 : r_max) + 1;
-  return 256 + align16(span + q) + (size_t)levels * span * sizeof(HT);
+__host__ __device__ inline size_t anchor_smem_bytes(int r_max) {
+  const size_t span = kATile + 2 * (size_t)anchor_halo(r_max);
+  return 256 + align16(span + 80) + 2 * align16((span + 8) * sizeof(HT));
 }
 
 // Pi of the q-gram whose packed code is `code` (see mjo_hash_qgrams for the
@@ -98,181 +93,301 @@ __global__ void tile_first_kernel(const int64_t* __restrict__ offsets, uint32_t 
   }
 }
 
-// Alg. 2 for one tile: a position i of string s (0-based, m = |s| - q + 1
-// q-gram starts, radius r) is an anchor iff i = 0, or r <= i <= m - 1 - r and
-// h[i] is strictly below both min(h[i-r .. i-1]) and min(h[i+1 .. i+r]).
-// Both window minima come from a sparse table over the tile's Pi values: a
-// window of length r is the union of two windows of length 2^t, t =
-// floor(log2 r).  Every step is branch-free across a warp.
+// Alg. 2's neighbourhood radius in 32-bit arithmetic (every length < 2^32).
+__device__ __forceinline__ int32_t radius32(uint32_t slen, uint32_t q, uint32_t T, int32_t r_min) {
+  const int64_t num = (int64_t)slen - q + 1 - T;
+  if (num < 0) return r_min;   // floor(num / den) < 0 <= r_min
+  const uint32_t r = (uint32_t)num / (2 * T + 2);
+  return r < (uint32_t)r_min ? r_min : (int32_t)r;
+}
+
+// Four consecutive table entries (16-byte aligned for 32-bit entries).
+__device__ __forceinline__ void load4(const uint32_t* p, uint32_t (&v)[4]) {
+  const uint4 u = *reinterpret_cast<const uint4*>(p);
+  v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
+}
+__device__ __forceinline__ void load4(const uint64_t* p, uint64_t (&v)[4]) {
+  const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(p);
+  const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void store4(uint32_t* p, const uint32_t (&v)[4]) {
+  *reinterpret_cast<uint4*>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(uint64_t* p, const uint64_t (&v)[4]) {
+  *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(v[0], v[1]);
+  *reinterpret_cast<ulonglong2*>(p + 2) = make_ulonglong2(v[2], v[3]);
+}
+
+// Alg. 2 for kATile positions: position i of string s (0-based, m = |s| - q
+// + 1 q-gram starts, radius r) is an anchor iff i = 0, or r <= i <= m - 1 - r
+// and h[i] is strictly below both min(h[i-r .. i-1]) and min(h[i+1 .. i+r]).
+// A window of length r is the union of two windows of length 2^t, t =
+// floor(log2 r), so level t of a range-minimum table answers it with two
+// reads.  The levels are built one at a time into two ping-pong buffers; a
+// position is tested right after its string's level is built.
+//   phase 1  rank codes of the tile and halos, staged with 16-byte loads;
+//   phase 2  Pi of every q-gram start (16 consecutive starts per thread,
+//            packed code rolled forward), and the verifier's bit-planes;
+//   phase 3  level 0 (Pi itself), then levels 1 .. t_max, 4 entries per
+//            thread and step; after level t the positions of strings with
+//            floor(log2 r) = t are tested (lane-interleaved: warp w holds
+//            positions 512 w + 32 j + lane);
+//   phase 4  one ballot per 32 positions gives the bitmap word.
 template <class HT, bool WIDE, bool TABLE>
-__global__ void __launch_bounds__(kThreads) anchor_flags_kernel(PartitionArgs a, uint32_t* __restrict__ bitmap,
+__global__ void __launch_bounds__(kThreads, sizeof(HT) == 4 ? 4 : 1) anchor_flags_kernel(PartitionArgs a, uint32_t* __restrict__ bitmap,
                                                                 uint32_t* __restrict__ tile_count,
                                                                 uint32_t* __restrict__ dev_flags,
                                                                 uint32_t* __restrict__ planes, uint64_t plane_words,
                                                                 uint32_t guard_words,
-                                                                const uint32_t* __restrict__ tile_first) {
+                                                                const uint32_t* __restrict__ tile_first,
+                                                                uint64_t tiles) {
   extern __shared__ __align__(16) uint8_t smem[];
-  __shared__ int64_t s_off[kMaxTileStrings + 1];   // offsets[sid0 .. sid0 + cap]
+  __shared__ int64_t s_off[kAMaxStrings + 1];   // offsets[sid0 .. sid0 + cap]
   __shared__ uint32_t s_ns;
   __shared__ uint32_t s_warp[kThreads / 32];
-  const int HL = a.r_max;
-  const int span = kPartTile + 2 * HL;        // positions holding a Pi value
-  const int nb = span + (int)a.q;              // staged symbols
-  const int levels = floor_log2(HL < 1 ? 1 : HL) + 1;
-  uint8_t* s_rank = smem;                      // 256-entry rank table
-  uint8_t* s_code = smem + 256;                // staged rank codes
-  HT* s_h = reinterpret_cast<HT*>(smem + 256 + align16(nb));   // level 0; level t at s_h + t * span
+  const int Hs = anchor_halo(a.r_max);
+  const int span = kATile + 2 * Hs;             // positions holding a Pi value
+  const int nsym = span + 80;                   // staged symbols (q-gram tails)
+  uint8_t* s_rank = smem;
+  uint8_t* s_code = smem + 256;
+  HT* lev0 = reinterpret_cast<HT*>(smem + 256 + align16(nsym));
+  HT* lev1 = reinterpret_cast<HT*>(reinterpret_cast<uint8_t*>(lev0) + align16((span + 8) * sizeof(HT)));
 
-  const uint64_t g0 = (uint64_t)blockIdx.x * kPartTile;
-  const int64_t base = (int64_t)g0 - HL;       // global position of s_code[0] and s_h[0]
+  const uint32_t g0 = blockIdx.x * (uint32_t)kATile;
+  const int64_t base = (int64_t)g0 - Hs;        // global position of s_code[0] and lev[0]
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t nbytes = (uint32_t)a.nbytes;
 
+  // ---- phase 0: rank table and the CTA's string offsets
   s_rank[threadIdx.x] = a.rank[threadIdx.x];
-  const uint32_t sid0 = __ldg(tile_first + blockIdx.x);
-  const uint32_t cap = min((uint32_t)kMaxTileStrings, a.n - sid0);
+  const uint32_t sid0 = __ldg(tile_first + 2 * (uint64_t)blockIdx.x);
+  const uint32_t cap = min((uint32_t)kAMaxStrings, a.n - sid0);
   for (uint32_t t = threadIdx.x; t <= cap; t += kThreads) s_off[t] = __ldg(a.offsets + sid0 + t);
   __syncthreads();
-  // rank codes of [base, base + nb), 16-byte loads where aligned and in range
+
+  // ---- phase 1: rank codes of [base, base + nsym), 16 per thread and step
   {
-    const int64_t al = base & ~int64_t(15);
-    for (int64_t c = al + 16 * (int64_t)threadIdx.x; c < base + nb; c += 16 * kThreads) {
-      if (c >= 0 && (uint64_t)c + 16 <= a.nbytes) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.bytes + c));
+    const bool vec = ((uintptr_t)a.bytes & 15) == 0;
+    for (int c = 16 * threadIdx.x; c < nsym; c += 16 * kThreads) {
+      const int64_t gb = base + c;
+      uint32_t out[4];
+      if (vec && gb >= 0 && gb + 16 <= (int64_t)nbytes) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.bytes + gb));
         const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int b = 0; b < 16; ++b) {
-          const int64_t idx = c + b - base;
-          if (idx >= 0 && idx < nb) s_code[idx] = s_rank[(w4[b >> 2] >> (8 * (b & 3))) & 255u];
+        for (int k = 0; k < 4; ++k) {
+          out[k] = (uint32_t)s_rank[w4[k] & 255u] | ((uint32_t)s_rank[(w4[k] >> 8) & 255u] << 8) |
+                   ((uint32_t)s_rank[(w4[k] >> 16) & 255u] << 16) | ((uint32_t)s_rank[w4[k] >> 24] << 24);
         }
       } else {
-        for (int b = 0; b < 16; ++b) {
-          const int64_t g = c + b, idx = g - base;
-          if (idx >= 0 && idx < nb) s_code[idx] = (g >= 0 && (uint64_t)g < a.nbytes) ? s_rank[__ldg(a.bytes + g)] : 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          uint32_t x = 0;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int64_t g = gb + 4 * k + b;
+            if (g >= 0 && g < (int64_t)nbytes) x |= (uint32_t)s_rank[__ldg(a.bytes + g)] << (8 * b);
+          }
+          out[k] = x;
         }
       }
+      *reinterpret_cast<uint4*>(s_code + c) = make_uint4(out[0], out[1], out[2], out[3]);
     }
   }
-  __syncthreads();
   if (threadIdx.x == 0) {
-    // strings that may hold tile positions: indices 0 .. ns-1 of s_off
+    // strings that may hold CTA positions: indices 0 .. ns-1 of s_off
     uint32_t lo = 0, hi = cap;
-    const int64_t gend = (int64_t)g0 + kPartTile;
+    const int64_t gend = (int64_t)g0 + kATile;
     while (hi - lo > 1) {
-      uint32_t mid = (lo + hi) >> 1;
+      const uint32_t mid = (lo + hi) >> 1;
       if (s_off[mid] < gend) lo = mid; else hi = mid;
     }
     s_ns = lo + 1;
   }
-  // bit-planes of the tile's rank codes for the verifier (one ballot per word)
-  if (planes) {
-    for (int w = wid; w < kPartTile / 32; w += kThreads / 32) {
-      const uint32_t r = s_code[HL + 32 * w + lane];
-      const uint64_t word = guard_words + (g0 >> 5) + w;
+  __syncthreads();
+
+  // ---- phase 2: Pi of every q-gram start in [0, span), and the bit-planes
+  {
+    // packed codes fit 32 bits unless WIDE (a table is indexed by codes < 2^32 too)
+    using CT = typename std::conditional<WIDE, uint64_t, uint32_t>::type;
+    const uint32_t qb = a.q * a.bits;
+    const CT mask = qb >= 8 * sizeof(CT) ? ~CT(0) : ((CT(1) << qb) - 1);
+    const uint32_t bsh = a.bits, qm1 = a.q - 1;
+    for (int x0 = kAPer * threadIdx.x; x0 < span; x0 += kAPer * kThreads) {
+      CT code = 0;
+      for (uint32_t t = 0; t < qm1; ++t) code = (code << bsh) | s_code[x0 + t];
+      const uint8_t* nxt = s_code + x0 + qm1;
+      HT hv[kAPer];
 #pragma unroll
-      for (int p = 0; p < 8; ++p) {
-        if (p < (int)a.bits) {
-          const uint32_t bw = __ballot_sync(0xffffffffu, (r >> p) & 1u);
-          if (lane == p) planes[(uint64_t)p * plane_words + word] = bw;
-        }
+      for (int j = 0; j < kAPer; ++j) {
+        code = ((code << bsh) | nxt[j]) & mask;
+        hv[j] = pi_value<HT, WIDE, TABLE>((uint64_t)code, a);
+      }
+      if (sizeof(HT) == 4) {
+#pragma unroll
+        for (int j = 0; j < kAPer; j += 4)
+          *reinterpret_cast<uint4*>(lev0 + x0 + j) =
+              make_uint4((uint32_t)hv[j], (uint32_t)hv[j + 1], (uint32_t)hv[j + 2], (uint32_t)hv[j + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < kAPer; ++j) lev0[x0 + j] = hv[j];
       }
     }
   }
-
-  // Pi of every q-gram start in [0, span): contiguous chunk per thread,
-  // packed code rolled forward (first symbol most significant).
-  {
-    const int per = (span + kThreads - 1) / kThreads;
-    const int p0 = threadIdx.x * per;
-    const int p1 = min(p0 + per, span);
-    const uint32_t qb = a.q * a.bits;
-    const uint64_t mask = qb >= 64 ? ~0ull : ((1ull << qb) - 1);
-    if (p0 < p1) {
-      uint64_t code = 0;
-      for (uint32_t t = 0; t + 1 < a.q; ++t) code = (code << a.bits) | s_code[p0 + t];
-      for (int p = p0; p < p1; ++p) {
-        code = ((code << a.bits) | s_code[p + a.q - 1]) & mask;
-        s_h[p] = pi_value<HT, WIDE, TABLE>(code, a);
+  if (planes) {
+    // plane p, word (g0 + 512 w) / 32 + j: one ballot per word; lane j stores it
+    const uint64_t word0 = guard_words + (uint64_t)(g0 >> 5) + (uint64_t)wid * (kAWarpSpan / 32);
+    const uint64_t wlimit = guard_words + tiles * (kPartTile / 32);
+    uint32_t sym[kAWarpSpan / 32];
+#pragma unroll
+    for (int j = 0; j < kAWarpSpan / 32; ++j) sym[j] = s_code[Hs + kAWarpSpan * wid + 32 * j + lane];
+    for (int p = 0; p < (int)a.bits; ++p) {
+      uint32_t mine = 0;
+#pragma unroll
+      for (int j = 0; j < kAWarpSpan / 32; ++j) {
+        const uint32_t bw = __ballot_sync(0xffffffffu, (sym[j] >> p) & 1u);
+        if (lane == j) mine = bw;
       }
+      if (lane < kAWarpSpan / 32 && word0 + lane < wlimit) planes[(uint64_t)p * plane_words + word0 + lane] = mine;
     }
   }
   __syncthreads();
-  // sparse table levels 1 .. levels-1
-  for (int t = 1; t < levels; ++t) {
-    const HT* src = s_h + (size_t)(t - 1) * span;
-    HT* dst = s_h + (size_t)t * span;
-    const int half = 1 << (t - 1);
-    const int cnt = span - (1 << t) + 1;
-    for (int x = threadIdx.x; x < cnt; x += kThreads) {
-      const HT u = src[x], v = src[x + half];
-      dst[x] = u < v ? u : v;
-    }
-    __syncthreads();
-  }
 
-  // the test: warp wid owns positions [g0 + kWarpPositions * wid, +kWarpPositions),
-  // lane l takes positions 32k + l
-  const uint64_t wbase = g0 + (uint64_t)wid * kWarpPositions;
+  // ---- phase 3: per position (lane-interleaved) string, radius and level
+  const uint32_t wbase = g0 + (uint32_t)(kAWarpSpan * wid);
   const uint32_t ns = s_ns;
-  const bool cached = ns < cap || sid0 + cap == a.n;   // every string of the tile is in s_off
-  uint32_t sid = 0;
-  int64_t s_o = 0, s_e = -1, m = 0;
-  int32_t r = 0;
+  const bool cached = ns < cap || sid0 + cap == a.n;   // every string of the CTA is in s_off
+  HT v[kAPer];          // Pi of the position
+  uint32_t info[kAPer]; // r (bits 0..23) and level t (bits 24..31; 31 = not tested)
+  uint32_t flags = 0;   // anchor bit per position
+  uint32_t level_mask = 0;
   {
-    const uint64_t g = wbase + lane;
-    if (g < a.nbytes) {
+    // the current string: [s_o, s_e), radius r, level t; positions i of it
+    // with r <= i <= i_hi are tested (i_hi < r: none)
+    uint32_t sid = 0, s_o = 0, s_e = 0;
+    int32_t r = 0, i_hi = -1;
+    uint32_t lvl = 0;
+    auto set_string = [&]() {
+      const uint32_t slen = s_e - s_o;
+      r = radius32(slen, a.q, a.T, a.r_min);
+      const int64_t hi = (int64_t)slen - a.q - r;   // m - 1 - r, m = |s| - q + 1
+      i_hi = hi < 0 ? -1 : (hi > 0x7fffffff ? 0x7fffffff : (int32_t)hi);
+      if (r > Hs && i_hi >= r) atomicOr(dev_flags, FLAG_BOUNDS);   // cannot happen: r_max bounds every r
+      lvl = (r == 0 || r > Hs || i_hi < r) ? 31u << 24
+                                            : ((uint32_t)(31 - __clz(r)) << 24) | (uint32_t)r;
+    };
+    const uint32_t gfirst = wbase + lane;
+    if (gfirst < nbytes) {
       if (cached) {
         uint32_t lo = 0, hi = ns;   // s_off[lo] <= g < s_off[hi]
         while (hi - lo > 1) {
-          uint32_t mid = (lo + hi) >> 1;
-          if ((uint64_t)s_off[mid] <= g) lo = mid; else hi = mid;
+          const uint32_t mid = (lo + hi) >> 1;
+          if ((uint64_t)s_off[mid] <= gfirst) lo = mid; else hi = mid;
         }
         sid = sid0 + lo;
       } else {
-        sid = string_of(a.offsets, a.n, g);
+        sid = string_of(a.offsets, a.n, gfirst);
       }
-      s_o = (sid - sid0 < cap) ? s_off[sid - sid0] : __ldg(a.offsets + sid);
-      s_e = (sid + 1 - sid0 <= cap) ? s_off[sid + 1 - sid0] : __ldg(a.offsets + sid + 1);
-      m = s_e - s_o - a.q + 1;
-      r = radius_of(s_e - s_o, a.q, a.T, a.r_min);
+      s_o = (uint32_t)((sid - sid0 <= cap) ? s_off[sid - sid0] : __ldg(a.offsets + sid));
+      s_e = (uint32_t)((sid + 1 - sid0 <= cap) ? s_off[sid + 1 - sid0] : __ldg(a.offsets + sid + 1));
+      set_string();
+    }
+#pragma unroll
+    for (int j = 0; j < kAPer; ++j) {
+      const uint32_t g = wbase + 32 * j + lane;
+      const int x = Hs + kAWarpSpan * wid + 32 * j + lane;
+      v[j] = lev0[x];
+      info[j] = 31u << 24;
+      if (g < nbytes) {
+        while (g >= s_e) {   // next non-empty string holding g
+          ++sid;
+          s_o = s_e;
+          s_e = (uint32_t)((sid + 1 - sid0 <= cap) ? s_off[sid + 1 - sid0] : __ldg(a.offsets + sid + 1));
+          set_string();
+        }
+        const int32_t i = (int32_t)(g - s_o);
+        const bool tested = i >= r && i <= i_hi;
+        if (i == 0 || (tested && r == 0)) flags |= 1u << j;
+        if (tested) info[j] = lvl;
+      }
+      level_mask |= 1u << (info[j] >> 24);   // bit 31 for untested positions
     }
   }
-  uint32_t tot = 0;
+  level_mask &= 0x7fffffffu;
+  // levels this CTA needs: 0 .. the highest floor(log2 r) of its positions
+  __shared__ uint32_t s_levels;
+  if (threadIdx.x == 0) s_levels = 0;
+  __syncthreads();
+  if (level_mask) atomicOr(&s_levels, level_mask);
+  __syncthreads();
+  const int t_top = s_levels ? 31 - __clz(s_levels) : 0;
+  HT* cur = lev0;
+  HT* oth = lev1;
 #pragma unroll 1
-  for (int k = 0; k < kWarpPositions / 32; ++k) {
-    const uint64_t g = wbase + 32 * k + lane;
-    bool anchor = false;
-    if (g < a.nbytes) {
-      while ((int64_t)g >= s_e) {   // next non-empty string holding g
-        ++sid;
-        s_o = s_e;
-        s_e = (sid + 1 - sid0 <= cap) ? s_off[sid + 1 - sid0] : __ldg(a.offsets + sid + 1);
-        m = s_e - s_o - a.q + 1;
-        r = radius_of(s_e - s_o, a.q, a.T, a.r_min);
+  for (int t = 0; t <= t_top; ++t) {
+    if (t > 0) {
+      // level t from level t - 1: min of entries x and x + 2^(t-1)
+      const int half = 1 << (t - 1);
+      const int cnt = span - (1 << t) + 1;
+      for (int x = 4 * threadIdx.x; x < cnt; x += 4 * kThreads) {
+        HT lo4[4], nx4[4], hi4[4];
+        load4(cur + x, lo4);
+        if (half >= 4) {
+          load4(cur + x + half, hi4);
+        } else {
+          load4(cur + x + 4, nx4);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int y = k + half;   // 1 .. 5
+            hi4[k] = y < 4 ? lo4[y & 3] : nx4[y & 3];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) lo4[k] = lo4[k] < hi4[k] ? lo4[k] : hi4[k];
+        store4(oth + x, lo4);
       }
-      const int64_t i = (int64_t)g - s_o;
-      const bool tested = i >= r && i <= m - 1 - r;
-      if (r > HL && tested) atomicOr(dev_flags, FLAG_BOUNDS);    // cannot happen: r_max bounds every r
-      const int p = (int)((int64_t)g - base);
-      const int rr = r < 1 ? 1 : (r > HL ? HL : r);
-      const int t = 31 - __clz(rr);
-      const int w = 1 << t;
-      const HT* lv = s_h + (size_t)t * span;
-      // indices stay inside [0, span) for every position of the tile
-      const HT lmin = min(lv[p - rr], lv[p - w]);
-      const HT rmin = min(lv[p + 1], lv[p + rr - w + 1]);
-      const HT v = s_h[p];
-      anchor = (i == 0) || (tested && r <= HL && (r == 0 || (v < lmin && v < rmin)));
+      __syncthreads();
+      HT* tmp = cur;
+      cur = oth;
+      oth = tmp;
     }
-    const uint32_t word = __ballot_sync(0xffffffffu, anchor);
-    if (lane == 0) bitmap[(wbase >> 5) + k] = word;
+    if ((level_mask >> t) & 1u) {
+      const int w = 1 << t;
+#pragma unroll
+      for (int j = 0; j < kAPer; ++j) {
+        if ((int)(info[j] >> 24) == t) {
+          const int r = (int)(info[j] & 0xffffffu);
+          const int x = Hs + kAWarpSpan * wid + 32 * j + lane;
+          const HT lmin = min(cur[x - r], cur[x - w]);
+          const HT rmin = min(cur[x + 1], cur[x + r - w + 1]);
+          if (v[j] < lmin && v[j] < rmin) flags |= 1u << j;
+        }
+      }
+    }
+  }
+
+  // ---- phase 4: bitmap words (lane j stores word j of the warp) and counts
+  uint32_t mine = 0, tot = 0;
+#pragma unroll
+  for (int j = 0; j < kAPer; ++j) {
+    const uint32_t word = __ballot_sync(0xffffffffu, (flags >> j) & 1u);
+    if (lane == j) mine = word;
     tot += __popc(word);
   }
+  const uint64_t wword = (uint64_t)(wbase >> 5) + lane;
+  if (lane < kAPer && wword < tiles * (kPartTile / 32)) bitmap[wword] = mine;
   if (lane == 0) s_warp[wid] = tot;
   __syncthreads();
   if (threadIdx.x == 0) {
-    uint32_t t = 0;
-    for (int w = 0; w < kThreads / 32; ++w) t += s_warp[w];
-    tile_count[blockIdx.x] = t;
+    constexpr int kHalf = kThreads / 64;   // warps per kPartTile tile
+    uint32_t c0 = 0, c1 = 0;
+    for (int w = 0; w < kHalf; ++w) {
+      c0 += s_warp[w];
+      c1 += s_warp[kHalf + w];
+    }
+    tile_count[2 * (uint64_t)blockIdx.x] = c0;
+    if (2 * (uint64_t)blockIdx.x + 1 < tiles) tile_count[2 * (uint64_t)blockIdx.x + 1] = c1;
   }
 }
 
@@ -369,27 +484,27 @@ int launch_anchor_flags(const PartitionArgs& a, uint32_t* bitmap, uint32_t* tile
   }
   const bool wide = (uint64_t)a.q * a.bits > 32;
   const bool table = a.table != nullptr;
-  const size_t smem = (table || wide) ? anchor_smem_bytes<uint64_t>(a.r_max, a.q)
-                                      : anchor_smem_bytes<uint32_t>(a.r_max, a.q);
+  const size_t smem = (table || wide) ? anchor_smem_bytes<uint64_t>(a.r_max) : anchor_smem_bytes<uint32_t>(a.r_max);
   int dev = 0, max_optin = 0;
   MJ_CUDA_TRY(cudaGetDevice(&dev));
   MJ_CUDA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if (smem + sizeof(int64_t) * (kMaxTileStrings + 1) + 64 > (size_t)max_optin) return MJ_ERR_UNSUPPORTED;
+  if (smem + sizeof(int64_t) * (kAMaxStrings + 1) + 64 > (size_t)max_optin) return MJ_ERR_UNSUPPORTED;
+  const unsigned grid = (unsigned)((tiles + 1) / 2);
   if (table) {
     auto k = anchor_flags_kernel<uint64_t, false, true>;
     MJ_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k<<<(unsigned)tiles, kThreads, smem, s>>>(a, bitmap, tile_count, dev_flags, planes, plane_words, guard_words,
-                                              tile_first);
+    k<<<grid, kThreads, smem, s>>>(a, bitmap, tile_count, dev_flags, planes, plane_words, guard_words, tile_first,
+                                   tiles);
   } else if (wide) {
     auto k = anchor_flags_kernel<uint64_t, true, false>;
     MJ_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k<<<(unsigned)tiles, kThreads, smem, s>>>(a, bitmap, tile_count, dev_flags, planes, plane_words, guard_words,
-                                              tile_first);
+    k<<<grid, kThreads, smem, s>>>(a, bitmap, tile_count, dev_flags, planes, plane_words, guard_words, tile_first,
+                                   tiles);
   } else {
     auto k = anchor_flags_kernel<uint32_t, false, false>;
     MJ_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k<<<(unsigned)tiles, kThreads, smem, s>>>(a, bitmap, tile_count, dev_flags, planes, plane_words, guard_words,
-                                              tile_first);
+    k<<<grid, kThreads, smem, s>>>(a, bitmap, tile_count, dev_flags, planes, plane_words, guard_words, tile_first,
+                                   tiles);
   }
   MJ_KERNEL_DONE();
   return MJ_OK;
