@@ -120,7 +120,6 @@ int exclusive_scan(const TI* in, TO* out, uint64_t n, TO* temp, TO* total_out, c
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per tile
-constexpr int kWarps = kSortThreads / 32;
 
 __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t* __restrict__ keys, uint64_t n,
                                                                   int shift, uint32_t num_tiles,
@@ -138,58 +137,102 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t
   hist[(uint64_t)threadIdx.x * num_tiles + blockIdx.x] = s_hist[threadIdx.x];
 }
 
-// Stable scatter of one tile: warp w owns items [w*512, w*512+512) of the
+// Stable scatter of one tile.  Warp w owns items [w*512, w*512+512) of the
 // tile, taken in 16 rounds of 32 consecutive items; ranks among equal digits
 // come from __match_any_sync within a round plus running per-warp counters.
-__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
+// The tile is first placed in digit order in shared memory, then written out
+// item by item in that order: items of one digit go to consecutive global
+// addresses, so a warp's stores form a few contiguous runs.
+constexpr size_t kScatterSmem = (size_t)kSortTile * (sizeof(uint64_t) + sizeof(uint32_t));
+constexpr int kScatThreads = 512;                       // threads of the scatter kernel
+constexpr int kScatItems = kSortTile / kScatThreads;    // items per thread
+constexpr int kScatWarps = kScatThreads / 32;
+
+__global__ void __launch_bounds__(kScatThreads) radix_scatter_kernel(
     const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, uint64_t n, int shift,
     uint32_t num_tiles, const uint32_t* __restrict__ offs, uint64_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out) {
-  __shared__ uint32_t s_cnt[kWarps][256];
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* s_vals = reinterpret_cast<uint32_t*>(smem + (size_t)kSortTile * sizeof(uint64_t));
+  __shared__ uint32_t s_cnt[kScatWarps][256];
+  __shared__ uint32_t s_start[256];   // first local position of each digit
+  __shared__ uint32_t s_goff[256];    // global position of each digit's first item
+  __shared__ uint32_t s_wsum[8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int d = threadIdx.x; d < kWarps * 256; d += kSortThreads) (&s_cnt[0][0])[d] = 0;
+  for (int d = threadIdx.x; d < kScatWarps * 256; d += kScatThreads) (&s_cnt[0][0])[d] = 0;
+  if (threadIdx.x < 256) s_goff[threadIdx.x] = offs[(uint64_t)threadIdx.x * num_tiles + blockIdx.x];
   __syncthreads();
-  const uint64_t base = (uint64_t)blockIdx.x * kSortTile + (uint64_t)wid * (kSortTile / kWarps);
-  uint64_t k_[kSortItems];
-  uint32_t rank_[kSortItems];
+  const uint64_t tile0 = (uint64_t)blockIdx.x * kSortTile;
+  const uint64_t base = tile0 + (uint64_t)wid * (kSortTile / kScatWarps);
+  const uint32_t valid = (uint32_t)min((uint64_t)kSortTile, n - tile0);
+  uint64_t k_[kScatItems];
+  uint32_t rank_[kScatItems];
   const uint32_t lt = (1u << lane) - 1;
 #pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
-    uint64_t idx = base + (uint64_t)r * 32 + lane;
-    bool valid = idx < n;
-    uint64_t key = valid ? keys[idx] : ~0ull;
-    uint32_t d = (uint32_t)(key >> shift) & 255u;
-    // invalid items sit at the end of the last tile: giving them a digit does
-    // not disturb the ranks of valid items before them
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
-    uint32_t before = __popc(peers & lt);
-    uint32_t cnt = s_cnt[wid][d];
+  for (int r = 0; r < kScatItems; ++r) {
+    const uint64_t idx = base + (uint64_t)r * 32 + lane;
+    k_[r] = idx < n ? keys[idx] : ~0ull;
+  }
+#pragma unroll
+  for (int r = 0; r < kScatItems; ++r) {
+    // invalid items sit at the end of the last tile: digit 255 after every
+    // valid item, so they take the last local positions
+    const uint32_t d = (uint32_t)(k_[r] >> shift) & 255u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t before = __popc(peers & lt);
+    const uint32_t cnt = s_cnt[wid][d];
     rank_[r] = cnt + before;
-    k_[r] = key;
     __syncwarp();
     if (before == 0) s_cnt[wid][d] = cnt + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
-  {
-    // per digit: exclusive prefix over warps, plus the tile's global offset
+  // per digit: exclusive prefix over warps; the digit's tile total, then an
+  // exclusive scan over digits (threads 0..255, warps 0..7) gives its first
+  // local position
+  uint32_t run = 0, x = 0;
+  if (threadIdx.x < 256) {
     const uint32_t d = threadIdx.x;
-    uint32_t run = offs[(uint64_t)d * num_tiles + blockIdx.x];
-    for (int w = 0; w < kWarps; ++w) {
-      uint32_t c = s_cnt[w][d];
+    for (int w = 0; w < kScatWarps; ++w) {
+      const uint32_t c = s_cnt[w][d];
       s_cnt[w][d] = run;
       run += c;
+    }
+    x = run;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[wid] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 256) {
+    uint32_t pre = 0;
+    for (int w = 0; w < wid; ++w) pre += s_wsum[w];
+    s_start[threadIdx.x] = pre + x - run;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kScatItems; ++r) {
+    const uint32_t d = (uint32_t)(k_[r] >> shift) & 255u;
+    const uint32_t pos = s_start[d] + s_cnt[wid][d] + rank_[r];
+    s_keys[pos] = k_[r];
+    if (vals) {
+      const uint64_t idx = base + (uint64_t)r * 32 + lane;
+      s_vals[pos] = idx < n ? vals[idx] : 0u;
     }
   }
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
-    uint64_t idx = base + (uint64_t)r * 32 + lane;
-    if (idx < n) {
-      uint32_t d = (uint32_t)(k_[r] >> shift) & 255u;
-      uint32_t dst = s_cnt[wid][d] + rank_[r];
-      keys_out[dst] = k_[r];
-      if (vals) vals_out[dst] = vals[idx];
+  for (int r = 0; r < kScatItems; ++r) {
+    const uint32_t i = (uint32_t)r * kScatThreads + threadIdx.x;
+    if (i < valid) {
+      const uint64_t key = s_keys[i];
+      const uint32_t d = (uint32_t)(key >> shift) & 255u;
+      const uint32_t dst = s_goff[d] + (i - s_start[d]);
+      keys_out[dst] = key;
+      if (vals) vals_out[dst] = s_vals[i];
     }
   }
 }
@@ -234,11 +277,14 @@ int radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t*
   uint32_t* src_v = vals;
   uint32_t* dst_v = vals_alt;
   bool alt = false;
+  MJ_CUDA_TRY(cudaFuncSetAttribute(radix_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kScatterSmem));
   for (int shift = bit_lo; shift < bit_hi; shift += 8) {
     radix_hist_kernel<<<tiles, kSortThreads, 0, s>>>(src_k, n, shift, tiles, hist);
     MJ_KERNEL_DONE();
     MJ_TRY(launch_exclusive_scan_u32(hist, offs, h, scan_tmp, nullptr, s));
-    radix_scatter_kernel<<<tiles, kSortThreads, 0, s>>>(src_k, src_v, n, shift, tiles, offs, dst_k, dst_v);
+    radix_scatter_kernel<<<tiles, kScatThreads, kScatterSmem, s>>>(src_k, src_v, n, shift, tiles, offs, dst_k,
+                                                                    dst_v);
     MJ_KERNEL_DONE();
     std::swap(src_k, dst_k);
     std::swap(src_v, dst_v);
