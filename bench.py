@@ -37,9 +37,17 @@ METRIC = "join wall time & verified DP cells/s; learned-band vs plain K-band, id
 UNIT = "cells/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-SM_COUNT = 152
-INT_LANES_PER_SM = 64        # 32-bit integer ALU lanes per SM and clock (4 partitions x 16)
+# 32-bit integer ALU lanes per SM and clock by compute capability major
+# (Blackwell SMs: 4 partitions x 16 lanes); the SM count and clock are read
+# from the device and from the sampled clocks
+INT_LANES_PER_SM = {10: 64, 12: 64, 9: 64}
 ALU_OPS_PER_WORD_COLUMN = 16 # ops of one band word in one column of the bit-vector recurrence
+RECORD_BYTES = 24            # one partition record written: sid, pos, len, string length (u32), key (u64)
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# capture of the same launch (dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by (section, workload number); None where no capture of the current
+# kernel exists
+TRAFFIC_BYTES = {}
 
 
 def band_cells(m: np.ndarray, n: np.ndarray, K: int) -> int:
@@ -310,10 +318,13 @@ def run_native(args):
         hbm_src = "measured" if hbm else "fallback"
         hbm = hbm or FALLBACK_HBM_GBS
         sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
+        props = torch.cuda.get_device_properties(dev)
+        alu = {"sms": props.multi_processor_count, "lanes": INT_LANES_PER_SM.get(props.major, 64), "mhz": sm_mhz}
         nbytes = int(s.bytes.shape[0])
         # dominant kernel: the section with the largest share of the step
         dom = max(sec_ms, key=lambda k: sec_ms[k])
-        roof = roofline(dom, sec_ms[dom], last, nbytes, hbm, hbm_src, sm_mhz, args)
+        roof = roofline(dom, sec_ms[dom], last, nbytes, hbm, hbm_src, alu, cfg)
+        part_roof = partition_roofline(sec_ms, last, nbytes, hbm, hbm_src)
         line = {
             "metric": METRIC, "value": cells_all / (ms / 1000.0), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -340,6 +351,7 @@ def run_native(args):
             "verify_word_columns": int(last["verify_word_columns"]),
             "sections_ms": {k: round(v, 4) for k, v in sec_ms.items()},
             "roofline": roof,
+            "partition_roofline": part_roof,
             "e2e": {"value": cells_all / (ms_e2e / 1000.0), "unit": UNIT, "ms_per_step": ms_e2e,
                     "h2d_bytes_per_step": nbytes + 8 * (s.n + 1),
                     "d2h_bytes_per_step": 12 * int(e2e_stats["n_output"])},
@@ -359,30 +371,42 @@ def run_native(args):
         dist.destroy_process_group()
 
 
-def roofline(section: str, ms: float, st: dict, nbytes: int, hbm: float, hbm_src: str, sm_mhz: float, args) -> dict:
+def roofline(section: str, ms: float, st: dict, nbytes: int, hbm: float, hbm_src: str, alu: dict, cfg: int) -> dict:
     """Roofline entry of the dominant section, from its algorithmic work."""
     sec = ms / 1000.0
+    traffic = TRAFFIC_BYTES.get((section, cfg))
     if section == "anchor_test":
         # reads every byte once, writes one anchor bit per byte
-        traffic = nbytes + nbytes / 8
-        ach = traffic / sec / 1e9
+        work = nbytes + nbytes / 8
+        ach = work / sec / 1e9
         return {"kernel": section, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "peak_source": hbm_src}
+                "frac": ach / hbm, "traffic": traffic, "peak_source": hbm_src}
     if section in ("record_sort", "pair_dedup"):
         n = st["n_partitions"] if section == "record_sort" else st["n_raw_pairs"]
         per = 24 if section == "record_sort" else 16   # one read and one write of key (+ value)
-        traffic = n * per
-        ach = traffic / sec / 1e9
+        work = n * per
+        ach = work / sec / 1e9
         return {"kernel": section, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "peak_source": hbm_src}
+                "frac": ach / hbm, "traffic": traffic, "peak_source": hbm_src}
     # verification is integer-ALU work: the bit-vector recurrence costs 16
     # 32-bit operations per band word and column (ALU_OPS_PER_WORD_COLUMN),
     # counted over the word-columns the verifier actually advanced
-    peak = SM_COUNT * INT_LANES_PER_SM * sm_mhz * 1e6 / 1e9   # Gop/s
+    peak = alu["sms"] * alu["lanes"] * alu["mhz"] * 1e6 / 1e9   # Gop/s
     ops = st["verify_word_columns"] * ALU_OPS_PER_WORD_COLUMN
     ach = ops / sec / 1e9
     return {"kernel": section, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gop/s", "frac": ach / peak,
-            "traffic": None, "peak_source": f"{SM_COUNT} SMs x {INT_LANES_PER_SM} int32 lanes x {sm_mhz:.0f} MHz"}
+            "traffic": traffic,
+            "peak_source": f"{alu['sms']} SMs x {alu['lanes']} int32 lanes x {alu['mhz']:.0f} MHz (sampled)"}
+
+
+def partition_roofline(sec_ms: dict, st: dict, nbytes: int, hbm: float, hbm_src: str) -> dict:
+    """The partition stage (q-gram values, anchors, partition records) against
+    HBM: every input byte read once plus one record written per partition."""
+    ms = sec_ms["anchor_test"] + sec_ms["partition_records"]
+    work = nbytes + RECORD_BYTES * st["n_partitions"]
+    ach = work / (ms / 1000.0) / 1e9
+    return {"sections": ["anchor_test", "partition_records"], "bound": "hbm", "achieved": ach, "peak": hbm,
+            "unit": "GB/s", "frac": ach / hbm, "algorithmic_bytes": work, "ms": ms, "peak_source": hbm_src}
 
 
 def main():

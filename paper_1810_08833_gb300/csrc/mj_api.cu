@@ -128,7 +128,14 @@ struct mj_ctx {
   uint32_t band_margin = 0, band_min_mult = 2;
   bool band_gate_auto = false;   // set band_min_mult from the training data
   int band_step = 0;
-  Buf feat_x, mult, run_start, parts, yhat, kband, vlist, vflags, voffs;
+  Buf feat_x, mult, run_start, parts, yhat, kband;
+  // learned first passes: bucket-sorted order, per-bucket ranges and work
+  // counters, and the streams the bucket launches run on concurrently
+  Buf lvals, franges, fnext, fcnt, ed_first;
+  static constexpr int kAuxStreams = 8;
+  cudaStream_t aux[kAuxStreams] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kAuxStreams] = {};
   bool have_features = false;
   bool work_started = false;   // verification counters cleared in this call
   bool planes_ready = false;
@@ -417,10 +424,23 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
 }
 
 // a8 on arbitrary pairs (rank codes from c->d).
+// Device flags and verification counters cleared for this call (once), on s.
+int verify_prep(mj_ctx* c, cudaStream_t s) {
+  MJ_TRY(c->dev_flags.reserve(64, s));
+  MJ_CUDA_TRY(cudaMemsetAsync(c->dev_flags.p, 0, 64, s));
+  MJ_TRY(c->small.reserve(64, s));
+  if (!c->work_started) {
+    MJ_CUDA_TRY(cudaMemsetAsync(c->small.p, 0, 48, s));
+    c->work_started = true;
+  }
+  return MJ_OK;
+}
+
 int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const uint32_t* d_i, const uint32_t* d_j,
            const uint32_t* d_k, uint64_t m, uint32_t K, uint32_t kmax, uint32_t* d_ed, bool count_cells,
            cudaStream_t s, const uint32_t* order = nullptr, const uint32_t* skip_kband = nullptr,
-           const uint32_t* range_lo = nullptr, const uint32_t* range_hi = nullptr, int kernel = -1, int lanes = -1) {
+           const uint32_t* range_lo = nullptr, const uint32_t* range_hi = nullptr, int kernel = -1, int lanes = -1,
+           unsigned long long* next = nullptr, bool prep = true, const uint32_t* first_ed = nullptr) {
   const Derived& d = c->d;
   if (m == 0) return MJ_OK;
   if (kmax >= (1u << 16)) return MJ_ERR_UNSUPPORTED;
@@ -438,13 +458,7 @@ int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const ui
     MJ_TRY(launch_build_planes(d_bytes, nbytes, rt, d.bits, c->planes.as<uint32_t>(), PW, GW, s));
     tstop(c, 5, s);
   }
-  MJ_TRY(c->dev_flags.reserve(64, s));
-  MJ_CUDA_TRY(cudaMemsetAsync(c->dev_flags.p, 0, 64, s));
-  MJ_TRY(c->small.reserve(64, s));
-  if (!c->work_started) {
-    MJ_CUDA_TRY(cudaMemsetAsync(c->small.p, 0, 48, s));
-    c->work_started = true;
-  }
+  if (prep) MJ_TRY(verify_prep(c, s));
   VerifyArgs a;
   a.planes = c->planes.as<uint32_t>();
   a.bits = d.bits;
@@ -456,6 +470,7 @@ int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const ui
   a.pk = d_k;
   a.order = order;
   a.skip_kband = skip_kband;
+  a.first_ed = first_ed;
   a.range_lo = range_lo;
   a.range_hi = range_hi;
   a.skipped = skip_kband ? c->small.as<unsigned long long>() + 4 : nullptr;
@@ -472,7 +487,7 @@ int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const ui
     kk = MJ_VERIFY_KERNEL_AUTO;
     ll = 0;
   }
-  MJ_TRY(launch_verify(a, PW, GW, kmax, c->small.as<unsigned long long>() + 1, s, kk, ll));
+  MJ_TRY(launch_verify(a, PW, GW, kmax, next ? next : c->small.as<unsigned long long>() + 1, s, kk, ll));
   tstop(c, 6, s);
   return MJ_OK;
 }
@@ -608,8 +623,7 @@ int verify_stage(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, ui
   const bool want_x = (p->flags & MJ_FLAG_FEATURES) != 0;
   if (want_feat) {
     MJ_TRY(c->parts.reserve((size_t)n * 4 + 16, s));
-    MJ_CUDA_TRY(cudaMemsetAsync(c->parts.p, 0, (size_t)n * 4, s));
-    MJ_TRY(launch_partition_counts(c->anchor_sid.as<uint32_t>(), c->n_part, c->parts.as<uint32_t>(), s));
+    MJ_TRY(launch_partition_counts(c->anchor_sid.as<uint32_t>(), c->n_part, n, c->parts.as<uint32_t>(), s));
   }
   if (want_x) {
     MJ_TRY(c->mult.reserve(m * 4, s));
@@ -630,40 +644,56 @@ int verify_stage(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, ui
     const uint32_t* order;
     MJ_TRY(pair_order(c, ci, cj, d_offsets, m, &skeys, &order, s));
     MJ_TRY(c->kband.reserve(m * 4, s));
-    MJ_TRY(c->vflags.reserve(m * 4, s));
-    MJ_TRY(c->voffs.reserve(m * 4 + 16, s));
-    MJ_TRY(c->vlist.reserve(m * 4 + 16, s));
-    MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(m), s));
+    MJ_TRY(c->lvals.reserve(m * 4 + 16, s));
+    MJ_TRY(c->franges.reserve(8 * (kMaxBandBuckets + 2), s));
+    MJ_TRY(c->fnext.reserve(8 * (kMaxBandBuckets + 2), s));
+    MJ_TRY(c->fcnt.reserve(8 * (kMaxBandBuckets + 2), s));
     MJ_TRY(launch_band_fused(c->band.as<float>(), ci, cj, c->run_start.as<uint32_t>(), c->stats.n_raw_pairs,
                              c->parts.as<uint32_t>(), d_offsets, m, K, c->d.T, c->band_margin, c->band_min_mult,
                              c->kband.as<uint32_t>(), s));
-    uint32_t* tot = c->voffs.as<uint32_t>() + m;
-    uint64_t first = 0;
-    int st = MJ_OK;
+    // the pairs of each first-pass bucket, listed contiguously
     const uint32_t wK = (K + 1 + 31) / 32;
-    // first passes: one launch per group of band widths (exact word counts up
-    // to 8 words, power-of-two ranges beyond)
-    for (uint32_t wlo = 1; wlo < wK;) {
-      const uint32_t whi = std::min(wK, wK <= 8 ? wlo + 1 : 2 * wlo);
-      MJ_TRY(launch_bucket_flags(c->kband.as<uint32_t>(), order, m, K, wlo, whi, c->vflags.as<uint32_t>(), s));
-      MJ_TRY(launch_exclusive_scan_u32(c->vflags.as<uint32_t>(), c->voffs.as<uint32_t>(), m, c->scan_tmp.p, tot, s));
-      const uint64_t cnt = readback_u32(c, tot, s, &st);
-      MJ_TRY(st);
-      if (cnt) {
-        MJ_TRY(launch_compact_index(c->vflags.as<uint32_t>(), c->voffs.as<uint32_t>(), order, m,
-                                    c->vlist.as<uint32_t>(), s));
-        MJ_TRY(verify(c, d_bytes, d_offsets, ci, cj, c->kband.as<uint32_t>(), cnt, K, 32 * (whi - 1) - 1, ed, false,
-                      s, c->vlist.as<uint32_t>()));
-        first += cnt;
-      }
-      wlo = whi;
+    const uint32_t nb = wK <= 1 ? 0 : (wK <= 8 ? wK - 1 : 32 - __builtin_clz(wK - 1));
+    uint32_t* ranges = c->franges.as<uint32_t>();
+    unsigned long long* first_total = c->small.as<unsigned long long>() + 5;
+    MJ_TRY(verify_prep(c, s));
+    const uint32_t* forder = c->lvals.as<uint32_t>();
+    if (nb > 0) {
+      MJ_TRY(launch_band_buckets(c->kband.as<uint32_t>(), m, K, nb, c->fcnt.as<uint32_t>(), ranges,
+                                 c->lvals.as<uint32_t>(), first_total, s));
+      MJ_CUDA_TRY(cudaMemsetAsync(c->fnext.p, 0, 8 * (kMaxBandBuckets + 2), s));
+    } else {
+      MJ_CUDA_TRY(cudaMemsetAsync(first_total, 0, 8, s));
     }
-    // band K for every pair the first passes did not settle
-    MJ_TRY(verify(c, d_bytes, d_offsets, ci, cj, nullptr, m, K, K, ed, false, s, order, c->kband.as<uint32_t>()));
-    MJ_TRY(readback(c, c->small.as<unsigned long long>() + 4, 8, s));
+    // first passes: one persistent launch per bucket (band widths up to the
+    // bucket's word count), all buckets at once on the context's streams,
+    // each reading its range from device memory and writing its own results;
+    // then band K on s for every pair they did not settle (a settled pair
+    // takes its first-pass result)
+    MJ_TRY(c->ed_first.reserve(m * 4, s));
+    MJ_CUDA_TRY(cudaMemsetAsync(c->ed_first.p, 0xff, m * 4, s));
+    tstart(c, 6, s);
+    if (nb > 0) {
+      MJ_CUDA_TRY(cudaEventRecord(c->ev_fork, s));
+      for (uint32_t b = 1; b <= nb; ++b) {
+        const uint32_t whi = wK <= 8 ? b + 1 : std::min(wK, 1u << b);
+        cudaStream_t sb = c->aux[(b - 1) % mj_ctx::kAuxStreams];
+        if (b <= (uint32_t)mj_ctx::kAuxStreams) MJ_CUDA_TRY(cudaStreamWaitEvent(sb, c->ev_fork, 0));
+        MJ_TRY(verify(c, d_bytes, d_offsets, ci, cj, c->kband.as<uint32_t>(), m, K, 32 * (whi - 1) - 1,
+                      c->ed_first.as<uint32_t>(), false, sb, forder, nullptr, ranges + 2 * b, ranges + 2 * b + 1,
+                      -1, -1, c->fnext.as<unsigned long long>() + b, false));
+      }
+      for (uint32_t b = 1; b <= std::min(nb, (uint32_t)mj_ctx::kAuxStreams); ++b) {
+        MJ_CUDA_TRY(cudaEventRecord(c->ev_join[b - 1], c->aux[b - 1]));
+        MJ_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[b - 1], 0));
+      }
+    }
+    MJ_TRY(verify(c, d_bytes, d_offsets, ci, cj, nullptr, m, K, K, ed, false, s, order, c->kband.as<uint32_t>(),
+                  nullptr, nullptr, -1, -1, nullptr, false, c->ed_first.as<uint32_t>()));
+    MJ_TRY(readback(c, c->small.as<unsigned long long>() + 4, 16, s));
     const uint64_t settled = c->h_small[0];
     c->stats.first_pass_settled = settled;
-    c->stats.fallback_pairs = first - settled;
+    c->stats.fallback_pairs = c->h_small[1] - settled;
   }
   c->have_features = want_x;
   return launch_band_cells(ci, cj, d_offsets, m, K, c->small.as<unsigned long long>() + 3, s);
@@ -752,6 +782,16 @@ int mj_create(mj_ctx** ctx, int device) {
       return MJ_ERR_CUDA;
     }
   }
+  bool ok = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; ok && i < mj_ctx::kAuxStreams; ++i) {
+    ok = cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    mj_destroy(c);
+    return MJ_ERR_CUDA;
+  }
   *ctx = c;
   return MJ_OK;
 }
@@ -767,9 +807,14 @@ void mj_destroy(mj_ctx* c) {
                  &c->s_slen, &c->s_len, &c->s_h61, &c->pair_count, &c->pair_off, &c->pairs, &c->pairs_alt,
                  &c->uflags, &c->uoffs, &c->cand_i, &c->cand_j, &c->planes, &c->ed, &c->eflags, &c->eoffs,
                  &c->out_i, &c->out_j, &c->out_ed, &c->in_bytes, &c->in_offsets, &c->branges,
-                 &c->band, &c->feat_x, &c->mult, &c->run_start, &c->parts, &c->yhat, &c->kband, &c->vlist,
-                 &c->vflags, &c->voffs};
+                 &c->band, &c->feat_x, &c->mult, &c->run_start, &c->parts, &c->yhat, &c->kband, &c->lvals,
+                 &c->franges, &c->fnext, &c->fcnt, &c->ed_first};
   for (Buf* b : bufs) b->release();
+  for (int i = 0; i < mj_ctx::kAuxStreams; ++i) {
+    if (c->aux[i]) cudaStreamDestroy(c->aux[i]);
+    if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : c->sec_ev)

@@ -202,43 +202,76 @@ __global__ void multiplicity_kernel(const uint32_t* __restrict__ run_start, uint
   }
 }
 
-__global__ void partition_counts_kernel(const uint32_t* __restrict__ sid, uint64_t n_anchor,
+// parts[s] = number of anchors (= partitions) of string s: the anchor list
+// is in string order, so it is the width of s's run, found by two binary
+// searches per string
+__device__ __forceinline__ uint64_t lower_bound_u32(const uint32_t* __restrict__ a, uint64_t n, uint32_t v) {
+  uint64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (a[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void partition_counts_kernel(const uint32_t* __restrict__ sid, uint64_t n_anchor, uint32_t n,
                                         uint32_t* __restrict__ parts) {
-  // the anchor list is in string order: count runs of equal string ids
-  for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n_anchor;
-       a += (uint64_t)gridDim.x * blockDim.x) {
-    if (a == 0 || sid[a] != sid[a - 1]) {
-      uint64_t e = a + 1;
-      while (e < n_anchor && sid[e] == sid[a]) ++e;
-      parts[sid[a]] = (uint32_t)(e - a);
+  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (uint64_t)gridDim.x * blockDim.x)
+    parts[s] = (uint32_t)(lower_bound_u32(sid, n_anchor, (uint32_t)s + 1) - lower_bound_u32(sid, n_anchor, (uint32_t)s));
+}
+
+// First-pass bucket of a learned band k (0: no first pass).  Band widths
+// (words of k + 1 bits) below the band-K word count wK: one bucket per word
+// count when wK <= 8, else power-of-two ranges [1,2), [2,4), ...
+__device__ __forceinline__ uint32_t first_pass_bucket(uint32_t k, uint32_t K, uint32_t wK) {
+  if (k >= K) return 0;
+  const uint32_t kw = (k + 1 + 31) / 32;
+  if (kw >= wK) return 0;
+  return wK <= 8 ? kw : 32 - __clz(kw);
+}
+
+// cnt[b] += pairs t with first-pass bucket b >= 1 (warp-aggregated)
+__global__ void band_bucket_count_kernel(const uint32_t* __restrict__ kband, uint64_t m, uint32_t K, uint32_t wK,
+                                         uint32_t* __restrict__ cnt) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t b = first_pass_bucket(kband[t], K, wK);
+    const uint32_t active = __activemask();
+    const uint32_t peers = __match_any_sync(active, b);
+    if (b && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(cnt + b, __popc(peers));
+  }
+}
+
+// ranges[2b], ranges[2b+1] = [start, end) of bucket b (b = 1 .. nb) in the
+// list, from the counts; cursor[b] = start; *first_total = all first-pass pairs
+__global__ void band_bucket_ranges_kernel(const uint32_t* __restrict__ cnt, uint32_t nb, uint32_t* __restrict__ ranges,
+                                          uint32_t* __restrict__ cursor, unsigned long long* __restrict__ first_total) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    uint32_t run = 0;
+    ranges[0] = ranges[1] = 0;
+    for (uint32_t b = 1; b <= nb; ++b) {
+      ranges[2 * b] = run;
+      cursor[b] = run;
+      run += cnt[b];
+      ranges[2 * b + 1] = run;
     }
+    if (first_total) *first_total = run;
   }
 }
 
-__global__ void bucket_flags_kernel(const uint32_t* __restrict__ kband, const uint32_t* __restrict__ order, uint64_t m,
-                                    uint32_t K, uint32_t wlo, uint32_t whi, uint32_t* __restrict__ flags) {
-  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t u = order ? order[q] : q;
-    const uint32_t k = kband[u];
-    const uint32_t kw = (k + 1 + 31) / 32;
-    flags[q] = (k < K && kw >= wlo && kw < whi) ? 1u : 0u;
+// list[cursor[b]++] = t for every pair t with first-pass bucket b >= 1
+__global__ void band_bucket_scatter_kernel(const uint32_t* __restrict__ kband, uint64_t m, uint32_t K, uint32_t wK,
+                                           uint32_t* __restrict__ cursor, uint32_t* __restrict__ list) {
+  const int lane = threadIdx.x & 31;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t b = first_pass_bucket(kband[t], K, wK);
+    const uint32_t active = __activemask();
+    const uint32_t peers = __match_any_sync(active, b);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (b && lane == leader) base = atomicAdd(cursor + b, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    if (b) list[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)t;
   }
-}
-
-__global__ void fallback_flags_kernel(const uint32_t* __restrict__ kband, const uint32_t* __restrict__ ed,
-                                      const uint32_t* __restrict__ order, uint64_t m, uint32_t K,
-                                      uint32_t* __restrict__ flags) {
-  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t u = order ? order[q] : q;
-    const uint32_t k = kband[u];
-    flags[q] = (k >= K || ed[u] > k) ? 1u : 0u;
-  }
-}
-
-__global__ void compact_index_kernel(const uint32_t* __restrict__ flags, const uint32_t* __restrict__ offs,
-                                     const uint32_t* __restrict__ order, uint64_t m, uint32_t* __restrict__ out) {
-  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x)
-    if (flags[q]) out[offs[q]] = order ? order[q] : (uint32_t)q;
 }
 
 // K-band cells of every candidate, summed (mj_stats.band_cells).
@@ -393,34 +426,29 @@ int launch_multiplicity(const uint32_t* run_start, uint64_t nc, uint64_t raw, ui
   return MJ_OK;
 }
 
-int launch_partition_counts(const uint32_t* anchor_sid, uint64_t n_anchor, uint32_t* parts, cudaStream_t s) {
-  if (!n_anchor) return MJ_OK;
-  partition_counts_kernel<<<grid_for(n_anchor), 256, 0, s>>>(anchor_sid, n_anchor, parts);
+int launch_partition_counts(const uint32_t* anchor_sid, uint64_t n_anchor, uint32_t n, uint32_t* parts,
+                            cudaStream_t s) {
+  if (!n) return MJ_OK;
+  partition_counts_kernel<<<grid_for(n), 256, 0, s>>>(anchor_sid, n_anchor, n, parts);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
-int launch_bucket_flags(const uint32_t* kband, const uint32_t* order, uint64_t m, uint32_t K, uint32_t wlo,
-                        uint32_t whi, uint32_t* flags, cudaStream_t s) {
-  if (!m) return MJ_OK;
-  bucket_flags_kernel<<<grid_for(m), 256, 0, s>>>(kband, order, m, K, wlo, whi, flags);
+int launch_band_buckets(const uint32_t* kband, uint64_t m, uint32_t K, uint32_t nb, uint32_t* cnt, uint32_t* ranges,
+                        uint32_t* list, unsigned long long* first_total, cudaStream_t s) {
+  const uint32_t wK = (K + 1 + 31) / 32;
+  MJ_CUDA_TRY(cudaMemsetAsync(cnt, 0, 4 * (kMaxBandBuckets + 2), s));
+  if (m) {
+    band_bucket_count_kernel<<<grid_for(m), 256, 0, s>>>(kband, m, K, wK, cnt);
+    MJ_KERNEL_DONE();
+  }
+  uint32_t* cursor = cnt + kMaxBandBuckets + 2;
+  band_bucket_ranges_kernel<<<1, 32, 0, s>>>(cnt, nb, ranges, cursor, first_total);
   MJ_KERNEL_DONE();
-  return MJ_OK;
-}
-
-int launch_fallback_flags(const uint32_t* kband, const uint32_t* ed, const uint32_t* order, uint64_t m, uint32_t K,
-                          uint32_t* flags, cudaStream_t s) {
-  if (!m) return MJ_OK;
-  fallback_flags_kernel<<<grid_for(m), 256, 0, s>>>(kband, ed, order, m, K, flags);
-  MJ_KERNEL_DONE();
-  return MJ_OK;
-}
-
-int launch_compact_index(const uint32_t* flags, const uint32_t* offs, const uint32_t* order, uint64_t m, uint32_t* out,
-                         cudaStream_t s) {
-  if (!m) return MJ_OK;
-  compact_index_kernel<<<grid_for(m), 256, 0, s>>>(flags, offs, order, m, out);
-  MJ_KERNEL_DONE();
+  if (m) {
+    band_bucket_scatter_kernel<<<grid_for(m), 256, 0, s>>>(kband, m, K, wK, cursor, list);
+    MJ_KERNEL_DONE();
+  }
   return MJ_OK;
 }
 

@@ -163,7 +163,8 @@ struct VerifyArgs {
   const uint32_t* pj;
   const uint32_t* pk;        // nullable per-pair band
   const uint32_t* order;     // nullable: pair indices in the order to verify them
-  const uint32_t* skip_kband; // nullable: skip pair t when ed[t] <= skip_kband[t] < K (already settled)
+  const uint32_t* skip_kband; // nullable: skip pair t when fed[t] <= skip_kband[t] < K (already settled)
+  const uint32_t* first_ed;  // nullable: first-pass results fed (else ed itself); a skipped pair copies fed[t] to ed[t]
   const uint32_t* range_lo;  // nullable: with range_hi, process order positions [*range_lo, *range_hi) only
   const uint32_t* range_hi;
   unsigned long long* skipped; // nullable: number of pairs skipped that way
@@ -225,15 +226,16 @@ int launch_band_rule(const float* yhat, const uint32_t* ci, const uint32_t* cj, 
 // multiplicity of every candidate from the run starts written by the pair
 // compaction; partitions per string from the anchor list
 int launch_multiplicity(const uint32_t* run_start, uint64_t nc, uint64_t raw, uint32_t* mult, cudaStream_t s);
-int launch_partition_counts(const uint32_t* anchor_sid, uint64_t n_anchor, uint32_t* parts, cudaStream_t s);
-// subset lists for the two verification passes
-// (order nullable: flags[q] refer to candidate order[q]; the list holds candidate ids)
-int launch_bucket_flags(const uint32_t* kband, const uint32_t* order, uint64_t m, uint32_t K, uint32_t wlo,
-                        uint32_t whi, uint32_t* flags, cudaStream_t s);
-int launch_fallback_flags(const uint32_t* kband, const uint32_t* ed, const uint32_t* order, uint64_t m, uint32_t K,
-                          uint32_t* flags, cudaStream_t s);
-int launch_compact_index(const uint32_t* flags, const uint32_t* offs, const uint32_t* order, uint64_t m, uint32_t* out,
-                         cudaStream_t s);
+int launch_partition_counts(const uint32_t* anchor_sid, uint64_t n_anchor, uint32_t n, uint32_t* parts,
+                            cudaStream_t s);
+// Learned first passes: the pairs of every first-pass bucket b = 1 .. nb
+// (band widths below band K's word count; bucket 0 = no first pass) listed
+// contiguously in list, bucket b at [ranges[2b], ranges[2b+1]); cnt holds
+// 2 * (kMaxBandBuckets + 2) words of scratch; *first_total = pairs listed.
+constexpr uint32_t kMaxBandBuckets = 16;
+int launch_band_buckets(const uint32_t* kband, uint64_t m, uint32_t K, uint32_t nb, uint32_t* cnt, uint32_t* ranges,
+                        uint32_t* list, unsigned long long* first_total, cudaStream_t s);
+// K-band cells of every candidate, summed into *out
 int launch_band_cells(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m, uint32_t K,
                       unsigned long long* out, cudaStream_t s);
 

@@ -92,6 +92,7 @@ extern "C" int mj_verify_static(const uint8_t* d_bytes, const int64_t* d_offsets
   a.pk = nullptr;
   a.order = nullptr;
   a.skip_kband = nullptr;
+  a.first_ed = nullptr;
   a.range_lo = nullptr;
   a.range_hi = nullptr;
   a.skipped = nullptr;

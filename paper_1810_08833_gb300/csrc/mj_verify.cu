@@ -306,7 +306,9 @@ __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t
           const uint64_t t = a.order ? a.order[q] : q;
           // a pair the first pass already decided needs nothing: the lane
           // stays idle and fetches again at the next iteration
-          const bool settled = a.skip_kband && a.skip_kband[t] < a.K && a.ed[t] <= a.skip_kband[t];
+          const uint32_t* fed = a.first_ed ? a.first_ed : a.ed;
+          const bool settled = a.skip_kband && a.skip_kband[t] < a.K && fed[t] <= a.skip_kband[t];
+          if (settled && a.first_ed) a.ed[t] = fed[t];
           nskip += settled ? 1 : 0;
           if (!settled) {
             if (a.cells) {
@@ -499,8 +501,10 @@ __global__ void __launch_bounds__(128, P <= 2 ? 8 : 1) verify_wave_kernel(Verify
           const uint32_t x = a.pi[t], y = a.pj[t];
           k = a.pk ? a.pk[t] : a.K;
           uint32_t res = 0xffffffffu;
-          const bool skip = a.skip_kband && a.skip_kband[t] < a.K && a.ed[t] <= a.skip_kband[t];
+          const uint32_t* fed = a.first_ed ? a.first_ed : a.ed;
+          const bool skip = a.skip_kband && a.skip_kband[t] < a.K && fed[t] <= a.skip_kband[t];
           if (skip) {
+            if (a.first_ed && gl == 0) a.ed[t] = fed[t];
             res = 0xfffffffeu;   // settled by the first pass: nothing to do
           } else if (x >= a.n_strings || y >= a.n_strings) {
             if (gl == 0) atomicOr(a.dev_flags, FLAG_BOUNDS);
