@@ -33,6 +33,8 @@
 // concatenated input (plane p holds bit p of every code).  For column j the
 // 32(W+1) plane bits starting at A's row j + dlo are ANDed against the rank of
 // B[j-1] (XNOR per plane) and funnel-shifted into band position.
+#include <algorithm>
+
 #include "mj_internal.cuh"
 
 namespace mj {
@@ -96,13 +98,10 @@ __device__ __forceinline__ uint64_t band_cells(int64_t m, int64_t n, int64_t K) 
 template <int W, int P>
 struct PairState {
   uint32_t Pv[W], Mv[W], M1[W];
-  uint32_t pw[P][W + 1];   // window of A's plane words (row-fixed)
-  uint32_t bw[P];          // B's plane bits of the current 32 columns
-  uint64_t wbase;          // plane word index of pw[.][0]
-  uint64_t bpos;           // plane bit index of B's next column symbol
-  int64_t j, n;            // next column, number of columns
+  uint64_t abit;           // plane bit index of the band's top row at column 1
+  uint64_t bpos;           // plane bit index of B's symbol of column j
+  int32_t j, n;            // next column, number of columns
   int32_t score;           // D at the band's top row
-  uint32_t sh;             // bit offset of the window in pw
   uint32_t k;              // band of this pair
   uint64_t t;              // pair index
 };
@@ -110,8 +109,8 @@ struct PairState {
 // Sets up pair t; returns false if the pair is decided without the DP
 // (result written to *res).
 template <int W, int P>
-__device__ __forceinline__ bool pair_init(PairState<W, P>& st, const VerifyArgs& a, uint64_t PW, uint32_t GW,
-                                          uint64_t t, uint32_t* res) {
+__device__ __forceinline__ bool pair_init(PairState<W, P>& st, const VerifyArgs& a, uint32_t GW, uint64_t t,
+                                          uint32_t* res) {
   const uint32_t x = a.pi[t], y = a.pj[t];
   const uint32_t k = a.pk ? a.pk[t] : a.K;
   st.t = t;
@@ -133,6 +132,11 @@ __device__ __forceinline__ bool pair_init(PairState<W, P>& st, const VerifyArgs&
   }
   if (n == 0) {
     *res = (uint32_t)d0;
+    return false;
+  }
+  if (m >= ((int64_t)1 << 30)) {         // column counters are 32-bit
+    atomicOr(a.dev_flags, FLAG_LENGTH);
+    *res = k + 1;
     return false;
   }
   const int32_t dlo = -(int32_t)(((int64_t)k - d0) >> 1);
@@ -157,72 +161,70 @@ __device__ __forceinline__ bool pair_init(PairState<W, P>& st, const VerifyArgs&
     st.M1[w] = a1 > a0 ? (hiMask & ~loMask) : 0u;
   }
   st.score = -dlo;                       // D[dlo][0] = -dlo
-  const uint64_t S = (uint64_t)(oA + dlo + 32 * (int64_t)GW);  // plane bit of row 1 + dlo (column 1)
-  st.wbase = S >> 5;
-  st.sh = (uint32_t)(S & 31);
-#pragma unroll
-  for (int p = 0; p < P; ++p) {
-#pragma unroll
-    for (int w = 0; w <= W; ++w) st.pw[p][w] = p < (int)a.bits ? __ldg(a.planes + (uint64_t)p * PW + st.wbase + w) : 0u;
-  }
+  st.abit = (uint64_t)(oA + dlo + 32 * (int64_t)GW);   // plane bit of row 1 + dlo (column 1)
   st.bpos = (uint64_t)(oB + 32 * (int64_t)GW);
   st.j = 1;
-  st.n = n;
+  st.n = (int32_t)n;
   return true;
 }
 
 constexpr int kChunk = 16;   // columns between two early-exit checks
 
 // Advances up to kChunk columns; returns true when the pair is decided.
+// The chunk's symbols are loaded at its start for every lane at once: A's
+// plane words of the rows the band covers in these columns (pre-shifted so
+// that column j0 + c needs a shift by c < 32), and B's plane bits of the
+// columns, bit-reversed so that the next column's bit is the sign bit.
 template <int W, int P>
 __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs& a, uint64_t PW, uint32_t* res) {
-  // B's symbol bits for columns j .. j+kChunk-1
+  const int32_t j0 = st.j;
+  uint32_t pa[P][W + 1];
+  uint32_t bw[P];
   {
+    const uint64_t ab = st.abit + (uint64_t)(j0 - 1);
+    const uint64_t aw = ab >> 5;
+    const uint32_t ash = (uint32_t)(ab & 31);
     const uint64_t wb = st.bpos >> 5;
     const uint32_t sb = (uint32_t)(st.bpos & 31);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       if (p < (int)a.bits) {
-        const uint32_t lo = __ldg(a.planes + (uint64_t)p * PW + wb);
-        const uint32_t hi = __ldg(a.planes + (uint64_t)p * PW + wb + 1);
-        st.bw[p] = __funnelshift_r(lo, hi, sb);
+        const uint32_t* plane = a.planes + (uint64_t)p * PW;
+        uint32_t w0 = __ldg(plane + aw);
+#pragma unroll
+        for (int w = 0; w <= W; ++w) {
+          const uint32_t w1 = __ldg(plane + aw + w + 1);
+          pa[p][w] = __funnelshift_r(w0, w1, ash);
+          w0 = w1;
+        }
+        bw[p] = __brev(__funnelshift_r(__ldg(plane + wb), __ldg(plane + wb + 1), sb));
       } else {
-        st.bw[p] = 0;
+#pragma unroll
+        for (int w = 0; w <= W; ++w) pa[p][w] = 0u;
+        bw[p] = 0u;
       }
     }
   }
-  const int64_t jend = st.j + (kChunk - 1) < st.n ? st.j + (kChunk - 1) : st.n;
-  const int64_t j0 = st.j;
-#pragma unroll 1
-  for (int64_t j = j0; j <= jend; ++j) {
-    if (j > 1) {
-      st.sh = (st.sh + 1) & 31;
-      if (st.sh == 0) {
-        ++st.wbase;
+  const int32_t cnt = min(kChunk, st.n - j0 + 1);
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-#pragma unroll
-          for (int w = 0; w < W; ++w) st.pw[p][w] = st.pw[p][w + 1];
-          st.pw[p][W] = p < (int)a.bits ? __ldg(a.planes + (uint64_t)p * PW + st.wbase + W) : 0u;
-        }
-      }
-    }
-    // equality bits of column j: XNOR of A's plane bits with B[j-1]'s code
-    const uint32_t c = (uint32_t)(j - j0);
+  for (int c = 0; c < kChunk; ++c) {
+    if (c >= cnt) break;
+    // equality bits of column j0 + c: A's plane bits XNOR B's, over the planes
     uint32_t EqF[W + 1];
 #pragma unroll
     for (int w = 0; w <= W; ++w) EqF[w] = 0xffffffffu;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       if (p < (int)a.bits) {
-        const uint32_t cm = ((st.bw[p] >> c) & 1u) - 1u;   // 0 if B's bit is 1, all ones if 0
+        const uint32_t xb = (uint32_t)__mulhi((int32_t)bw[p], 1);   // B's bit broadcast (sign)
+        bw[p] *= 2u;
 #pragma unroll
-        for (int w = 0; w <= W; ++w) EqF[w] &= st.pw[p][w] ^ cm;
+        for (int w = 0; w <= W; ++w) EqF[w] &= ~(pa[p][w] ^ xb);
       }
     }
     uint32_t Eq[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) Eq[w] = __funnelshift_r(EqF[w], EqF[w + 1], st.sh);
+    for (int w = 0; w < W; ++w) Eq[w] = __funnelshift_r(EqF[w], EqF[w + 1], (uint32_t)c);
 
     // band slides down one row: the new bottom row gets a +1 vertical delta
 #pragma unroll
@@ -251,16 +253,17 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
       Ph[w] = __funnelshift_l(Ph[w - 1], Ph[w], 1);
       Mh[w] = __funnelshift_l(Mh[w - 1], Mh[w], 1);
     }
-    Ph[0] = (Ph[0] << 1) | 1u;
-    Mh[0] = Mh[0] << 1;
+    Ph[0] = Ph[0] * 2u + 1u;
+    Mh[0] = Mh[0] * 2u;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
       st.Pv[w] = Mh[w] | ~(Xv[w] | Ph[w]);
       st.Mv[w] = Ph[w] & Xv[w];
     }
   }
+  const int32_t jend = j0 + cnt - 1;
   st.j = jend + 1;
-  st.bpos += kChunk;
+  st.bpos += (uint64_t)cnt;
   // D on diagonal d0 at column jend: a lower bound of D[m][n] (exact at n)
   int32_t diag = st.score;
 #pragma unroll
@@ -320,7 +323,7 @@ __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t
               }
             }
             uint32_t res;
-            if (pair_init<W, P>(st, a, PW, GW, t, &res)) {
+            if (pair_init<W, P>(st, a, GW, t, &res)) {
               active = true;
             } else {
               a.ed[t] = res;
@@ -332,7 +335,7 @@ __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t
     if (!__any_sync(0xffffffffu, active || more)) break;
     if (active) {
       uint32_t res;
-      const int64_t j_before = st.j;
+      const int32_t j_before = st.j;
       const bool done = pair_chunk<W, P>(st, a, PW, &res);
       work += (uint64_t)(st.j - j_before) * W;
       if (done) {
@@ -673,6 +676,11 @@ int launch_wp(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long*
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, verify_diag_kernel<W, P>, 128, 0);
+  // at least ~3 pairs per lane, so that the shared queue evens out the early
+  // exits (a warp lasts as long as its slowest lane), but at least 3 blocks
+  // per SM to hide the recurrence's latency
+  const uint64_t per_sm_pairs = (a.m + 3ull * 128 * sms - 1) / (3ull * 128 * sms);
+  per_sm = (int)std::min<uint64_t>((uint64_t)per_sm, std::max<uint64_t>(3, per_sm_pairs));
   if (per_sm < 1) per_sm = 1;
   uint64_t need = (a.m + 127) / 128;
   uint64_t grid = (uint64_t)sms * per_sm;
