@@ -44,12 +44,10 @@ INT_LANES_PER_SM = {10: 64, 12: 64, 9: 64}
 ALU_OPS_PER_WORD_COLUMN = 16 # ops of one band word in one column of the bit-vector recurrence
 RECORD_BYTES = 24            # one partition record written: sid, pos, len, string length (u32), key (u64)
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by (section,
-# workload number); absent where no capture of the current kernel exists.
-# Read-length DNA: verify_diag_kernel<4, 2> captured on 3,000 of the 5,000
-# families (32.1 MB per launch), scaled by the candidates (x 1.666) to the
-# full workload: the bit-planes and pair arrays it reads grow with them.
-TRAFFIC_BYTES = {("verify_kernel", 2): 53.5e6}
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current
+# kernel, keyed by (section, workload number); absent (reported as null)
+# where no capture of the current kernel exists
+TRAFFIC_BYTES = {}
 
 
 def band_cells(m: np.ndarray, n: np.ndarray, K: int) -> int:

@@ -103,7 +103,7 @@ struct mj_ctx {
   Buf anchor_pos, anchor_sid;
   Buf rec_sid, rec_pos, rec_len, rec_slen, rec_h61;
   Buf keys, keys_alt, idx, idx_alt, sort_tmp;
-  Buf s_sid, s_pos, s_slen, s_len, s_h61;
+  Buf srec;   // partition records in group order (PRec)
   Buf pair_count, pair_off, pairs, pairs_alt;
   Buf uflags, uoffs, cand_i, cand_j;
   Buf planes, ed, eflags, eoffs;
@@ -362,21 +362,16 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
                         c->idx_alt.as<uint32_t>(), nr, 0, 32 + slen_bits, c->sort_tmp.p, &alt, s));
   const uint64_t* skeys = alt ? c->keys_alt.as<uint64_t>() : c->keys.as<uint64_t>();
   const uint32_t* sidx = alt ? c->idx_alt.as<uint32_t>() : c->idx.as<uint32_t>();
-  MJ_TRY(c->s_sid.reserve((size_t)nr * 4, s));
-  MJ_TRY(c->s_pos.reserve((size_t)nr * 4, s));
-  MJ_TRY(c->s_slen.reserve((size_t)nr * 4, s));
-  MJ_TRY(c->s_len.reserve((size_t)nr * 4, s));
-  MJ_TRY(c->s_h61.reserve((size_t)nr * 8, s));
-  SortedRecs r{c->s_sid.as<uint32_t>(), c->s_pos.as<uint32_t>(), c->s_slen.as<uint32_t>(), c->s_len.as<uint32_t>(),
-               c->s_h61.as<uint64_t>()};
-  MJ_TRY(launch_gather_records(sidx, nr, c->rec_sid.as<uint32_t>(), c->rec_pos.as<uint32_t>(),
-                               c->rec_slen.as<uint32_t>(), c->rec_len.as<uint32_t>(), c->rec_h61.as<uint64_t>(), r,
-                               s));
+  MJ_TRY(c->srec.reserve((size_t)nr * sizeof(PRec), s));
+  const PRec* r = c->srec.as<PRec>();
+  MJ_TRY(launch_gather_records(sidx, skeys, nr, slen_bits, c->rec_sid.as<uint32_t>(), c->rec_pos.as<uint32_t>(),
+                               c->rec_slen.as<uint32_t>(), c->rec_len.as<uint32_t>(), c->rec_h61.as<uint64_t>(),
+                               c->srec.as<PRec>(), s));
   tstop(c, 2, s);
   if (flags & 1u) {
     MJ_TRY(c->small.reserve(64, s));
     MJ_CUDA_TRY(cudaMemsetAsync(c->small.p, 0, 8, s));
-    MJ_TRY(launch_key_check(skeys, r, d_bytes, d_offsets, nr, slen_bits, c->small.as<unsigned long long>(), s));
+    MJ_TRY(launch_key_check(r, d_bytes, d_offsets, nr, c->small.as<unsigned long long>(), s));
     MJ_TRY(readback(c, c->small.p, 8, s));
     c->stats.key_collisions = c->h_small[0];
   }
@@ -384,7 +379,7 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   MJ_TRY(c->pair_off.reserve((size_t)nr * 8 + 16, s));
   MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(nr), s));
   tstart(c, 3, s);
-  MJ_TRY(launch_count_pairs(skeys, r, nr, slen_bits, d.K, c->pair_count.as<uint32_t>(), s));
+  MJ_TRY(launch_count_pairs(r, nr, d.K, c->pair_count.as<uint32_t>(), s));
   uint64_t* total = c->pair_off.as<uint64_t>() + nr;
   MJ_TRY(launch_exclusive_scan_u32_to_u64(c->pair_count.as<uint32_t>(), c->pair_off.as<uint64_t>(), nr,
                                           c->scan_tmp.p, total, s));
@@ -398,7 +393,7 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   MJ_TRY(c->pairs_alt.reserve(raw * 8, s));
   tstart(c, 4, s);
   const int nb = bits_for(n ? n - 1 : 0);   // pair (i, j) packed as i << nb | j
-  MJ_TRY(launch_fill_pairs(skeys, r, nr, slen_bits, d.K, nb, c->pair_off.as<uint64_t>(), c->pairs.as<uint64_t>(), s));
+  MJ_TRY(launch_fill_pairs(r, nr, d.K, nb, c->pair_off.as<uint64_t>(), c->pairs.as<uint64_t>(), s));
   MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(raw), s));
   MJ_TRY(radix_sort_u64(c->pairs.as<uint64_t>(), c->pairs_alt.as<uint64_t>(), nullptr, nullptr, raw, 0, 2 * nb,
                         c->sort_tmp.p, &alt, s));
@@ -803,8 +798,7 @@ void mj_destroy(mj_ctx* c) {
   Buf* bufs[] = {&c->hist, &c->dev_flags, &c->small, &c->bitmap, &c->tile_count, &c->tile_off, &c->scan_tmp,
                  &c->tile_first,
                  &c->anchor_pos, &c->anchor_sid, &c->rec_sid, &c->rec_pos, &c->rec_len, &c->rec_slen,
-                 &c->rec_h61, &c->keys, &c->keys_alt, &c->idx, &c->idx_alt, &c->sort_tmp, &c->s_sid, &c->s_pos,
-                 &c->s_slen, &c->s_len, &c->s_h61, &c->pair_count, &c->pair_off, &c->pairs, &c->pairs_alt,
+                 &c->rec_h61, &c->keys, &c->keys_alt, &c->idx, &c->idx_alt, &c->sort_tmp, &c->srec, &c->pair_count, &c->pair_off, &c->pairs, &c->pairs_alt,
                  &c->uflags, &c->uoffs, &c->cand_i, &c->cand_j, &c->planes, &c->ed, &c->eflags, &c->eoffs,
                  &c->out_i, &c->out_j, &c->out_ed, &c->in_bytes, &c->in_offsets, &c->branges,
                  &c->band, &c->feat_x, &c->mult, &c->run_start, &c->parts, &c->yhat, &c->kband, &c->lvals,

@@ -72,44 +72,58 @@ __global__ void group_keys_kernel(const uint32_t* __restrict__ rec_len, const ui
   }
 }
 
-__global__ void gather_kernel(const uint32_t* __restrict__ idx, uint32_t n, const uint32_t* __restrict__ sid,
-                              const uint32_t* __restrict__ pos, const uint32_t* __restrict__ slen,
-                              const uint32_t* __restrict__ len, const uint64_t* __restrict__ h61, SortedRecs o) {
+__global__ void gather_kernel(const uint32_t* __restrict__ idx, const uint64_t* __restrict__ keys, uint32_t n,
+                              int slen_bits, const uint32_t* __restrict__ sid, const uint32_t* __restrict__ pos,
+                              const uint32_t* __restrict__ slen, const uint32_t* __restrict__ len,
+                              const uint64_t* __restrict__ h61, PRec* __restrict__ o) {
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t s = idx[t];
-    o.sid[t] = sid[s];
-    o.pos[t] = pos[s];
-    o.slen[t] = slen[s];
-    o.len[t] = len[s];
-    o.h61[t] = h61[s];
+    const uint32_t s = idx[t];
+    PRec r;
+    r.h61 = h61[s];
+    r.run = (uint32_t)(keys[t] >> slen_bits);
+    r.slen = slen[s];
+    r.len = len[s];
+    r.sid = sid[s];
+    r.pos = pos[s];
+    r.pad = 0;
+    o[t] = r;
   }
 }
 
-__device__ __forceinline__ int64_t iabs64(int64_t x) { return x < 0 ? -x : x; }
+__device__ __forceinline__ PRec load_rec(const PRec* __restrict__ r, uint64_t u) {
+  const uint4* p = reinterpret_cast<const uint4*>(r + u);
+  const uint4 a = __ldg(p), b = __ldg(p + 1);
+  PRec x;
+  x.h61 = (uint64_t)a.x | ((uint64_t)a.y << 32);
+  x.run = a.z;
+  x.slen = a.w;
+  x.len = b.x;
+  x.sid = b.y;
+  x.pos = b.z;
+  x.pad = b.w;
+  return x;
+}
 
 // Walks the run of record t; EMIT=false counts, EMIT=true writes pairs.
 template <bool EMIT>
-__global__ void pairs_kernel(const uint64_t* __restrict__ keys, SortedRecs r, uint32_t n, int slen_bits, uint32_t K,
-                             int nb, uint32_t* __restrict__ count, const uint64_t* __restrict__ offs,
-                             uint64_t* __restrict__ pairs) {
+__global__ void pairs_kernel(const PRec* __restrict__ r, uint32_t n, uint32_t K, int nb, uint32_t* __restrict__ count,
+                             const uint64_t* __restrict__ offs, uint64_t* __restrict__ pairs) {
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t run = keys[t] >> slen_bits;
-    const uint32_t sid = r.sid[t], len = r.len[t];
-    const int64_t pos = r.pos[t], slen = r.slen[t];
-    const uint64_t h = r.h61[t];
+    const PRec me = load_rec(r, t);
+    const int32_t pos = (int32_t)me.pos, slen = (int32_t)me.slen;
     uint32_t c = 0;
     uint64_t out = EMIT ? offs[t] : 0;
     for (uint64_t u = t + 1; u < n; ++u) {
-      if ((keys[u] >> slen_bits) != run) break;
-      const int64_t slen_u = r.slen[u];
-      if (slen_u - slen > (int64_t)K) break;               // length filter (run sorted by length)
-      if (r.len[u] != len || r.h61[u] != h) continue;        // same partition substring
-      const uint32_t sid_u = r.sid[u];
-      if (sid_u == sid) continue;                            // i != j
-      const int64_t pos_u = r.pos[u];
-      if (iabs64(pos - pos_u) + iabs64((slen - pos) - (slen_u - pos_u)) > (int64_t)K) continue;  // position filter
+      const PRec o = load_rec(r, u);
+      if (o.run != me.run) break;
+      if ((int32_t)o.slen - slen > (int32_t)K) break;      // length filter (run sorted by length)
+      if (o.len != me.len || o.h61 != me.h61) continue;    // same partition substring
+      if (o.sid == me.sid) continue;                       // i != j
+      const int32_t pos_u = (int32_t)o.pos;
+      const int32_t dl = pos - pos_u, dr = (slen - pos) - ((int32_t)o.slen - pos_u);
+      if (abs(dl) + abs(dr) > (int32_t)K) continue;       // position filter
       if (EMIT) {
-        uint32_t a = sid < sid_u ? sid : sid_u, b = sid < sid_u ? sid_u : sid;
+        const uint32_t a = me.sid < o.sid ? me.sid : o.sid, b = me.sid < o.sid ? o.sid : me.sid;
         pairs[out++] = ((uint64_t)a << nb) | b;
       } else {
         ++c;
@@ -121,21 +135,26 @@ __global__ void pairs_kernel(const uint64_t* __restrict__ keys, SortedRecs r, ui
 
 // flags bit 0 check: every record's bytes equal the first record of its
 // (len, key) class inside the run.
-__global__ void key_check_kernel(const uint64_t* __restrict__ keys, SortedRecs r, const uint8_t* __restrict__ bytes,
-                                 const int64_t* __restrict__ offsets, uint32_t n, int slen_bits,
+__global__ void key_check_kernel(const PRec* __restrict__ r, const uint8_t* __restrict__ bytes,
+                                 const int64_t* __restrict__ offsets, uint32_t n,
                                  unsigned long long* __restrict__ mismatches) {
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t run = keys[t] >> slen_bits;
+    const PRec me = load_rec(r, t);
     // first record of the run with the same (len, key)
     uint64_t f = t;
+    PRec first = me;
     for (uint64_t u = t; u-- > 0;) {
-      if ((keys[u] >> slen_bits) != run) break;
-      if (r.len[u] == r.len[t] && r.h61[u] == r.h61[t]) f = u;
+      const PRec o = load_rec(r, u);
+      if (o.run != me.run) break;
+      if (o.len == me.len && o.h61 == me.h61) {
+        f = u;
+        first = o;
+      }
     }
     if (f == t) continue;
-    const uint8_t* a = bytes + offsets[r.sid[t]] + r.pos[t];
-    const uint8_t* b = bytes + offsets[r.sid[f]] + r.pos[f];
-    for (uint32_t x = 0; x < r.len[t]; ++x) {
+    const uint8_t* a = bytes + offsets[me.sid] + me.pos;
+    const uint8_t* b = bytes + offsets[first.sid] + first.pos;
+    for (uint32_t x = 0; x < me.len; ++x) {
       if (a[x] != b[x]) {
         atomicAdd(mismatches, 1ull);
         break;
@@ -351,35 +370,34 @@ int launch_make_group_keys(const uint32_t* rec_len, const uint32_t* rec_slen, co
   return MJ_OK;
 }
 
-int launch_gather_records(const uint32_t* idx, uint32_t n, const uint32_t* sid, const uint32_t* pos,
-                          const uint32_t* slen, const uint32_t* len, const uint64_t* h61, SortedRecs o,
-                          cudaStream_t s) {
+int launch_gather_records(const uint32_t* idx, const uint64_t* keys, uint32_t n, int slen_bits, const uint32_t* sid,
+                          const uint32_t* pos, const uint32_t* slen, const uint32_t* len, const uint64_t* h61,
+                          PRec* o, cudaStream_t s) {
   if (!n) return MJ_OK;
-  gather_kernel<<<grid_for(n), 256, 0, s>>>(idx, n, sid, pos, slen, len, h61, o);
+  gather_kernel<<<grid_for(n), 256, 0, s>>>(idx, keys, n, slen_bits, sid, pos, slen, len, h61, o);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
-int launch_count_pairs(const uint64_t* keys, SortedRecs r, uint32_t n, int slen_bits, uint32_t K, uint32_t* count,
-                       cudaStream_t s) {
+int launch_count_pairs(const PRec* r, uint32_t n, uint32_t K, uint32_t* count, cudaStream_t s) {
   if (!n) return MJ_OK;
-  pairs_kernel<false><<<grid_for(n), 256, 0, s>>>(keys, r, n, slen_bits, K, 0, count, nullptr, nullptr);
+  pairs_kernel<false><<<grid_for(n), 256, 0, s>>>(r, n, K, 0, count, nullptr, nullptr);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
-int launch_fill_pairs(const uint64_t* keys, SortedRecs r, uint32_t n, int slen_bits, uint32_t K, int nb,
-                      const uint64_t* offs, uint64_t* pairs, cudaStream_t s) {
+int launch_fill_pairs(const PRec* r, uint32_t n, uint32_t K, int nb, const uint64_t* offs, uint64_t* pairs,
+                      cudaStream_t s) {
   if (!n) return MJ_OK;
-  pairs_kernel<true><<<grid_for(n), 256, 0, s>>>(keys, r, n, slen_bits, K, nb, nullptr, offs, pairs);
+  pairs_kernel<true><<<grid_for(n), 256, 0, s>>>(r, n, K, nb, nullptr, offs, pairs);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
-int launch_key_check(const uint64_t* keys, SortedRecs r, const uint8_t* bytes, const int64_t* offsets, uint32_t n,
-                     int slen_bits, unsigned long long* mismatches, cudaStream_t s) {
+int launch_key_check(const PRec* r, const uint8_t* bytes, const int64_t* offsets, uint32_t n,
+                     unsigned long long* mismatches, cudaStream_t s) {
   if (!n) return MJ_OK;
-  key_check_kernel<<<grid_for(n), 256, 0, s>>>(keys, r, bytes, offsets, n, slen_bits, mismatches);
+  key_check_kernel<<<grid_for(n), 256, 0, s>>>(r, bytes, offsets, n, mismatches);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }

@@ -126,23 +126,23 @@ int radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t*
 int launch_make_group_keys(const uint32_t* rec_len, const uint32_t* rec_slen, const uint64_t* rec_h61,
                            uint32_t n_rec, int slen_bits, uint64_t* keys, uint32_t* idx,
                            cudaStream_t s);
-struct SortedRecs {
-  uint32_t* sid;
-  uint32_t* pos;
-  uint32_t* slen;
-  uint32_t* len;
-  uint64_t* h61;
+// A partition record in group order, packed for the walks of the pair
+// emission (two 16-byte loads): Karp-Rabin key, group run (the 32 hash bits
+// of the sort key), string length, partition length, string id, position.
+struct alignas(16) PRec {
+  uint64_t h61;
+  uint32_t run, slen, len, sid, pos, pad;
 };
-int launch_gather_records(const uint32_t* idx, uint32_t n_rec, const uint32_t* rec_sid,
-                          const uint32_t* rec_pos, const uint32_t* rec_slen, const uint32_t* rec_len,
-                          const uint64_t* rec_h61, SortedRecs out, cudaStream_t s);
-int launch_count_pairs(const uint64_t* keys, SortedRecs r, uint32_t n_rec, int slen_bits, uint32_t K,
-                       uint32_t* count, cudaStream_t s);
+static_assert(sizeof(PRec) == 32, "PRec is two 16-byte words");
+int launch_gather_records(const uint32_t* idx, const uint64_t* keys, uint32_t n_rec, int slen_bits,
+                          const uint32_t* rec_sid, const uint32_t* rec_pos, const uint32_t* rec_slen,
+                          const uint32_t* rec_len, const uint64_t* rec_h61, PRec* out, cudaStream_t s);
+int launch_count_pairs(const PRec* r, uint32_t n_rec, uint32_t K, uint32_t* count, cudaStream_t s);
 // pairs are packed as (i << nb) | j, i < j
-int launch_fill_pairs(const uint64_t* keys, SortedRecs r, uint32_t n_rec, int slen_bits, uint32_t K, int nb,
-                      const uint64_t* offs, uint64_t* pairs, cudaStream_t s);
-int launch_key_check(const uint64_t* keys, SortedRecs r, const uint8_t* bytes, const int64_t* offsets,
-                     uint32_t n_rec, int slen_bits, unsigned long long* mismatches, cudaStream_t s);
+int launch_fill_pairs(const PRec* r, uint32_t n_rec, uint32_t K, int nb, const uint64_t* offs, uint64_t* pairs,
+                      cudaStream_t s);
+int launch_key_check(const PRec* r, const uint8_t* bytes, const int64_t* offsets, uint32_t n_rec,
+                     unsigned long long* mismatches, cudaStream_t s);
 // a7: unique of sorted u64 pairs -> flags; then compaction.
 int launch_unique_flags(const uint64_t* sorted, uint64_t n, uint32_t* flags, cudaStream_t s);
 // run_start (nullable): run_start[u] = index of candidate u's first raw pair
