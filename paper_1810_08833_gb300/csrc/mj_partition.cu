@@ -439,29 +439,56 @@ __device__ __forceinline__ uint64_t mulmod61(uint64_t a, uint64_t b) {
   return r >= kM61 ? r - kM61 : r;
 }
 
+__device__ __forceinline__ uint64_t addmod61(uint64_t a, uint64_t b) {
+  uint64_t r = a + b;   // a, b < 2^61: no overflow
+  return r >= kM61 ? r - kM61 : r;
+}
+
 // One partition per anchor: it runs to the next anchor of the same string,
-// else to the string's end (Alg. 1).  The key is a Karp-Rabin polynomial of
-// the substring modulo 2^61-1 with base `key_base`, over symbols byte+1.
-__global__ void partition_records_kernel(const uint8_t* __restrict__ bytes, const int64_t* __restrict__ offsets,
-                                         const uint32_t* __restrict__ anchor_pos,
-                                         const uint32_t* __restrict__ anchor_sid, uint32_t n_anchor,
-                                         uint64_t key_base, uint32_t* __restrict__ rec_sid,
-                                         uint32_t* __restrict__ rec_pos, uint32_t* __restrict__ rec_len,
-                                         uint32_t* __restrict__ rec_slen, uint64_t* __restrict__ rec_h61) {
+// else to the string's end (Alg. 1).  The key is the Karp-Rabin polynomial
+// sum of (byte + 1) * base^(len-1-x) modulo 2^61-1, evaluated by Horner's
+// rule four bytes per modular multiply: with T_k[c] = (c+1) * base^k (k = 1..3,
+// shared-memory tables built per block), a block of four bytes adds
+// T3[b0] + T2[b1] + T1[b2] + (b3+1) to h * base^4.  The key equals the
+// byte-at-a-time polynomial.
+constexpr int kRecThreads = 256;
+
+__global__ void __launch_bounds__(kRecThreads) partition_records_kernel(
+    const uint8_t* __restrict__ bytes, const int64_t* __restrict__ offsets, const uint32_t* __restrict__ anchor_pos,
+    const uint32_t* __restrict__ anchor_sid, uint32_t n_anchor, uint64_t key_base, uint32_t* __restrict__ rec_sid,
+    uint32_t* __restrict__ rec_pos, uint32_t* __restrict__ rec_len, uint32_t* __restrict__ rec_slen,
+    uint64_t* __restrict__ rec_h61) {
+  __shared__ uint64_t s_t[3][256];
+  const uint64_t b2 = mulmod61(key_base, key_base), b3 = mulmod61(b2, key_base), b4 = mulmod61(b3, key_base);
+  {
+    const uint64_t c1 = (uint64_t)threadIdx.x + 1;
+    s_t[0][threadIdx.x] = mulmod61(c1, key_base);
+    s_t[1][threadIdx.x] = mulmod61(c1, b2);
+    s_t[2][threadIdx.x] = mulmod61(c1, b3);
+  }
+  __syncthreads();
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_anchor;
        t += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t g = anchor_pos[t], sid = anchor_sid[t];
     const int64_t s_off = __ldg(offsets + sid), s_end = __ldg(offsets + sid + 1);
     int64_t end = s_end;
     if (t + 1 < n_anchor && anchor_sid[t + 1] == sid) end = anchor_pos[t + 1];
+    const uint8_t* p = bytes + g;
+    const uint32_t len = (uint32_t)(end - (int64_t)g);
+    const uint32_t head = len & 3u;
     uint64_t h = 0;
-    for (int64_t x = g; x < end; ++x) {
-      h = mulmod61(h, key_base) + (uint64_t)__ldg(bytes + x) + 1;
-      if (h >= kM61) h -= kM61;
+    for (uint32_t x = 0; x < head; ++x) h = addmod61(mulmod61(h, key_base), (uint64_t)__ldg(p + x) + 1);
+    for (uint32_t x = head; x < len; x += 4) {
+      const uint32_t c0 = __ldg(p + x), c1 = __ldg(p + x + 1), c2 = __ldg(p + x + 2), c3 = __ldg(p + x + 3);
+      uint64_t u = s_t[2][c0] + s_t[1][c1];     // < 2^62
+      u = (u & kM61) + (u >> 61);
+      u += s_t[0][c2] + (uint64_t)c3 + 1;       // < 2^63
+      u = (u & kM61) + (u >> 61);
+      h = addmod61(mulmod61(h, b4), u >= kM61 ? u - kM61 : u);
     }
     rec_sid[t] = sid;
     rec_pos[t] = (uint32_t)((int64_t)g - s_off);
-    rec_len[t] = (uint32_t)(end - (int64_t)g);
+    rec_len[t] = len;
     rec_slen[t] = (uint32_t)(s_end - s_off);
     rec_h61[t] = h;
   }
@@ -526,7 +553,7 @@ int launch_partition_records(const uint8_t* bytes, const int64_t* offsets, const
                              cudaStream_t s) {
   if (n_anchor == 0) return MJ_OK;
   unsigned grid = (unsigned)std::min<uint64_t>((n_anchor + 255) / 256, (uint64_t)kNumSMsHint * 16);
-  partition_records_kernel<<<grid, 256, 0, s>>>(bytes, offsets, anchor_pos, anchor_sid, n_anchor, key_base,
+  partition_records_kernel<<<grid, kRecThreads, 0, s>>>(bytes, offsets, anchor_pos, anchor_sid, n_anchor, key_base,
                                                 rec_sid, rec_pos, rec_len, rec_slen, rec_h61);
   MJ_KERNEL_DONE();
   return MJ_OK;
