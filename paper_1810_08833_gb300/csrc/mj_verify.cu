@@ -168,6 +168,74 @@ __device__ __forceinline__ bool pair_init(PairState<W, P>& st, const VerifyArgs&
   return true;
 }
 
+// s = a + b over W 32-bit words (word 0 least significant): one carry chain
+// (add.cc / addc) for bands up to 8 words, 64-bit partial sums beyond.
+template <int W>
+struct add_chain {
+  static __device__ __forceinline__ void run(const uint32_t* a, const uint32_t* b, uint32_t* s) {
+    uint32_t carry = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const uint64_t sum = (uint64_t)a[w] + b[w] + carry;
+      carry = (uint32_t)(sum >> 32);
+      s[w] = (uint32_t)sum;
+    }
+  }
+};
+template <>
+struct add_chain<1> {
+  static __device__ __forceinline__ void run(const uint32_t* a, const uint32_t* b, uint32_t* s) { s[0] = a[0] + b[0]; }
+};
+template <> struct add_chain<2> {
+  static __device__ __forceinline__ void run(const uint32_t* a, const uint32_t* b, uint32_t* s) {
+    asm("add.cc.u32 %0, %2, %4;\n\taddc.u32 %1, %3, %5;"
+        : "=r"(s[0]), "=r"(s[1])
+        : "r"(a[0]), "r"(a[1]), "r"(b[0]), "r"(b[1]));
+  }
+};
+template <> struct add_chain<3> {
+  static __device__ __forceinline__ void run(const uint32_t* a, const uint32_t* b, uint32_t* s) {
+    asm("add.cc.u32 %0, %3, %6;\n\taddc.cc.u32 %1, %4, %7;\n\taddc.u32 %2, %5, %8;"
+        : "=r"(s[0]), "=r"(s[1]), "=r"(s[2])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(b[0]), "r"(b[1]), "r"(b[2]));
+  }
+};
+template <> struct add_chain<4> {
+  static __device__ __forceinline__ void run(const uint32_t* a, const uint32_t* b, uint32_t* s) {
+    asm("add.cc.u32 %0, %4, %8;\n\taddc.cc.u32 %1, %5, %9;\n\taddc.cc.u32 %2, %6, %10;\n\taddc.u32 %3, %7, %11;"
+        : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]));
+  }
+};
+template <> struct add_chain<5> {
+  static __device__ __forceinline__ void run(const uint32_t* a, const uint32_t* b, uint32_t* s) {
+    asm("add.cc.u32 %0, %5, %10;\n\taddc.cc.u32 %1, %6, %11;\n\taddc.cc.u32 %2, %7, %12;\n\taddc.cc.u32 %3, %8, %13;\n\taddc.u32 %4, %9, %14;"
+        : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]));
+  }
+};
+template <> struct add_chain<6> {
+  static __device__ __forceinline__ void run(const uint32_t* a, const uint32_t* b, uint32_t* s) {
+    asm("add.cc.u32 %0, %6, %12;\n\taddc.cc.u32 %1, %7, %13;\n\taddc.cc.u32 %2, %8, %14;\n\taddc.cc.u32 %3, %9, %15;\n\taddc.cc.u32 %4, %10, %16;\n\taddc.u32 %5, %11, %17;"
+        : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]));
+  }
+};
+template <> struct add_chain<7> {
+  static __device__ __forceinline__ void run(const uint32_t* a, const uint32_t* b, uint32_t* s) {
+    asm("add.cc.u32 %0, %7, %14;\n\taddc.cc.u32 %1, %8, %15;\n\taddc.cc.u32 %2, %9, %16;\n\taddc.cc.u32 %3, %10, %17;\n\taddc.cc.u32 %4, %11, %18;\n\taddc.cc.u32 %5, %12, %19;\n\taddc.u32 %6, %13, %20;"
+        : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]));
+  }
+};
+template <> struct add_chain<8> {
+  static __device__ __forceinline__ void run(const uint32_t* a, const uint32_t* b, uint32_t* s) {
+    asm("add.cc.u32 %0, %8, %16;\n\taddc.cc.u32 %1, %9, %17;\n\taddc.cc.u32 %2, %10, %18;\n\taddc.cc.u32 %3, %11, %19;\n\taddc.cc.u32 %4, %12, %20;\n\taddc.cc.u32 %5, %13, %21;\n\taddc.cc.u32 %6, %14, %22;\n\taddc.u32 %7, %15, %23;"
+        : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(s[7])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]));
+  }
+};
+
 constexpr int kChunk = 16;   // columns between two early-exit checks
 
 // Advances up to kChunk columns; returns true when the pair is decided.
@@ -236,14 +304,14 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
     st.Mv[W - 1] = st.Mv[W - 1] >> 1;
     const int32_t sv = (int32_t)(st.Pv[0] & 1u) - (int32_t)(st.Mv[0] & 1u);
 
-    uint32_t Xv[W], Ph[W], Mh[W];
-    uint32_t carry = 0;
+    uint32_t Xv[W], Ph[W], Mh[W], EP[W], SUM[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) EP[w] = Eq[w] & st.Pv[w];
+    add_chain<W>::run(EP, st.Pv, SUM);   // (Eq & Pv) + Pv across the band's words
 #pragma unroll
     for (int w = 0; w < W; ++w) {
       Xv[w] = Eq[w] | st.Mv[w];
-      const uint64_t sum = (uint64_t)(Eq[w] & st.Pv[w]) + st.Pv[w] + carry;
-      carry = (uint32_t)(sum >> 32);
-      const uint32_t Xh = ((uint32_t)sum ^ st.Pv[w]) | Eq[w];
+      const uint32_t Xh = (SUM[w] ^ st.Pv[w]) | Eq[w];
       Ph[w] = st.Mv[w] | ~(Xh | st.Pv[w]);
       Mh[w] = st.Pv[w] & Xh;
     }
