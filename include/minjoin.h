@@ -45,6 +45,9 @@ extern "C" {
 /* mj_params.flags */
 #define MJ_FLAG_KEY_CHECK 1u     /* check byte equality of every group of equal partition keys */
 #define MJ_FLAG_FEATURES 16u     /* mj_join keeps every candidate's band features (mj_features_copy) */
+#define MJ_FLAG_FIRST_PASS 32u   /* learned mode: run the first passes however few pairs they hold (by default
+                                    they run only with at least 384 pairs per SM, below which their latency
+                                    exceeds what they save, and every pair goes to band K) */
 
 /* verification modes (mj_params.verify_mode) */
 #define MJ_VERIFY_PLAIN 0        /* one pass with band K */
@@ -106,7 +109,8 @@ typedef struct {
  *  verify_mode  MJ_VERIFY_PLAIN or MJ_VERIFY_LEARNED.
  *  flags   MJ_FLAG_KEY_CHECK: check every group of equal partition keys for
  *          byte equality (mismatches counted in mj_stats.key_collisions);
- *          MJ_FLAG_FEATURES: keep the candidates' band features. */
+ *          MJ_FLAG_FEATURES: keep the candidates' band features;
+ *          MJ_FLAG_FIRST_PASS: run the learned first passes however few pairs they hold. */
 typedef struct {
   uint32_t K;
   uint32_t T;

@@ -52,6 +52,7 @@ class BandTrainParams(ctypes.Structure):
 
 MJ_FLAG_KEY_CHECK = 1
 MJ_FLAG_FEATURES = 16
+MJ_FLAG_FIRST_PASS = 32
 BAND_FEATURES = 8
 BAND_PARAMS = 4801
 

@@ -93,6 +93,7 @@ using namespace mj;
 
 struct mj_ctx {
   int device = 0;
+  int sms = 152;   // streaming multiprocessors of the device
   mj_stats stats{};
   Derived d;
   // pinned host staging for small readbacks
@@ -653,10 +654,17 @@ int verify_stage(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, ui
     unsigned long long* first_total = c->small.as<unsigned long long>() + 5;
     MJ_TRY(verify_prep(c, s));
     const uint32_t* forder = c->lvals.as<uint32_t>();
+    // the first passes run only when they hold enough pairs to keep the
+    // verifier's lanes busy (3 blocks of 128 per SM); fewer pairs are
+    // latency-bound there (each on one lane) and cost more than they save,
+    // so they go straight to band K
+    bool first = false;
     if (nb > 0) {
       MJ_TRY(launch_band_buckets(c->kband.as<uint32_t>(), m, K, nb, c->fcnt.as<uint32_t>(), ranges,
                                  c->lvals.as<uint32_t>(), first_total, s));
       MJ_CUDA_TRY(cudaMemsetAsync(c->fnext.p, 0, 8 * (kMaxBandBuckets + 2), s));
+      MJ_TRY(readback(c, first_total, 8, s));
+      first = (p->flags & MJ_FLAG_FIRST_PASS) || c->h_small[0] >= (uint64_t)c->sms * 384;
     } else {
       MJ_CUDA_TRY(cudaMemsetAsync(first_total, 0, 8, s));
     }
@@ -665,10 +673,12 @@ int verify_stage(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, ui
     // each reading its range from device memory and writing its own results;
     // then band K on s for every pair they did not settle (a settled pair
     // takes its first-pass result)
-    MJ_TRY(c->ed_first.reserve(m * 4, s));
-    MJ_CUDA_TRY(cudaMemsetAsync(c->ed_first.p, 0xff, m * 4, s));
+    if (first) {
+      MJ_TRY(c->ed_first.reserve(m * 4, s));
+      MJ_CUDA_TRY(cudaMemsetAsync(c->ed_first.p, 0xff, m * 4, s));
+    }
     tstart(c, 6, s);
-    if (nb > 0) {
+    if (first) {
       MJ_CUDA_TRY(cudaEventRecord(c->ev_fork, s));
       for (uint32_t b = 1; b <= nb; ++b) {
         const uint32_t whi = wK <= 8 ? b + 1 : std::min(wK, 1u << b);
@@ -678,17 +688,18 @@ int verify_stage(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, ui
                       c->ed_first.as<uint32_t>(), false, sb, forder, nullptr, ranges + 2 * b, ranges + 2 * b + 1,
                       -1, -1, c->fnext.as<unsigned long long>() + b, false));
       }
-      for (uint32_t b = 1; b <= std::min(nb, (uint32_t)mj_ctx::kAuxStreams); ++b) {
+      for (uint32_t b = 1; first && b <= std::min(nb, (uint32_t)mj_ctx::kAuxStreams); ++b) {
         MJ_CUDA_TRY(cudaEventRecord(c->ev_join[b - 1], c->aux[b - 1]));
         MJ_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[b - 1], 0));
       }
     }
-    MJ_TRY(verify(c, d_bytes, d_offsets, ci, cj, nullptr, m, K, K, ed, false, s, order, c->kband.as<uint32_t>(),
-                  nullptr, nullptr, -1, -1, nullptr, false, c->ed_first.as<uint32_t>()));
+    MJ_TRY(verify(c, d_bytes, d_offsets, ci, cj, nullptr, m, K, K, ed, false, s, order,
+                  first ? c->kband.as<uint32_t>() : nullptr, nullptr, nullptr, -1, -1, nullptr, false,
+                  first ? c->ed_first.as<uint32_t>() : nullptr));
     MJ_TRY(readback(c, c->small.as<unsigned long long>() + 4, 16, s));
     const uint64_t settled = c->h_small[0];
     c->stats.first_pass_settled = settled;
-    c->stats.fallback_pairs = c->h_small[1] - settled;
+    c->stats.fallback_pairs = first ? c->h_small[1] - settled : 0;
   }
   c->have_features = want_x;
   return launch_band_cells(ci, cj, d_offsets, m, K, c->small.as<unsigned long long>() + 3, s);
@@ -758,6 +769,10 @@ int mj_create(mj_ctx** ctx, int device) {
   DeviceGuard g(device);
   mj_ctx* c = new mj_ctx();
   c->device = device;
+  if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || c->sms < 1) {
+    cudaGetLastError();
+    c->sms = 152;
+  }
   if (cudaMallocHost(&c->h_small, 4096) != cudaSuccess) {
     cudaGetLastError();
     delete c;

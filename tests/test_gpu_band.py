@@ -147,7 +147,8 @@ def test_learned_join_equals_plain_and_gains(ctx, cfg, roots):
     data, off = to_device(s)
     pi, pj, pe = ctx.join(data, off, mj.params(s.K, T=s.T))
     plain = ctx.stats()
-    li, lj, le = ctx.join(data, off, mj.params(s.K, T=s.T, verify_mode=mj.MJ_VERIFY_LEARNED))
+    li, lj, le = ctx.join(data, off, mj.params(s.K, T=s.T, verify_mode=mj.MJ_VERIFY_LEARNED,
+                                                flags=mj.MJ_FLAG_FIRST_PASS))
     learned = ctx.stats()
     for a, b in ((pi, li), (pj, lj), (pe, le)):
         assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
