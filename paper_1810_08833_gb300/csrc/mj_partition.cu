@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(HT) == 4 ? 4 : 1) anchor_flag
   __shared__ int64_t s_off[kAMaxStrings + 1];   // offsets[sid0 .. sid0 + cap]
   __shared__ uint32_t s_ns;
   __shared__ uint32_t s_warp[kThreads / 32];
+  __shared__ uint32_t s_levels;
   const int Hs = anchor_halo(a.r_max);
   const int span = kATile + 2 * Hs;             // positions holding a Pi value
   const int nsym = span + 80;                   // staged symbols (q-gram tails)
@@ -161,6 +162,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(HT) == 4 ? 4 : 1) anchor_flag
 
   // ---- phase 0: rank table and the CTA's string offsets
   s_rank[threadIdx.x] = a.rank[threadIdx.x];
+  if (threadIdx.x == 0) s_levels = 0;
   const uint32_t sid0 = __ldg(tile_first + 2 * (uint64_t)blockIdx.x);
   const uint32_t cap = min((uint32_t)kAMaxStrings, a.n - sid0);
   for (uint32_t t = threadIdx.x; t <= cap; t += kThreads) s_off[t] = __ldg(a.offsets + sid0 + t);
@@ -258,8 +260,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(HT) == 4 ? 4 : 1) anchor_flag
   const uint32_t wbase = g0 + (uint32_t)(kAWarpSpan * wid);
   const uint32_t ns = s_ns;
   const bool cached = ns < cap || sid0 + cap == a.n;   // every string of the CTA is in s_off
-  HT v[kAPer];          // Pi of the position
-  uint32_t info[kAPer]; // r (bits 0..23) and level t (bits 24..31; 31 = not tested)
+  uint32_t rq2[kAPer / 2];   // radius of position j in bits 16(j&1) .. of word j/2 (0: not queried)
   uint32_t flags = 0;   // anchor bit per position
   uint32_t level_mask = 0;
   {
@@ -274,8 +275,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(HT) == 4 ? 4 : 1) anchor_flag
       const int64_t hi = (int64_t)slen - a.q - r;   // m - 1 - r, m = |s| - q + 1
       i_hi = hi < 0 ? -1 : (hi > 0x7fffffff ? 0x7fffffff : (int32_t)hi);
       if (r > Hs && i_hi >= r) atomicOr(dev_flags, FLAG_BOUNDS);   // cannot happen: r_max bounds every r
-      lvl = (r == 0 || r > Hs || i_hi < r) ? 31u << 24
-                                            : ((uint32_t)(31 - __clz(r)) << 24) | (uint32_t)r;
+      lvl = (r == 0 || r > Hs || i_hi < r) ? 0u : (uint32_t)r;   // radius of a range query, 0: none
     };
     const uint32_t gfirst = wbase + lane;
     if (gfirst < nbytes) {
@@ -294,11 +294,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(HT) == 4 ? 4 : 1) anchor_flag
       set_string();
     }
 #pragma unroll
+    for (int j = 0; j < kAPer / 2; ++j) rq2[j] = 0;
+#pragma unroll
     for (int j = 0; j < kAPer; ++j) {
       const uint32_t g = wbase + 32 * j + lane;
-      const int x = Hs + kAWarpSpan * wid + 32 * j + lane;
-      v[j] = lev0[x];
-      info[j] = 31u << 24;
       if (g < nbytes) {
         while (g >= s_e) {   // next non-empty string holding g
           ++sid;
@@ -309,19 +308,20 @@ __global__ void __launch_bounds__(kThreads, sizeof(HT) == 4 ? 4 : 1) anchor_flag
         const int32_t i = (int32_t)(g - s_o);
         const bool tested = i >= r && i <= i_hi;
         if (i == 0 || (tested && r == 0)) flags |= 1u << j;
-        if (tested) info[j] = lvl;
+        if (tested && lvl) {
+          rq2[j / 2] |= lvl << (16 * (j & 1));
+          level_mask |= 1u << (31 - __clz(lvl));
+        }
       }
-      level_mask |= 1u << (info[j] >> 24);   // bit 31 for untested positions
     }
   }
-  level_mask &= 0x7fffffffu;
-  // levels this CTA needs: 0 .. the highest floor(log2 r) of its positions
-  __shared__ uint32_t s_levels;
-  if (threadIdx.x == 0) s_levels = 0;
-  __syncthreads();
+  // levels this CTA needs: 0 .. the highest floor(log2 r) of its tested positions
   if (level_mask) atomicOr(&s_levels, level_mask);
   __syncthreads();
   const int t_top = s_levels ? 31 - __clz(s_levels) : 0;
+  HT v[kAPer];          // Pi of the position
+#pragma unroll
+  for (int j = 0; j < kAPer; ++j) v[j] = lev0[Hs + kAWarpSpan * wid + 32 * j + lane];
   HT* cur = lev0;
   HT* oth = lev1;
 #pragma unroll 1
@@ -356,8 +356,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(HT) == 4 ? 4 : 1) anchor_flag
       const int w = 1 << t;
 #pragma unroll
       for (int j = 0; j < kAPer; ++j) {
-        if ((int)(info[j] >> 24) == t) {
-          const int r = (int)(info[j] & 0xffffffu);
+        const int r = (int)((rq2[j / 2] >> (16 * (j & 1))) & 0xffffu);
+        if (r != 0 && 31 - __clz(r) == t) {
           const int x = Hs + kAWarpSpan * wid + 32 * j + lane;
           const HT lmin = min(cur[x - r], cur[x - w]);
           const HT rmin = min(cur[x + 1], cur[x + r - w + 1]);
