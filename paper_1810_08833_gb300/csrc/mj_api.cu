@@ -350,6 +350,11 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   c->stats.key_collisions = 0;
   if (nr == 0) return MJ_OK;
   const int slen_bits = bits_for(d.N);
+  // Group runs only need to separate most (len, key) classes: the pair walk
+  // compares len and key itself.  So the hash takes the bits that fill whole
+  // 8-bit radix passes above the length, at least 24 and at most 32.
+  const int sort_passes = (24 + slen_bits + 7) / 8;
+  const int hash_bits = std::min(32, 8 * sort_passes - slen_bits);
   MJ_TRY(c->keys.reserve((size_t)nr * 8, s));
   MJ_TRY(c->keys_alt.reserve((size_t)nr * 8, s));
   MJ_TRY(c->idx.reserve((size_t)nr * 4, s));
@@ -357,10 +362,10 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(nr), s));
   tstart(c, 2, s);
   MJ_TRY(launch_make_group_keys(c->rec_len.as<uint32_t>(), c->rec_slen.as<uint32_t>(), c->rec_h61.as<uint64_t>(), nr,
-                                slen_bits, c->keys.as<uint64_t>(), c->idx.as<uint32_t>(), s));
+                                slen_bits, hash_bits, c->keys.as<uint64_t>(), c->idx.as<uint32_t>(), s));
   bool alt = false;
   MJ_TRY(radix_sort_u64(c->keys.as<uint64_t>(), c->keys_alt.as<uint64_t>(), c->idx.as<uint32_t>(),
-                        c->idx_alt.as<uint32_t>(), nr, 0, 32 + slen_bits, c->sort_tmp.p, &alt, s));
+                        c->idx_alt.as<uint32_t>(), nr, 0, hash_bits + slen_bits, c->sort_tmp.p, &alt, s));
   const uint64_t* skeys = alt ? c->keys_alt.as<uint64_t>() : c->keys.as<uint64_t>();
   const uint32_t* sidx = alt ? c->idx_alt.as<uint32_t>() : c->idx.as<uint32_t>();
   MJ_TRY(c->srec.reserve((size_t)nr * sizeof(PRec), s));

@@ -63,11 +63,11 @@ __device__ __forceinline__ uint64_t mix64(uint64_t k) {  // MurmurHash3 fmix64
 
 // Group key: 32 hash bits of (len, key) above slen_bits bits of string length.
 __global__ void group_keys_kernel(const uint32_t* __restrict__ rec_len, const uint32_t* __restrict__ rec_slen,
-                                  const uint64_t* __restrict__ rec_h61, uint32_t n, int slen_bits,
+                                  const uint64_t* __restrict__ rec_h61, uint32_t n, int slen_bits, int hash_bits,
                                   uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t g = mix64(rec_h61[t] ^ ((uint64_t)rec_len[t] * 0x9e3779b97f4a7c15ull));
-    keys[t] = ((g >> 32) << slen_bits) | (uint64_t)rec_slen[t];
+    keys[t] = ((g >> (64 - hash_bits)) << slen_bits) | (uint64_t)rec_slen[t];
     idx[t] = (uint32_t)t;
   }
 }
@@ -363,9 +363,10 @@ int launch_max_length(const int64_t* offsets, uint32_t n, unsigned long long* ou
 }
 
 int launch_make_group_keys(const uint32_t* rec_len, const uint32_t* rec_slen, const uint64_t* rec_h61, uint32_t n,
-                           int slen_bits, uint64_t* keys, uint32_t* idx, cudaStream_t s) {
+                           int slen_bits, int hash_bits, uint64_t* keys, uint32_t* idx, cudaStream_t s) {
   if (!n) return MJ_OK;
-  group_keys_kernel<<<grid_for(n), 256, 0, s>>>(rec_len, rec_slen, rec_h61, n, slen_bits, keys, idx);
+  if (hash_bits < 1 || hash_bits > 32 || slen_bits < 1 || slen_bits + hash_bits > 64) return MJ_ERR_ARG;
+  group_keys_kernel<<<grid_for(n), 256, 0, s>>>(rec_len, rec_slen, rec_h61, n, slen_bits, hash_bits, keys, idx);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }

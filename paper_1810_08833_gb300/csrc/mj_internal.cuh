@@ -88,6 +88,9 @@ struct PartitionArgs {
   uint64_t seed64;
   const uint64_t* table;  // nullable explicit Pi
   uint8_t rank[256];
+  // set by the launcher: 2^19 and 2^16, so that x >> 13 and x >> 16 are the
+  // high words of x * mul (the mixer's shifts on the multiply pipe)
+  uint32_t mul_shr13, mul_shr16;
 };
 constexpr int kPartTile = 2048;  // byte positions per CTA tile
 uint64_t partition_num_tiles(uint64_t nbytes);
@@ -122,12 +125,13 @@ int radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t*
                    uint64_t n, int bit_lo, int bit_hi, void* temp, bool* result_in_alt,
                    cudaStream_t s);
 
-// a5-a6: grouping keys and pair emission.
+// a5-a6: grouping keys and pair emission.  A key is hash_bits (<= 32) bits
+// of a hash of (len, Karp-Rabin key) above slen_bits bits of string length.
 int launch_make_group_keys(const uint32_t* rec_len, const uint32_t* rec_slen, const uint64_t* rec_h61,
-                           uint32_t n_rec, int slen_bits, uint64_t* keys, uint32_t* idx,
+                           uint32_t n_rec, int slen_bits, int hash_bits, uint64_t* keys, uint32_t* idx,
                            cudaStream_t s);
 // A partition record in group order, packed for the walks of the pair
-// emission (two 16-byte loads): Karp-Rabin key, group run (the 32 hash bits
+// emission (two 16-byte loads): Karp-Rabin key, group run (the hash bits
 // of the sort key), string length, partition length, string id, position.
 struct alignas(16) PRec {
   uint64_t h61;

@@ -3,10 +3,10 @@
 // paper, computed for all strings at once over the concatenated bytes.
 //
 // Work decomposition: the concatenation is cut into tiles of kPartTile byte
-// positions, one CTA per tile.  A tile stages its bytes (as rank codes) plus a
-// halo of r_max positions on the left and r_max + q - 1 on the right in shared
-// memory, computes Pi of every q-gram start in tile+halo there, then tests the
-// tile's own positions.  A position's string is found by binary search over
+// positions, two per CTA of the anchor kernel.  A CTA stages its bytes (as
+// rank codes) plus a halo of r_max positions (rounded up to 32) on each side
+// and the q - 1 symbols after it in shared memory, computes Pi of every
+// q-gram start of tiles and halos there, then tests the tiles' own positions.  A position's string is found by binary search over
 // the offsets; the strict-minimum test of a position never looks outside its
 // own string (positions i in [r, m-1-r] of a string have all their 2r
 // neighbours inside the string's q-gram range), so halos that run into a
@@ -17,18 +17,6 @@
 
 namespace mj {
 namespace {
-
-// MurmurHash3 32-bit finaliser (A. Appleby, public domain): the random
-// function Pi on q-grams whose packed code fits 32 bits.  A bijection, so
-// equal values mean equal q-grams.
-__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
-  h ^= h >> 16;
-  h *= 0x85ebca6bu;
-  h ^= h >> 13;
-  h *= 0xc2b2ae35u;
-  h ^= h >> 16;
-  return h;
-}
 
 // MurmurHash3 64-bit finaliser, for packed codes wider than 32 bits.
 __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
@@ -54,31 +42,25 @@ constexpr int kThreads = 256;
 constexpr int kPerThread = kPartTile / kThreads;  // positions per thread in the emit kernel
 
 // The anchor kernel: one CTA per kATile positions (two kPartTile tiles).
+// Each of the first 256 threads owns a run of 16 consecutive positions of the
+// tile; a ninth warp takes the runs of the halos.
 constexpr int kATile = 2 * kPartTile;
-constexpr int kAPer = kATile / kThreads;           // 16 positions per thread
-constexpr int kAWarpSpan = kATile / (kThreads / 32);   // 512 positions per warp
-constexpr int kAMaxStrings = 256;                  // string offsets cached per CTA
+constexpr int kARun = 16;                          // positions per thread run
+constexpr int kATileRuns = kATile / kARun;         // 256 runs per tile
+constexpr int kAThreads = kATileRuns + 32;         // tile runs + one warp of halo runs
+constexpr int kAMaxStrings = 256;                  // strings cached per CTA
+constexpr int kABlockRadius = 15;                  // radius from which block tests use run minima
 
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+// Halo of the anchor kernel: r_max positions rounded up to 32, so that the
+// span starts on a 32-position word of the bitmap and bit-planes.
+__host__ __device__ inline int anchor_halo(int r_max) { return ((r_max < 1 ? 1 : r_max) + 31) & ~31; }
 
-// Halo of the anchor kernel: r_max positions rounded up to 16.
-__host__ __device__ inline int anchor_halo(int r_max) { return (int)align16((size_t)(r_max < 1 ? 1 : r_max)); }
-
-// Shared memory of the anchor kernel: rank table, staged rank codes of the
-// tile, its halo and q-gram tail, then two range-minimum levels (ping-pong).
+// Shared memory of the anchor kernel: Pi of every position of the span, and
+// for radii of 15 and more also the prefix and suffix minima of every run.
 template <class HT>
 __host__ __device__ inline size_t anchor_smem_bytes(int r_max) {
   const size_t span = kATile + 2 * (size_t)anchor_halo(r_max);
-  return 256 + align16(span + 80) + 2 * align16((span + 8) * sizeof(HT));
-}
-
-// Pi of the q-gram whose packed code is `code` (see mjo_hash_qgrams for the
-// definition shared with the paper's Table 2 form).
-template <class HT, bool WIDE, bool TABLE>
-__device__ __forceinline__ HT pi_value(uint64_t code, const PartitionArgs& a) {
-  if (TABLE) return (HT)__ldg(a.table + code);
-  if (WIDE) return (HT)fmix64(code ^ a.seed64);
-  return (HT)fmix32((uint32_t)code ^ a.seed32);
+  return span * sizeof(HT) * (r_max >= kABlockRadius ? 3 : 1);
 }
 
 // tile_first[t] = the string holding byte t * kPartTile: every non-empty
@@ -101,286 +83,424 @@ __device__ __forceinline__ int32_t radius32(uint32_t slen, uint32_t q, uint32_t 
   return r < (uint32_t)r_min ? r_min : (int32_t)r;
 }
 
-// Four consecutive table entries (16-byte aligned for 32-bit entries).
-__device__ __forceinline__ void load4(const uint32_t* p, uint32_t (&v)[4]) {
-  const uint4 u = *reinterpret_cast<const uint4*>(p);
-  v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
+// Bit j set iff h[j] equals the minimum of its aligned block of B positions.
+template <int B, class HT>
+__device__ __forceinline__ uint32_t block_min_mask(const HT (&h)[kARun]) {
+  uint32_t e = 0;
+#pragma unroll
+  for (int b = 0; b < kARun; b += B) {
+    HT m = h[b];
+#pragma unroll
+    for (int j = 1; j < B; ++j) m = h[b + j] < m ? h[b + j] : m;
+#pragma unroll
+    for (int j = 0; j < B; ++j) e |= (h[b + j] == m ? 1u : 0u) << (b + j);
+  }
+  return e;
 }
-__device__ __forceinline__ void load4(const uint64_t* p, uint64_t (&v)[4]) {
-  const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(p);
-  const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(p + 2);
-  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+
+// Minimum of the n entries p[0 .. n-1] and of m.
+template <class HT>
+__device__ __forceinline__ HT range_min(const HT* p, int n, HT m) {
+  for (; n >= 4; n -= 4, p += 4) {
+    const HT a = p[0] < p[1] ? p[0] : p[1], b = p[2] < p[3] ? p[2] : p[3];
+    const HT c = a < b ? a : b;
+    m = c < m ? c : m;
+  }
+  for (; n > 0; --n, ++p) m = *p < m ? *p : m;
+  return m;
 }
-__device__ __forceinline__ void store4(uint32_t* p, const uint32_t (&v)[4]) {
-  *reinterpret_cast<uint4*>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+
+// The MurmurHash3 32-bit finaliser (A. Appleby, public domain) of code ^ seed:
+// the random function Pi on q-grams whose packed code fits 32 bits.  A
+// bijection, so equal values mean equal q-grams.  seed' = seed ^ (seed >> 16)
+// folds the seed into the first step: (c ^ s) ^ ((c ^ s) >> 16) = c ^ (c >> 16)
+// ^ s'.  The other two shifts are taken as high words of products (m13 =
+// 2^19, m16 = 2^16), which run on the multiply pipe beside the logic ops.
+__device__ __forceinline__ uint32_t pi32(uint32_t code, uint32_t seed_folded, uint32_t m13, uint32_t m16) {
+  uint32_t h = code ^ (code >> 16) ^ seed_folded;
+  h *= 0x85ebca6bu;
+  h ^= __umulhi(h, m13);
+  h *= 0xc2b2ae35u;
+  h ^= __umulhi(h, m16);
+  return h;
 }
-__device__ __forceinline__ void store4(uint64_t* p, const uint64_t (&v)[4]) {
-  *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(v[0], v[1]);
-  *reinterpret_cast<ulonglong2*>(p + 2) = make_ulonglong2(v[2], v[3]);
+
+// Pi of the q-gram whose packed code is `code` (see mjo_hash_qgrams for the
+// definition shared with the paper's Table 2 form).
+template <class HT, bool WIDE, bool TABLE>
+__device__ __forceinline__ HT pi_value(uint64_t code, const PartitionArgs& a, uint32_t seed_folded) {
+  if (TABLE) return (HT)__ldg(a.table + code);
+  if (WIDE) return (HT)fmix64(code ^ a.seed64);
+  return (HT)pi32((uint32_t)code, seed_folded, a.mul_shr13, a.mul_shr16);
 }
+
+// hi32(a * b) + c in one multiply-add.
+__device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+// One backward step of the packed q-gram code: the symbol enters at the top
+// field (bits top .. top + bits - 1) and the lowest field drops out, so the
+// code holds the q symbols starting at the last one entered.  The fields are
+// disjoint, so for 32-bit codes (code >> bits) | (sym << top) is the multiply
+// -add hi32(code * 2^(32 - bits)) + sym * 2^top.
+struct Roll {
+  uint32_t bsh, top, rmul, tmul;
+  __device__ __forceinline__ uint32_t operator()(uint32_t code, uint32_t sym) const {
+    return mad_hi(code, rmul, sym * tmul);
+  }
+  __device__ __forceinline__ uint64_t operator()(uint64_t code, uint32_t sym) const {
+    return (code >> bsh) | ((uint64_t)sym << top);
+  }
+};
+
+// Rank code of byte g, 0 outside [0, nbytes).
+__device__ __forceinline__ uint32_t rank_at(const PartitionArgs& a, const uint8_t* s_rank, int64_t g) {
+  return (g >= 0 && g < (int64_t)a.nbytes) ? (uint32_t)s_rank[__ldg(a.bytes + g)] : 0u;
+}
+
+// The 16 bytes at global position g (a 16-byte aligned load; PARTIAL: chunks
+// at the ends of the input, read byte by byte with 0 codes outside it).
+template <bool PARTIAL>
+__device__ __forceinline__ void load_chunk(const PartitionArgs& a, int64_t g, uint32_t (&w)[4]) {
+  if (PARTIAL) {
+    w[0] = w[1] = w[2] = w[3] = 0;
+  } else {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.bytes + g));
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+  }
+}
+
+// Rank code of symbol j (0..15) of the chunk at g.
+template <bool PARTIAL>
+__device__ __forceinline__ uint32_t chunk_sym(const uint32_t (&w)[4], int j, const PartitionArgs& a,
+                                              const uint8_t* s_rank, int64_t g) {
+  if (PARTIAL) return rank_at(a, s_rank, g + j);
+  return (uint32_t)s_rank[(w[j >> 2] >> (8 * (j & 3))) & 255u];
+}
+
+// The code rolled backwards over the first N symbols of the chunk at g.
+template <bool PARTIAL, int N, class CT>
+__device__ __forceinline__ CT prime_chunk(CT code, const PartitionArgs& a, const uint8_t* s_rank, int64_t g,
+                                          const Roll& roll) {
+  uint32_t w[4];
+  load_chunk<PARTIAL>(a, g, w);
+#pragma unroll
+  for (int j = N - 1; j >= 0; --j) code = roll(code, chunk_sym<PARTIAL>(w, j, a, s_rank, g));
+  return code;
+}
+
+template <int N, class CT>
+__device__ __forceinline__ CT prime(CT code, const PartitionArgs& a, const uint8_t* s_rank, int64_t g, bool vec,
+                                    const Roll& roll) {
+  return (vec && g >= 0 && g + 16 <= (int64_t)a.nbytes) ? prime_chunk<false, N, CT>(code, a, s_rank, g, roll)
+                                                        : prime_chunk<true, N, CT>(code, a, s_rank, g, roll);
+}
+
+// Pi of the 16 q-grams starting at g (h[j] for start g + j), continuing the
+// backward roll from `code` (which holds the q - 1 symbols after the run in
+// its upper fields); with PACK, symw gets the run's rank codes, one per byte.
+template <bool PARTIAL, bool PACK, class CT, class HT, bool WIDE, bool TABLE>
+__device__ __forceinline__ void hash_run(CT code, const PartitionArgs& a, const uint8_t* s_rank, int64_t g,
+                                         const Roll& roll, uint32_t seed_folded, HT (&h)[kARun],
+                                         uint32_t (&symw)[4]) {
+  uint32_t w[4];
+  load_chunk<PARTIAL>(a, g, w);
+#pragma unroll
+  for (int j = kARun - 1; j >= 0; --j) {
+    const uint32_t sym = chunk_sym<PARTIAL>(w, j, a, s_rank, g);
+    if (PACK) symw[j >> 2] = __byte_perm(symw[j >> 2], sym, (0x3210u & ~(0xfu << (4 * (j & 3)))) | (4u << (4 * (j & 3))));
+    code = roll(code, sym);
+    h[j] = pi_value<HT, WIDE, TABLE>((uint64_t)code, a, seed_folded);
+  }
+}
+
+template <bool PACK, class CT, class HT, bool WIDE, bool TABLE>
+__device__ __forceinline__ void hash_run_at(CT code, const PartitionArgs& a, const uint8_t* s_rank, int64_t g,
+                                            bool vec, const Roll& roll, uint32_t seed_folded, HT (&h)[kARun],
+                                            uint32_t (&symw)[4]) {
+  if (vec && g >= 0 && g + 16 <= (int64_t)a.nbytes)
+    hash_run<false, PACK, CT, HT, WIDE, TABLE>(code, a, s_rank, g, roll, seed_folded, h, symw);
+  else
+    hash_run<true, PACK, CT, HT, WIDE, TABLE>(code, a, s_rank, g, roll, seed_folded, h, symw);
+}
+
+// Index of entry o of the prefix- and suffix-minimum arrays: the four 16-byte
+// quarters of a run are rotated by (run / 2) mod 4, which puts the quarter
+// stores of the 8 lanes of a store phase in 8 different bank groups.
+__device__ __forceinline__ int swz(int o) { return o ^ (((o >> 5) & 3) << 2); }
 
 // Alg. 2 for kATile positions: position i of string s (0-based, m = |s| - q
 // + 1 q-gram starts, radius r) is an anchor iff i = 0, or r <= i <= m - 1 - r
-// and h[i] is strictly below both min(h[i-r .. i-1]) and min(h[i+1 .. i+r]).
-// A window of length r is the union of two windows of length 2^t, t =
-// floor(log2 r), so level t of a range-minimum table answers it with two
-// reads.  The levels are built one at a time into two ping-pong buffers; a
-// position is tested right after its string's level is built.
-//   phase 1  rank codes of the tile and halos, staged with 16-byte loads;
-//   phase 2  Pi of every q-gram start (16 consecutive starts per thread,
-//            packed code rolled forward), and the verifier's bit-planes;
-//   phase 3  level 0 (Pi itself), then levels 1 .. t_max, 4 entries per
-//            thread and step; after level t the positions of strings with
-//            floor(log2 r) = t are tested (lane-interleaved: warp w holds
-//            positions 512 w + 32 j + lane);
-//   phase 4  one ballot per 32 positions gives the bitmap word.
+// and h[i] < h[j] for every other j in [i - r, i + r].
+// The test runs on candidates only.  Take B = 2^floor(log2(r + 1)), at most
+// 16: the aligned block of B positions holding i lies inside i's window, so
+// an anchor is a minimum of its block.  For r < 15 a candidate is compared
+// with the 2r other positions of its window.  For r >= 15 the block is the
+// whole run and the candidate must be its unique minimum; the window outside
+// the run is then covered by a suffix minimum, the minima of whole runs and a
+// prefix minimum.
+//   phase 0  rank table, the CTA's string offsets and radii, and which of
+//            the two tests its strings need;
+//   phase 1  per run: Pi of the 16 q-grams starting in it, from the packed
+//            code rolled backwards, primed with the q - 1 symbols after the
+//            run; the run's Pi values (or its prefix and suffix minima) go to
+//            shared memory; the runs of the tiles also give the verifier's
+//            bit-planes;
+//   phase 2  per tile run: its strings, tested positions, block minima and
+//            candidate tests; one 16-bit bitmap store per run, and counts.
 template <class HT, bool WIDE, bool TABLE>
-__global__ void __launch_bounds__(kThreads, sizeof(HT) == 4 ? 4 : 1) anchor_flags_kernel(PartitionArgs a, uint32_t* __restrict__ bitmap,
-                                                                uint32_t* __restrict__ tile_count,
-                                                                uint32_t* __restrict__ dev_flags,
-                                                                uint32_t* __restrict__ planes, uint64_t plane_words,
-                                                                uint32_t guard_words,
-                                                                const uint32_t* __restrict__ tile_first,
-                                                                uint64_t tiles) {
+__global__ void __launch_bounds__(kAThreads, sizeof(HT) == 4 ? 4 : 2) anchor_flags_kernel(
+    PartitionArgs a, uint32_t* __restrict__ bitmap, uint32_t* __restrict__ tile_count,
+    uint32_t* __restrict__ dev_flags, uint32_t* __restrict__ planes, uint64_t plane_words, uint32_t guard_words,
+    const uint32_t* __restrict__ tile_first, uint64_t tiles) {
   extern __shared__ __align__(16) uint8_t smem[];
-  __shared__ int64_t s_off[kAMaxStrings + 1];   // offsets[sid0 .. sid0 + cap]
+  __shared__ uint8_t s_rank[256];
+  __shared__ uint32_t s_off[kAMaxStrings + 1];  // offsets[sid0 .. sid0 + cap]
+  __shared__ int32_t s_rad[kAMaxStrings];       // radius of strings sid0 .. sid0 + cap - 1
   __shared__ uint32_t s_ns;
-  __shared__ uint32_t s_warp[kThreads / 32];
-  __shared__ uint32_t s_levels;
+  __shared__ uint32_t s_warp[kATileRuns / 32];
   const int Hs = anchor_halo(a.r_max);
   const int span = kATile + 2 * Hs;             // positions holding a Pi value
-  const int nsym = span + 80;                   // staged symbols (q-gram tails)
-  uint8_t* s_rank = smem;
-  uint8_t* s_code = smem + 256;
-  HT* lev0 = reinterpret_cast<HT*>(smem + 256 + align16(nsym));
-  HT* lev1 = reinterpret_cast<HT*>(reinterpret_cast<uint8_t*>(lev0) + align16((span + 8) * sizeof(HT)));
+  HT* s_h = reinterpret_cast<HT*>(smem);
+  HT* s_P = s_h + span;                          // present if r_max >= kABlockRadius
+  HT* s_S = s_P + span;
 
   const uint32_t g0 = blockIdx.x * (uint32_t)kATile;
-  const int64_t base = (int64_t)g0 - Hs;        // global position of s_code[0] and lev[0]
+  const uint32_t gend = g0 + (uint32_t)kATile;
+  const int64_t base = (int64_t)g0 - Hs;        // global position of entry 0
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t nbytes = (uint32_t)a.nbytes;
 
-  // ---- phase 0: rank table and the CTA's string offsets
-  s_rank[threadIdx.x] = a.rank[threadIdx.x];
-  if (threadIdx.x == 0) s_levels = 0;
+  // ---- phase 0
+  if (threadIdx.x < 256) s_rank[threadIdx.x] = a.rank[threadIdx.x];
   const uint32_t sid0 = __ldg(tile_first + 2 * (uint64_t)blockIdx.x);
   const uint32_t cap = min((uint32_t)kAMaxStrings, a.n - sid0);
-  for (uint32_t t = threadIdx.x; t <= cap; t += kThreads) s_off[t] = __ldg(a.offsets + sid0 + t);
-  __syncthreads();
-
-  // ---- phase 1: rank codes of [base, base + nsym), 16 per thread and step
-  {
-    const bool vec = ((uintptr_t)a.bytes & 15) == 0;
-    for (int c = 16 * threadIdx.x; c < nsym; c += 16 * kThreads) {
-      const int64_t gb = base + c;
-      uint32_t out[4];
-      if (vec && gb >= 0 && gb + 16 <= (int64_t)nbytes) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.bytes + gb));
-        const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          out[k] = (uint32_t)s_rank[w4[k] & 255u] | ((uint32_t)s_rank[(w4[k] >> 8) & 255u] << 8) |
-                   ((uint32_t)s_rank[(w4[k] >> 16) & 255u] << 16) | ((uint32_t)s_rank[w4[k] >> 24] << 24);
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          uint32_t x = 0;
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int64_t g = gb + 4 * k + b;
-            if (g >= 0 && g < (int64_t)nbytes) x |= (uint32_t)s_rank[__ldg(a.bytes + g)] << (8 * b);
-          }
-          out[k] = x;
-        }
+  bool need_scan = false, need_minima = false;   // tests of this thread's strings
+  for (uint32_t t = threadIdx.x; t <= cap; t += kAThreads) {
+    const uint32_t so = (uint32_t)__ldg(a.offsets + sid0 + t);
+    s_off[t] = so;
+    if (t < cap) {
+      const uint32_t se = (uint32_t)__ldg(a.offsets + sid0 + t + 1);
+      const int32_t r = radius32(se - so, a.q, a.T, a.r_min);
+      s_rad[t] = r;
+      if (so < gend && se > g0 && se > so && r > 0) {
+        need_scan |= r < kABlockRadius;
+        need_minima |= r >= kABlockRadius;
       }
-      *reinterpret_cast<uint4*>(s_code + c) = make_uint4(out[0], out[1], out[2], out[3]);
+    } else if (sid0 + cap < a.n && so < gend) {
+      need_scan = need_minima = true;   // strings beyond the cache: both
     }
   }
+  need_minima = __syncthreads_or(need_minima) && a.r_max >= kABlockRadius;
+  need_scan = __syncthreads_or(need_scan);
   if (threadIdx.x == 0) {
     // strings that may hold CTA positions: indices 0 .. ns-1 of s_off
     uint32_t lo = 0, hi = cap;
-    const int64_t gend = (int64_t)g0 + kATile;
     while (hi - lo > 1) {
       const uint32_t mid = (lo + hi) >> 1;
       if (s_off[mid] < gend) lo = mid; else hi = mid;
     }
     s_ns = lo + 1;
   }
-  __syncthreads();
 
-  // ---- phase 2: Pi of every q-gram start in [0, span), and the bit-planes
+  // ---- phase 1: Pi of the runs (tile runs: threads 0..255; halo runs: warp 8)
+  HT h[kARun];
   {
-    // packed codes fit 32 bits unless WIDE (a table is indexed by codes < 2^32 too)
     using CT = typename std::conditional<WIDE, uint64_t, uint32_t>::type;
-    const uint32_t qb = a.q * a.bits;
-    const CT mask = qb >= 8 * sizeof(CT) ? ~CT(0) : ((CT(1) << qb) - 1);
-    const uint32_t bsh = a.bits, qm1 = a.q - 1;
-    for (int x0 = kAPer * threadIdx.x; x0 < span; x0 += kAPer * kThreads) {
+    Roll roll;
+    roll.bsh = a.bits;
+    roll.top = a.bits * (a.q - 1);
+    roll.rmul = 1u << (32 - a.bits);
+    roll.tmul = roll.top < 32 ? 1u << roll.top : 0u;   // 32-bit codes only
+    const int qm1 = (int)a.q - 1;
+    const int prime_chunks = (qm1 + 15) / 16;                  // chunks after the run holding q - 1 symbols
+    const int far_syms = qm1 - 16 * (prime_chunks - 1);         // needed symbols of the farthest one
+    const uint32_t seed_folded = a.seed32 ^ (a.seed32 >> 16);
+    const bool vec = ((uintptr_t)a.bytes & 15) == 0;
+    const int halo_runs = 2 * Hs / kARun;
+    const int nwork = threadIdx.x < kATileRuns ? 1 : (halo_runs + 31 - lane) / 32;
+    for (int it = 0; it < nwork; ++it) {
+      int u;   // run index in the span
+      if (threadIdx.x < kATileRuns) {
+        u = Hs / kARun + threadIdx.x;
+      } else {
+        const int k = lane + 32 * it;
+        u = k < Hs / kARun ? k : k + kATileRuns;
+      }
+      const int o0 = kARun * u;
+      const int64_t gx = base + o0;
+      // prime with the q - 1 symbols after the run, farthest chunk first
       CT code = 0;
-      for (uint32_t t = 0; t < qm1; ++t) code = (code << bsh) | s_code[x0 + t];
-      const uint8_t* nxt = s_code + x0 + qm1;
-      HT hv[kAPer];
-#pragma unroll
-      for (int j = 0; j < kAPer; ++j) {
-        code = ((code << bsh) | nxt[j]) & mask;
-        hv[j] = pi_value<HT, WIDE, TABLE>((uint64_t)code, a);
+      if (prime_chunks > 0) {
+        const int64_t gf = gx + 16 * prime_chunks;
+        if (far_syms <= 4) code = prime<4, CT>(code, a, s_rank, gf, vec, roll);
+        else if (far_syms <= 8) code = prime<8, CT>(code, a, s_rank, gf, vec, roll);
+        else if (far_syms <= 12) code = prime<12, CT>(code, a, s_rank, gf, vec, roll);
+        else code = prime<16, CT>(code, a, s_rank, gf, vec, roll);
+        for (int c = prime_chunks - 1; c >= 1; --c) code = prime<16, CT>(code, a, s_rank, gx + 16 * c, vec, roll);
       }
-      if (sizeof(HT) == 4) {
+      uint32_t symw[4] = {0, 0, 0, 0};   // rank codes of the run, one per byte
+      const bool pack = planes && threadIdx.x < kATileRuns;
+      if (pack)
+        hash_run_at<true, CT, HT, WIDE, TABLE>(code, a, s_rank, gx, vec, roll, seed_folded, h, symw);
+      else
+        hash_run_at<false, CT, HT, WIDE, TABLE>(code, a, s_rank, gx, vec, roll, seed_folded, h, symw);
+      if (need_scan) {
 #pragma unroll
-        for (int j = 0; j < kAPer; j += 4)
-          *reinterpret_cast<uint4*>(lev0 + x0 + j) =
-              make_uint4((uint32_t)hv[j], (uint32_t)hv[j + 1], (uint32_t)hv[j + 2], (uint32_t)hv[j + 3]);
-      } else {
+        for (int j = 0; j < kARun; j += 4) {
+          if (sizeof(HT) == 4) {
+            *reinterpret_cast<uint4*>(s_h + o0 + j) =
+                make_uint4((uint32_t)h[j], (uint32_t)h[j + 1], (uint32_t)h[j + 2], (uint32_t)h[j + 3]);
+          } else {
 #pragma unroll
-        for (int j = 0; j < kAPer; ++j) lev0[x0 + j] = hv[j];
-      }
-    }
-  }
-  if (planes) {
-    // plane p, word (g0 + 512 w) / 32 + j: one ballot per word; lane j stores it
-    const uint64_t word0 = guard_words + (uint64_t)(g0 >> 5) + (uint64_t)wid * (kAWarpSpan / 32);
-    const uint64_t wlimit = guard_words + tiles * (kPartTile / 32);
-    uint32_t sym[kAWarpSpan / 32];
-#pragma unroll
-    for (int j = 0; j < kAWarpSpan / 32; ++j) sym[j] = s_code[Hs + kAWarpSpan * wid + 32 * j + lane];
-    for (int p = 0; p < (int)a.bits; ++p) {
-      uint32_t mine = 0;
-#pragma unroll
-      for (int j = 0; j < kAWarpSpan / 32; ++j) {
-        const uint32_t bw = __ballot_sync(0xffffffffu, (sym[j] >> p) & 1u);
-        if (lane == j) mine = bw;
-      }
-      if (lane < kAWarpSpan / 32 && word0 + lane < wlimit) planes[(uint64_t)p * plane_words + word0 + lane] = mine;
-    }
-  }
-  __syncthreads();
-
-  // ---- phase 3: per position (lane-interleaved) string, radius and level
-  const uint32_t wbase = g0 + (uint32_t)(kAWarpSpan * wid);
-  const uint32_t ns = s_ns;
-  const bool cached = ns < cap || sid0 + cap == a.n;   // every string of the CTA is in s_off
-  uint32_t rq2[kAPer / 2];   // radius of position j in bits 16(j&1) .. of word j/2 (0: not queried)
-  uint32_t flags = 0;   // anchor bit per position
-  uint32_t level_mask = 0;
-  {
-    // the current string: [s_o, s_e), radius r, level t; positions i of it
-    // with r <= i <= i_hi are tested (i_hi < r: none)
-    uint32_t sid = 0, s_o = 0, s_e = 0;
-    int32_t r = 0, i_hi = -1;
-    uint32_t lvl = 0;
-    auto set_string = [&]() {
-      const uint32_t slen = s_e - s_o;
-      r = radius32(slen, a.q, a.T, a.r_min);
-      const int64_t hi = (int64_t)slen - a.q - r;   // m - 1 - r, m = |s| - q + 1
-      i_hi = hi < 0 ? -1 : (hi > 0x7fffffff ? 0x7fffffff : (int32_t)hi);
-      if (r > Hs && i_hi >= r) atomicOr(dev_flags, FLAG_BOUNDS);   // cannot happen: r_max bounds every r
-      lvl = (r == 0 || r > Hs || i_hi < r) ? 0u : (uint32_t)r;   // radius of a range query, 0: none
-    };
-    const uint32_t gfirst = wbase + lane;
-    if (gfirst < nbytes) {
-      if (cached) {
-        uint32_t lo = 0, hi = ns;   // s_off[lo] <= g < s_off[hi]
-        while (hi - lo > 1) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if ((uint64_t)s_off[mid] <= gfirst) lo = mid; else hi = mid;
-        }
-        sid = sid0 + lo;
-      } else {
-        sid = string_of(a.offsets, a.n, gfirst);
-      }
-      s_o = (uint32_t)((sid - sid0 <= cap) ? s_off[sid - sid0] : __ldg(a.offsets + sid));
-      s_e = (uint32_t)((sid + 1 - sid0 <= cap) ? s_off[sid + 1 - sid0] : __ldg(a.offsets + sid + 1));
-      set_string();
-    }
-#pragma unroll
-    for (int j = 0; j < kAPer / 2; ++j) rq2[j] = 0;
-#pragma unroll
-    for (int j = 0; j < kAPer; ++j) {
-      const uint32_t g = wbase + 32 * j + lane;
-      if (g < nbytes) {
-        while (g >= s_e) {   // next non-empty string holding g
-          ++sid;
-          s_o = s_e;
-          s_e = (uint32_t)((sid + 1 - sid0 <= cap) ? s_off[sid + 1 - sid0] : __ldg(a.offsets + sid + 1));
-          set_string();
-        }
-        const int32_t i = (int32_t)(g - s_o);
-        const bool tested = i >= r && i <= i_hi;
-        if (i == 0 || (tested && r == 0)) flags |= 1u << j;
-        if (tested && lvl) {
-          rq2[j / 2] |= lvl << (16 * (j & 1));
-          level_mask |= 1u << (31 - __clz(lvl));
-        }
-      }
-    }
-  }
-  // levels this CTA needs: 0 .. the highest floor(log2 r) of its tested positions
-  if (level_mask) atomicOr(&s_levels, level_mask);
-  __syncthreads();
-  const int t_top = s_levels ? 31 - __clz(s_levels) : 0;
-  HT v[kAPer];          // Pi of the position
-#pragma unroll
-  for (int j = 0; j < kAPer; ++j) v[j] = lev0[Hs + kAWarpSpan * wid + 32 * j + lane];
-  HT* cur = lev0;
-  HT* oth = lev1;
-#pragma unroll 1
-  for (int t = 0; t <= t_top; ++t) {
-    if (t > 0) {
-      // level t from level t - 1: min of entries x and x + 2^(t-1)
-      const int half = 1 << (t - 1);
-      const int cnt = span - (1 << t) + 1;
-      for (int x = 4 * threadIdx.x; x < cnt; x += 4 * kThreads) {
-        HT lo4[4], nx4[4], hi4[4];
-        load4(cur + x, lo4);
-        if (half >= 4) {
-          load4(cur + x + half, hi4);
-        } else {
-          load4(cur + x + 4, nx4);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int y = k + half;   // 1 .. 5
-            hi4[k] = y < 4 ? lo4[y & 3] : nx4[y & 3];
+            for (int e = 0; e < 4; ++e) s_h[o0 + j + e] = h[j + e];
           }
         }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) lo4[k] = lo4[k] < hi4[k] ? lo4[k] : hi4[k];
-        store4(oth + x, lo4);
       }
-      __syncthreads();
-      HT* tmp = cur;
-      cur = oth;
-      oth = tmp;
-    }
-    if ((level_mask >> t) & 1u) {
-      const int w = 1 << t;
+      if (need_minima) {
+        HT P[kARun], S[kARun];
+        P[0] = h[0];
 #pragma unroll
-      for (int j = 0; j < kAPer; ++j) {
-        const int r = (int)((rq2[j / 2] >> (16 * (j & 1))) & 0xffffu);
-        if (r != 0 && 31 - __clz(r) == t) {
-          const int x = Hs + kAWarpSpan * wid + 32 * j + lane;
-          const HT lmin = min(cur[x - r], cur[x - w]);
-          const HT rmin = min(cur[x + 1], cur[x + r - w + 1]);
-          if (v[j] < lmin && v[j] < rmin) flags |= 1u << j;
+        for (int j = 1; j < kARun; ++j) P[j] = h[j] < P[j - 1] ? h[j] : P[j - 1];
+        S[kARun - 1] = h[kARun - 1];
+#pragma unroll
+        for (int j = kARun - 2; j >= 0; --j) S[j] = h[j] < S[j + 1] ? h[j] : S[j + 1];
+#pragma unroll
+        for (int j = 0; j < kARun; j += 4) {
+          const int o = swz(o0 + j);
+          if (sizeof(HT) == 4) {
+            *reinterpret_cast<uint4*>(s_P + o) =
+                make_uint4((uint32_t)P[j], (uint32_t)P[j + 1], (uint32_t)P[j + 2], (uint32_t)P[j + 3]);
+            *reinterpret_cast<uint4*>(s_S + o) =
+                make_uint4((uint32_t)S[j], (uint32_t)S[j + 1], (uint32_t)S[j + 2], (uint32_t)S[j + 3]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              s_P[o + e] = P[j + e];
+              s_S[o + e] = S[j + e];
+            }
+          }
+        }
+      }
+      if (pack) {
+        // plane p, positions g .. g+15 of this run: one 16-bit half of word g / 32
+        const uint64_t g = (uint64_t)gx;
+        const uint64_t word = guard_words + (g >> 5);
+        if (word < guard_words + tiles * (kPartTile / 32)) {
+          for (int p = 0; p < (int)a.bits; ++p) {
+            uint32_t half = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              // bit p of the four byte-codes of symw[k] into a nibble (k-th symbol at bit k)
+              const uint32_t x = (symw[k] >> p) & 0x01010101u;
+              half += ((x * 0x01020408u) >> 24) << (4 * k);
+            }
+            reinterpret_cast<uint16_t*>(planes + (uint64_t)p * plane_words + word)[(g >> 4) & 1] = (uint16_t)half;
+          }
         }
       }
     }
   }
+  __syncthreads();
 
-  // ---- phase 4: bitmap words (lane j stores word j of the warp) and counts
-  uint32_t mine = 0, tot = 0;
-#pragma unroll
-  for (int j = 0; j < kAPer; ++j) {
-    const uint32_t word = __ballot_sync(0xffffffffu, (flags >> j) & 1u);
-    if (lane == j) mine = word;
-    tot += __popc(word);
+  // ---- phase 2: the tested positions of each tile run
+  uint32_t flags = 0;   // anchor bit per position of the run
+  const int v = threadIdx.x;
+  const uint32_t x0 = g0 + kARun * (uint32_t)v;   // first position of the run
+  if (v < kATileRuns && x0 < nbytes) {
+    const int o0 = Hs + kARun * v;
+    const uint32_t ns = s_ns;
+    const bool cached = ns < cap || sid0 + cap == a.n;   // every string of the CTA is in s_off
+    uint32_t k;   // the string holding x0
+    if (cached) {
+      uint32_t lo = 0, hi = ns;   // s_off[lo] <= x0 < s_off[hi]
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_off[mid] <= x0) lo = mid; else hi = mid;
+      }
+      k = sid0 + lo;
+    } else {
+      k = string_of(a.offsets, a.n, x0);
+    }
+    const uint32_t xl = x0 + kARun - 1;   // last position of the run
+    for (;;) {
+      uint32_t s_o, s_e;
+      int32_t r;
+      if (k - sid0 < cap) {
+        s_o = s_off[k - sid0];
+        s_e = s_off[k - sid0 + 1];
+        r = s_rad[k - sid0];
+      } else {
+        s_o = (uint32_t)__ldg(a.offsets + k);
+        s_e = (uint32_t)__ldg(a.offsets + k + 1);
+        r = radius32(s_e - s_o, a.q, a.T, a.r_min);
+      }
+      if (s_e > s_o) {
+        if (s_o >= x0) flags |= 1u << (s_o - x0);   // i = 0
+        const int64_t i_hi = (int64_t)(s_e - s_o) - (int64_t)a.q - r;   // m - 1 - r
+        if (i_hi >= r) {
+          const uint32_t lo = max(s_o + (uint32_t)r, x0), hi = min(s_o + (uint32_t)i_hi, xl);
+          if (r > Hs) {
+            atomicOr(dev_flags, FLAG_BOUNDS);   // cannot happen: r_max bounds every r
+          } else if (lo <= hi) {
+            const uint32_t tested = (0xffffu >> (xl - hi)) & (0xffffu << (lo - x0));
+            if (r == 0) {
+              flags |= tested;
+            } else if (r >= kABlockRadius) {
+              // the run lies in every tested window: a candidate is its unique minimum
+              const uint32_t eq = block_min_mask<16>(h);
+              if (__popc(eq) == 1 && (eq & tested)) {
+                const int j = __ffs(eq) - 1;
+                const int o = o0 + j;
+                const HT hx = s_P[swz(o0 + kARun - 1)];
+                // [o - r, o0): suffix minimum of the first run, then whole runs
+                const int la = o - r;
+                HT m = ~HT(0);
+                if (la < o0) {
+                  m = s_S[swz(la)];
+                  for (int u = (la >> 4) + 1; u < (o0 >> 4); ++u) m = min(m, s_S[swz(16 * u)]);
+                }
+                // (o0 + 15, o + r]: whole runs, then a prefix minimum of the last run
+                const int rb = o + r;
+                for (int u = (o0 >> 4) + 1; u < (rb >> 4); ++u) m = min(m, s_S[swz(16 * u)]);
+                if (rb >= o0 + kARun) m = min(m, s_P[swz(rb)]);
+                if (hx < m) flags |= 1u << j;
+              }
+            } else {
+              const int B = r >= 7 ? 8 : (r >= 3 ? 4 : 2);
+              uint32_t cand = (B == 8 ? block_min_mask<8>(h) : (B == 4 ? block_min_mask<4>(h) : block_min_mask<2>(h))) &
+                              tested;
+              while (cand) {
+                const int j = __ffs(cand) - 1;
+                cand &= cand - 1;
+                const int o = o0 + j;
+                const HT hx = s_h[o];
+                HT m = range_min<HT>(s_h + o - r, r, ~HT(0));
+                m = range_min<HT>(s_h + o + 1, r, m);
+                if (hx < m) flags |= 1u << j;
+              }
+            }
+          }
+        }
+      }
+      if (s_e > xl || k + 1 >= a.n) break;
+      ++k;
+    }
   }
-  const uint64_t wword = (uint64_t)(wbase >> 5) + lane;
-  if (lane < kAPer && wword < tiles * (kPartTile / 32)) bitmap[wword] = mine;
-  if (lane == 0) s_warp[wid] = tot;
+
+  // ---- bitmap half-words (16 positions each) and the two tiles' counts
+  if (v < kATileRuns) {
+    const uint64_t hw = (uint64_t)x0 >> 4;
+    if (hw < tiles * (kPartTile / 16)) reinterpret_cast<uint16_t*>(bitmap)[hw] = (uint16_t)flags;
+    const uint32_t tot = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(flags));
+    if (lane == 0) s_warp[wid] = tot;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    constexpr int kHalf = kThreads / 64;   // warps per kPartTile tile
+    constexpr int kHalf = kATileRuns / 64;   // warps per kPartTile tile
     uint32_t c0 = 0, c1 = 0;
     for (int w = 0; w < kHalf; ++w) {
       c0 += s_warp[w];
@@ -509,28 +629,32 @@ int launch_anchor_flags(const PartitionArgs& a, uint32_t* bitmap, uint32_t* tile
     tile_first_kernel<<<(unsigned)(blocks ? blocks : 1), 256, 0, s>>>(a.offsets, a.n, tiles, tile_first);
     MJ_KERNEL_DONE();
   }
+  PartitionArgs ka = a;
+  ka.mul_shr13 = 1u << 19;
+  ka.mul_shr16 = 1u << 16;
   const bool wide = (uint64_t)a.q * a.bits > 32;
   const bool table = a.table != nullptr;
   const size_t smem = (table || wide) ? anchor_smem_bytes<uint64_t>(a.r_max) : anchor_smem_bytes<uint32_t>(a.r_max);
   int dev = 0, max_optin = 0;
   MJ_CUDA_TRY(cudaGetDevice(&dev));
   MJ_CUDA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if (smem + sizeof(int64_t) * (kAMaxStrings + 1) + 64 > (size_t)max_optin) return MJ_ERR_UNSUPPORTED;
+  if (smem + 256 + sizeof(int64_t) * (kAMaxStrings + 1) + sizeof(int32_t) * kAMaxStrings + 64 > (size_t)max_optin)
+    return MJ_ERR_UNSUPPORTED;
   const unsigned grid = (unsigned)((tiles + 1) / 2);
   if (table) {
     auto k = anchor_flags_kernel<uint64_t, false, true>;
     MJ_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k<<<grid, kThreads, smem, s>>>(a, bitmap, tile_count, dev_flags, planes, plane_words, guard_words, tile_first,
+    k<<<grid, kAThreads, smem, s>>>(ka, bitmap, tile_count, dev_flags, planes, plane_words, guard_words, tile_first,
                                    tiles);
   } else if (wide) {
     auto k = anchor_flags_kernel<uint64_t, true, false>;
     MJ_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k<<<grid, kThreads, smem, s>>>(a, bitmap, tile_count, dev_flags, planes, plane_words, guard_words, tile_first,
+    k<<<grid, kAThreads, smem, s>>>(ka, bitmap, tile_count, dev_flags, planes, plane_words, guard_words, tile_first,
                                    tiles);
   } else {
     auto k = anchor_flags_kernel<uint32_t, false, false>;
     MJ_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k<<<grid, kThreads, smem, s>>>(a, bitmap, tile_count, dev_flags, planes, plane_words, guard_words, tile_first,
+    k<<<grid, kAThreads, smem, s>>>(ka, bitmap, tile_count, dev_flags, planes, plane_words, guard_words, tile_first,
                                    tiles);
   }
   MJ_KERNEL_DONE();
