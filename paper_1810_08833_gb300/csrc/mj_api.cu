@@ -101,8 +101,7 @@ struct mj_ctx {
   // workspace
   Buf hist, dev_flags, small;
   Buf bitmap, tile_count, tile_off, scan_tmp, tile_first;
-  Buf anchor_pos, anchor_sid;
-  Buf rec_sid, rec_pos, rec_len, rec_slen, rec_h61;
+  Buf recs;   // partition records (PRec) in position order
   Buf keys, keys_alt, idx, idx_alt, sort_tmp;
   Buf srec;   // partition records in group order (PRec)
   Buf pair_count, pair_off, pairs, pairs_alt;
@@ -319,21 +318,10 @@ int partition(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
   const uint32_t n_anchor = *(uint32_t*)c->h_small;
   c->stats.device_flags |= *(uint32_t*)((char*)c->h_small + 8);
   if (c->stats.device_flags) return MJ_ERR_DEVICE;
-  MJ_TRY(c->anchor_pos.reserve((size_t)n_anchor * 4 + 16, s));
-  MJ_TRY(c->anchor_sid.reserve((size_t)n_anchor * 4 + 16, s));
+  MJ_TRY(c->recs.reserve((size_t)n_anchor * sizeof(PRec) + sizeof(PRec), s));
   tstart(c, 1, s);
-  MJ_TRY(launch_anchor_emit(a, c->bitmap.as<uint32_t>(), c->tile_off.as<uint32_t>(), c->tile_first.as<uint32_t>(),
-                            c->anchor_pos.as<uint32_t>(),
-                            c->anchor_sid.as<uint32_t>(), s));
-  MJ_TRY(c->rec_sid.reserve((size_t)n_anchor * 4 + 16, s));
-  MJ_TRY(c->rec_pos.reserve((size_t)n_anchor * 4 + 16, s));
-  MJ_TRY(c->rec_len.reserve((size_t)n_anchor * 4 + 16, s));
-  MJ_TRY(c->rec_slen.reserve((size_t)n_anchor * 4 + 16, s));
-  MJ_TRY(c->rec_h61.reserve((size_t)n_anchor * 8 + 16, s));
-  MJ_TRY(launch_partition_records(d_bytes, d_offsets, c->anchor_pos.as<uint32_t>(), c->anchor_sid.as<uint32_t>(),
-                                  n_anchor, key_base_for(d.seed), c->rec_sid.as<uint32_t>(),
-                                  c->rec_pos.as<uint32_t>(), c->rec_len.as<uint32_t>(), c->rec_slen.as<uint32_t>(),
-                                  c->rec_h61.as<uint64_t>(), s));
+  MJ_TRY(launch_partition_records(a, c->bitmap.as<uint32_t>(), c->tile_off.as<uint32_t>(),
+                                  c->tile_first.as<uint32_t>(), key_base_for(d.seed), c->recs.as<PRec>(), s));
   tstop(c, 1, s);
   c->n_part = n_anchor;
   c->stats.n_partitions = n_anchor;
@@ -361,8 +349,8 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   MJ_TRY(c->idx_alt.reserve((size_t)nr * 4, s));
   MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(nr), s));
   tstart(c, 2, s);
-  MJ_TRY(launch_make_group_keys(c->rec_len.as<uint32_t>(), c->rec_slen.as<uint32_t>(), c->rec_h61.as<uint64_t>(), nr,
-                                slen_bits, hash_bits, c->keys.as<uint64_t>(), c->idx.as<uint32_t>(), s));
+  MJ_TRY(launch_make_group_keys(c->recs.as<PRec>(), nr, slen_bits, hash_bits, c->keys.as<uint64_t>(),
+                                c->idx.as<uint32_t>(), s));
   bool alt = false;
   MJ_TRY(radix_sort_u64(c->keys.as<uint64_t>(), c->keys_alt.as<uint64_t>(), c->idx.as<uint32_t>(),
                         c->idx_alt.as<uint32_t>(), nr, 0, hash_bits + slen_bits, c->sort_tmp.p, &alt, s));
@@ -370,9 +358,7 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   const uint32_t* sidx = alt ? c->idx_alt.as<uint32_t>() : c->idx.as<uint32_t>();
   MJ_TRY(c->srec.reserve((size_t)nr * sizeof(PRec), s));
   const PRec* r = c->srec.as<PRec>();
-  MJ_TRY(launch_gather_records(sidx, skeys, nr, slen_bits, c->rec_sid.as<uint32_t>(), c->rec_pos.as<uint32_t>(),
-                               c->rec_slen.as<uint32_t>(), c->rec_len.as<uint32_t>(), c->rec_h61.as<uint64_t>(),
-                               c->srec.as<PRec>(), s));
+  MJ_TRY(launch_gather_records(sidx, skeys, nr, slen_bits, c->recs.as<PRec>(), c->srec.as<PRec>(), s));
   tstop(c, 2, s);
   if (flags & 1u) {
     MJ_TRY(c->small.reserve(64, s));
@@ -602,11 +588,6 @@ int verify_ordered_graph(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_off
   return MJ_OK;
 }
 
-uint64_t readback_u32(mj_ctx* c, const uint32_t* d, cudaStream_t s, int* st) {
-  *st = readback(c, d, 4, s);
-  return *st == MJ_OK ? (uint64_t)*(uint32_t*)c->h_small : 0;
-}
-
 // Verification of all candidates of the last mj_join (a8, and a9 in learned
 // mode), then the K-band cell count.  Plain: one pass with band K.  Learned:
 // features -> MLP -> first-pass band per pair; first passes grouped by band
@@ -624,7 +605,7 @@ int verify_stage(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, ui
   const bool want_x = (p->flags & MJ_FLAG_FEATURES) != 0;
   if (want_feat) {
     MJ_TRY(c->parts.reserve((size_t)n * 4 + 16, s));
-    MJ_TRY(launch_partition_counts(c->anchor_sid.as<uint32_t>(), c->n_part, n, c->parts.as<uint32_t>(), s));
+    MJ_TRY(launch_partition_counts(c->recs.as<PRec>(), c->n_part, n, c->parts.as<uint32_t>(), s));
   }
   if (want_x) {
     MJ_TRY(c->mult.reserve(m * 4, s));
@@ -817,8 +798,7 @@ void mj_destroy(mj_ctx* c) {
   cudaDeviceSynchronize();
   Buf* bufs[] = {&c->hist, &c->dev_flags, &c->small, &c->bitmap, &c->tile_count, &c->tile_off, &c->scan_tmp,
                  &c->tile_first,
-                 &c->anchor_pos, &c->anchor_sid, &c->rec_sid, &c->rec_pos, &c->rec_len, &c->rec_slen,
-                 &c->rec_h61, &c->keys, &c->keys_alt, &c->idx, &c->idx_alt, &c->sort_tmp, &c->srec, &c->pair_count, &c->pair_off, &c->pairs, &c->pairs_alt,
+                 &c->recs, &c->keys, &c->keys_alt, &c->idx, &c->idx_alt, &c->sort_tmp, &c->srec, &c->pair_count, &c->pair_off, &c->pairs, &c->pairs_alt,
                  &c->uflags, &c->uoffs, &c->cand_i, &c->cand_j, &c->planes, &c->ed, &c->eflags, &c->eoffs,
                  &c->out_i, &c->out_j, &c->out_ed, &c->in_bytes, &c->in_offsets, &c->branges,
                  &c->band, &c->feat_x, &c->mult, &c->run_start, &c->parts, &c->yhat, &c->kband, &c->lvals,
@@ -896,11 +876,7 @@ int mj_partition_copy(mj_ctx* c, uint32_t* d_sid, uint32_t* d_pos, uint32_t* d_l
   cudaStream_t s = S(stream);
   const size_t n = c->n_part;
   if (!n) return MJ_OK;
-  if (d_sid) MJ_CUDA_TRY(cudaMemcpyAsync(d_sid, c->rec_sid.p, n * 4, cudaMemcpyDeviceToDevice, s));
-  if (d_pos) MJ_CUDA_TRY(cudaMemcpyAsync(d_pos, c->rec_pos.p, n * 4, cudaMemcpyDeviceToDevice, s));
-  if (d_len) MJ_CUDA_TRY(cudaMemcpyAsync(d_len, c->rec_len.p, n * 4, cudaMemcpyDeviceToDevice, s));
-  if (d_key) MJ_CUDA_TRY(cudaMemcpyAsync(d_key, c->rec_h61.p, n * 8, cudaMemcpyDeviceToDevice, s));
-  return MJ_OK;
+  return launch_unpack_records(c->recs.as<PRec>(), n, d_sid, d_pos, d_len, d_key, s);
 }
 
 int mj_candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const mj_params* p,

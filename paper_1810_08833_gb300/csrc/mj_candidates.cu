@@ -62,46 +62,35 @@ __device__ __forceinline__ uint64_t mix64(uint64_t k) {  // MurmurHash3 fmix64
 }
 
 // Group key: 32 hash bits of (len, key) above slen_bits bits of string length.
-__global__ void group_keys_kernel(const uint32_t* __restrict__ rec_len, const uint32_t* __restrict__ rec_slen,
-                                  const uint64_t* __restrict__ rec_h61, uint32_t n, int slen_bits, int hash_bits,
+__global__ void group_keys_kernel(const PRec* __restrict__ recs, uint32_t n, int slen_bits, int hash_bits,
                                   uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t g = mix64(rec_h61[t] ^ ((uint64_t)rec_len[t] * 0x9e3779b97f4a7c15ull));
-    keys[t] = ((g >> (64 - hash_bits)) << slen_bits) | (uint64_t)rec_slen[t];
+    const PRec r = load_rec(recs, t);
+    uint64_t g = mix64(r.h61 ^ ((uint64_t)r.len * 0x9e3779b97f4a7c15ull));
+    keys[t] = ((g >> (64 - hash_bits)) << slen_bits) | (uint64_t)r.slen;
     idx[t] = (uint32_t)t;
   }
 }
 
 __global__ void gather_kernel(const uint32_t* __restrict__ idx, const uint64_t* __restrict__ keys, uint32_t n,
-                              int slen_bits, const uint32_t* __restrict__ sid, const uint32_t* __restrict__ pos,
-                              const uint32_t* __restrict__ slen, const uint32_t* __restrict__ len,
-                              const uint64_t* __restrict__ h61, PRec* __restrict__ o) {
+                              int slen_bits, const PRec* __restrict__ recs, PRec* __restrict__ o) {
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t s = idx[t];
-    PRec r;
-    r.h61 = h61[s];
+    PRec r = load_rec(recs, idx[t]);
     r.run = (uint32_t)(keys[t] >> slen_bits);
-    r.slen = slen[s];
-    r.len = len[s];
-    r.sid = sid[s];
-    r.pos = pos[s];
-    r.pad = 0;
-    o[t] = r;
+    store_rec(o, t, r);
   }
 }
 
-__device__ __forceinline__ PRec load_rec(const PRec* __restrict__ r, uint64_t u) {
-  const uint4* p = reinterpret_cast<const uint4*>(r + u);
-  const uint4 a = __ldg(p), b = __ldg(p + 1);
-  PRec x;
-  x.h61 = (uint64_t)a.x | ((uint64_t)a.y << 32);
-  x.run = a.z;
-  x.slen = a.w;
-  x.len = b.x;
-  x.sid = b.y;
-  x.pos = b.z;
-  x.pad = b.w;
-  return x;
+__global__ void unpack_records_kernel(const PRec* __restrict__ recs, uint64_t n, uint32_t* __restrict__ sid,
+                                      uint32_t* __restrict__ pos, uint32_t* __restrict__ len,
+                                      uint64_t* __restrict__ key) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
+    const PRec r = load_rec(recs, t);
+    if (sid) sid[t] = r.sid;
+    if (pos) pos[t] = r.pos;
+    if (len) len[t] = r.len;
+    if (key) key[t] = r.h61;
+  }
 }
 
 // Walks the run of record t; EMIT=false counts, EMIT=true writes pairs.
@@ -224,19 +213,20 @@ __global__ void multiplicity_kernel(const uint32_t* __restrict__ run_start, uint
 // parts[s] = number of anchors (= partitions) of string s: the anchor list
 // is in string order, so it is the width of s's run, found by two binary
 // searches per string
-__device__ __forceinline__ uint64_t lower_bound_u32(const uint32_t* __restrict__ a, uint64_t n, uint32_t v) {
+// First record of string >= v among n records in string order.
+__device__ __forceinline__ uint64_t first_rec_of(const PRec* __restrict__ r, uint64_t n, uint32_t v) {
   uint64_t lo = 0, hi = n;
   while (lo < hi) {
     const uint64_t mid = (lo + hi) >> 1;
-    if (a[mid] < v) lo = mid + 1; else hi = mid;
+    if (__ldg(&r[mid].sid) < v) lo = mid + 1; else hi = mid;
   }
   return lo;
 }
 
-__global__ void partition_counts_kernel(const uint32_t* __restrict__ sid, uint64_t n_anchor, uint32_t n,
+__global__ void partition_counts_kernel(const PRec* __restrict__ recs, uint64_t n_rec, uint32_t n,
                                         uint32_t* __restrict__ parts) {
   for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (uint64_t)gridDim.x * blockDim.x)
-    parts[s] = (uint32_t)(lower_bound_u32(sid, n_anchor, (uint32_t)s + 1) - lower_bound_u32(sid, n_anchor, (uint32_t)s));
+    parts[s] = (uint32_t)(first_rec_of(recs, n_rec, (uint32_t)s + 1) - first_rec_of(recs, n_rec, (uint32_t)s));
 }
 
 // First-pass bucket of a learned band k (0: no first pass).  Band widths
@@ -362,20 +352,27 @@ int launch_max_length(const int64_t* offsets, uint32_t n, unsigned long long* ou
   return MJ_OK;
 }
 
-int launch_make_group_keys(const uint32_t* rec_len, const uint32_t* rec_slen, const uint64_t* rec_h61, uint32_t n,
-                           int slen_bits, int hash_bits, uint64_t* keys, uint32_t* idx, cudaStream_t s) {
+int launch_make_group_keys(const PRec* recs, uint32_t n, int slen_bits, int hash_bits, uint64_t* keys,
+                           uint32_t* idx, cudaStream_t s) {
   if (!n) return MJ_OK;
   if (hash_bits < 1 || hash_bits > 32 || slen_bits < 1 || slen_bits + hash_bits > 64) return MJ_ERR_ARG;
-  group_keys_kernel<<<grid_for(n), 256, 0, s>>>(rec_len, rec_slen, rec_h61, n, slen_bits, hash_bits, keys, idx);
+  group_keys_kernel<<<grid_for(n), 256, 0, s>>>(recs, n, slen_bits, hash_bits, keys, idx);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
-int launch_gather_records(const uint32_t* idx, const uint64_t* keys, uint32_t n, int slen_bits, const uint32_t* sid,
-                          const uint32_t* pos, const uint32_t* slen, const uint32_t* len, const uint64_t* h61,
+int launch_gather_records(const uint32_t* idx, const uint64_t* keys, uint32_t n, int slen_bits, const PRec* recs,
                           PRec* o, cudaStream_t s) {
   if (!n) return MJ_OK;
-  gather_kernel<<<grid_for(n), 256, 0, s>>>(idx, keys, n, slen_bits, sid, pos, slen, len, h61, o);
+  gather_kernel<<<grid_for(n), 256, 0, s>>>(idx, keys, n, slen_bits, recs, o);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
+int launch_unpack_records(const PRec* recs, uint64_t n, uint32_t* sid, uint32_t* pos, uint32_t* len, uint64_t* key,
+                          cudaStream_t s) {
+  if (!n) return MJ_OK;
+  unpack_records_kernel<<<grid_for(n), 256, 0, s>>>(recs, n, sid, pos, len, key);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }
@@ -445,10 +442,9 @@ int launch_multiplicity(const uint32_t* run_start, uint64_t nc, uint64_t raw, ui
   return MJ_OK;
 }
 
-int launch_partition_counts(const uint32_t* anchor_sid, uint64_t n_anchor, uint32_t n, uint32_t* parts,
-                            cudaStream_t s) {
+int launch_partition_counts(const PRec* recs, uint64_t n_rec, uint32_t n, uint32_t* parts, cudaStream_t s) {
   if (!n) return MJ_OK;
-  partition_counts_kernel<<<grid_for(n), 256, 0, s>>>(anchor_sid, n_anchor, n, parts);
+  partition_counts_kernel<<<grid_for(n), 256, 0, s>>>(recs, n_rec, n, parts);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }

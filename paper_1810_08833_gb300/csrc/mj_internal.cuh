@@ -76,6 +76,35 @@ int launch_byte_histogram(const uint8_t* bytes, uint64_t nbytes, unsigned long l
                           cudaStream_t s);
 int launch_max_length(const int64_t* offsets, uint32_t n, unsigned long long* out, cudaStream_t s);
 
+// A partition record, packed in two 16-byte words: Karp-Rabin key, group
+// run (the hash bits of the grouping sort key; 0 until the records are put
+// in group order), string length, partition length, string id, position.
+struct alignas(16) PRec {
+  uint64_t h61;
+  uint32_t run, slen, len, sid, pos, pad;
+};
+static_assert(sizeof(PRec) == 32, "PRec is two 16-byte words");
+
+__device__ __forceinline__ PRec load_rec(const PRec* __restrict__ r, uint64_t u) {
+  const uint4* p = reinterpret_cast<const uint4*>(r + u);
+  const uint4 a = __ldg(p), b = __ldg(p + 1);
+  PRec x;
+  x.h61 = (uint64_t)a.x | ((uint64_t)a.y << 32);
+  x.run = a.z;
+  x.slen = a.w;
+  x.len = b.x;
+  x.sid = b.y;
+  x.pos = b.z;
+  x.pad = b.w;
+  return x;
+}
+
+__device__ __forceinline__ void store_rec(PRec* __restrict__ r, uint64_t u, const PRec& x) {
+  uint4* p = reinterpret_cast<uint4*>(r + u);
+  p[0] = make_uint4((uint32_t)x.h61, (uint32_t)(x.h61 >> 32), x.run, x.slen);
+  p[1] = make_uint4(x.len, x.sid, x.pos, x.pad);
+}
+
 // a2-a3: anchor bitmap (1 bit per byte position) and per-tile anchor counts.
 struct PartitionArgs {
   const uint8_t* bytes;
@@ -99,14 +128,13 @@ uint64_t partition_num_tiles(uint64_t nbytes);
 int launch_anchor_flags(const PartitionArgs& a, uint32_t* bitmap, uint32_t* tile_count,
                         uint32_t* dev_flags, uint32_t* planes, uint64_t plane_words,
                         uint32_t guard_words, uint32_t* tile_first, cudaStream_t s);
-// a4: anchors in position order (global byte position and string id).
-int launch_anchor_emit(const PartitionArgs& a, const uint32_t* bitmap, const uint32_t* tile_offset,
-                       const uint32_t* tile_first, uint32_t* anchor_pos, uint32_t* anchor_sid, cudaStream_t s);
-// a4: partition records from consecutive anchors; key = (len, H61(substring)).
-int launch_partition_records(const uint8_t* bytes, const int64_t* offsets, const uint32_t* anchor_pos,
-                             const uint32_t* anchor_sid, uint32_t n_anchor, uint64_t key_base,
-                             uint32_t* rec_sid, uint32_t* rec_pos, uint32_t* rec_len,
-                             uint32_t* rec_slen, uint64_t* rec_h61, cudaStream_t s);
+// a4: one partition record per anchor, in position order (so string order),
+// from the bitmap and the per-tile list offsets; key = (len, H61(substring)).
+int launch_partition_records(const PartitionArgs& a, const uint32_t* bitmap, const uint32_t* tile_offset,
+                             const uint32_t* tile_first, uint64_t key_base, PRec* recs, cudaStream_t s);
+// The fields of n records as separate arrays (any may be null).
+int launch_unpack_records(const PRec* recs, uint64_t n, uint32_t* sid, uint32_t* pos, uint32_t* len, uint64_t* key,
+                          cudaStream_t s);
 
 // scans (exclusive, in place allowed); temp from scan_temp_bytes
 size_t scan_temp_bytes(uint64_t n);
@@ -127,20 +155,11 @@ int radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t*
 
 // a5-a6: grouping keys and pair emission.  A key is hash_bits (<= 32) bits
 // of a hash of (len, Karp-Rabin key) above slen_bits bits of string length.
-int launch_make_group_keys(const uint32_t* rec_len, const uint32_t* rec_slen, const uint64_t* rec_h61,
-                           uint32_t n_rec, int slen_bits, int hash_bits, uint64_t* keys, uint32_t* idx,
-                           cudaStream_t s);
-// A partition record in group order, packed for the walks of the pair
-// emission (two 16-byte loads): Karp-Rabin key, group run (the hash bits
-// of the sort key), string length, partition length, string id, position.
-struct alignas(16) PRec {
-  uint64_t h61;
-  uint32_t run, slen, len, sid, pos, pad;
-};
-static_assert(sizeof(PRec) == 32, "PRec is two 16-byte words");
+int launch_make_group_keys(const PRec* recs, uint32_t n_rec, int slen_bits, int hash_bits, uint64_t* keys,
+                           uint32_t* idx, cudaStream_t s);
+// Records in group order: out[t] = recs[idx[t]] with run = keys[t] >> slen_bits.
 int launch_gather_records(const uint32_t* idx, const uint64_t* keys, uint32_t n_rec, int slen_bits,
-                          const uint32_t* rec_sid, const uint32_t* rec_pos, const uint32_t* rec_slen,
-                          const uint32_t* rec_len, const uint64_t* rec_h61, PRec* out, cudaStream_t s);
+                          const PRec* recs, PRec* out, cudaStream_t s);
 int launch_count_pairs(const PRec* r, uint32_t n_rec, uint32_t K, uint32_t* count, cudaStream_t s);
 // pairs are packed as (i << nb) | j, i < j
 int launch_fill_pairs(const PRec* r, uint32_t n_rec, uint32_t K, int nb, const uint64_t* offs, uint64_t* pairs,
@@ -228,10 +247,9 @@ int launch_band_rule(const float* yhat, const uint32_t* ci, const uint32_t* cj, 
                      uint32_t K, uint32_t margin, uint32_t* kband, cudaStream_t s);
 
 // multiplicity of every candidate from the run starts written by the pair
-// compaction; partitions per string from the anchor list
+// compaction; partitions per string from the records (in string order)
 int launch_multiplicity(const uint32_t* run_start, uint64_t nc, uint64_t raw, uint32_t* mult, cudaStream_t s);
-int launch_partition_counts(const uint32_t* anchor_sid, uint64_t n_anchor, uint32_t n, uint32_t* parts,
-                            cudaStream_t s);
+int launch_partition_counts(const PRec* recs, uint64_t n_rec, uint32_t n, uint32_t* parts, cudaStream_t s);
 // Learned first passes: the pairs of every first-pass bucket b = 1 .. nb
 // (band widths below band K's word count; bucket 0 = no first pass) listed
 // contiguously in list, bucket b at [ranges[2b], ranges[2b+1]); cnt holds

@@ -38,9 +38,6 @@ __device__ __forceinline__ uint32_t string_of(const int64_t* __restrict__ off, u
   return lo;
 }
 
-constexpr int kThreads = 256;
-constexpr int kPerThread = kPartTile / kThreads;  // positions per thread in the emit kernel
-
 // The anchor kernel: one CTA per kATile positions (two kPartTile tiles).
 // Each of the first 256 threads owns a run of 16 consecutive positions of the
 // tile; a ninth warp takes the runs of the halos.
@@ -511,46 +508,6 @@ __global__ void __launch_bounds__(kAThreads, sizeof(HT) == 4 ? 4 : 2) anchor_fla
   }
 }
 
-// Anchors of one tile in position order, at the tile's offset in the list.
-// Thread t takes kPerThread consecutive positions (a slice of one bitmap word).
-__global__ void __launch_bounds__(kThreads) anchor_emit_kernel(PartitionArgs a, const uint32_t* __restrict__ bitmap,
-                                                               const uint32_t* __restrict__ tile_offset,
-                                                               const uint32_t* __restrict__ tile_first,
-                                                               uint32_t* __restrict__ anchor_pos,
-                                                               uint32_t* __restrict__ anchor_sid) {
-  constexpr int kPer = 32 / kPerThread;  // threads sharing one bitmap word
-  const uint32_t word = __ldg(bitmap + (uint64_t)blockIdx.x * (kPartTile / 32) + threadIdx.x / kPer);
-  const uint32_t flags = (word >> (kPerThread * (threadIdx.x % kPer))) & ((1u << kPerThread) - 1u);
-  const uint32_t c = __popc(flags);
-  // block exclusive scan of c
-  uint32_t x = c;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  __shared__ uint32_t s_warp[kThreads / 32];
-  if (lane == 31) s_warp[wid] = x;
-  __syncthreads();
-  uint32_t wsum = 0;
-  for (int w = 0; w < wid; ++w) wsum += s_warp[w];
-  uint32_t out = __ldg(tile_offset + blockIdx.x) + wsum + x - c;
-  if (!flags) return;
-  const uint64_t gfirst = (uint64_t)blockIdx.x * kPartTile + (uint64_t)threadIdx.x * kPerThread;
-  uint32_t sid = __ldg(tile_first + blockIdx.x);
-  int64_t s_end = __ldg(a.offsets + sid + 1);
-  uint32_t f = flags;
-  while (f) {
-    int k = __ffs(f) - 1;
-    f &= f - 1;
-    uint64_t g = gfirst + k;
-    while ((int64_t)g >= s_end) { ++sid; s_end = __ldg(a.offsets + sid + 1); }
-    anchor_pos[out] = (uint32_t)g;
-    anchor_sid[out] = sid;
-    ++out;
-  }
-}
-
 constexpr uint64_t kM61 = (1ull << 61) - 1;
 
 __device__ __forceinline__ uint64_t mulmod61(uint64_t a, uint64_t b) {
@@ -564,53 +521,139 @@ __device__ __forceinline__ uint64_t addmod61(uint64_t a, uint64_t b) {
   return r >= kM61 ? r - kM61 : r;
 }
 
-// One partition per anchor: it runs to the next anchor of the same string,
-// else to the string's end (Alg. 1).  The key is the Karp-Rabin polynomial
-// sum of (byte + 1) * base^(len-1-x) modulo 2^61-1, evaluated by Horner's
-// rule four bytes per modular multiply: with T_k[c] = (c+1) * base^k (k = 1..3,
-// shared-memory tables built per block), a block of four bytes adds
-// T3[b0] + T2[b1] + T1[b2] + (b3+1) to h * base^4.  The key equals the
+// One partition per anchor (Alg. 1): it runs from the anchor to the next
+// anchor of its string, else to the string's end.  Every non-empty string
+// starts with an anchor, so that end is the next anchor of the bitmap (or the
+// end of the input).  The key is the Karp-Rabin polynomial sum of
+// (byte + 1) * base^(len-1-x) modulo 2^61-1, evaluated by Horner's rule eight
+// bytes per modular multiply: with T_k[c] = (c+1) * base^k (k = 1..7,
+// shared-memory tables built per block), a block of eight bytes adds
+// T7[b0] + T6[b1] + ... + T1[b6] + (b7+1) to h * base^8 (the leading len mod 8
+// bytes go first, one at a time or as one block of four).  The key equals the
 // byte-at-a-time polynomial.
+// A CTA takes kRecWords bitmap words (whole kPartTile tiles).  It lists their
+// anchors in shared memory (a block scan of the words' counts), then its
+// threads take one anchor at a time; an anchor's record goes to its tile's
+// list offset plus its rank within the tile.
 constexpr int kRecThreads = 256;
+constexpr int kRecWords = kRecThreads;                 // 8,192 positions: 4 tiles
+constexpr int kRecTileWords = kPartTile / 32;          // 64 words per tile
+constexpr int kRecStrings = 256;                       // string offsets cached per CTA
 
 __global__ void __launch_bounds__(kRecThreads) partition_records_kernel(
-    const uint8_t* __restrict__ bytes, const int64_t* __restrict__ offsets, const uint32_t* __restrict__ anchor_pos,
-    const uint32_t* __restrict__ anchor_sid, uint32_t n_anchor, uint64_t key_base, uint32_t* __restrict__ rec_sid,
-    uint32_t* __restrict__ rec_pos, uint32_t* __restrict__ rec_len, uint32_t* __restrict__ rec_slen,
-    uint64_t* __restrict__ rec_h61) {
-  __shared__ uint64_t s_t[3][256];
-  const uint64_t b2 = mulmod61(key_base, key_base), b3 = mulmod61(b2, key_base), b4 = mulmod61(b3, key_base);
+    PartitionArgs a, const uint32_t* __restrict__ bitmap, uint64_t nwords, const uint32_t* __restrict__ tile_offset,
+    const uint32_t* __restrict__ tile_first, uint64_t key_base, PRec* __restrict__ recs) {
+  __shared__ uint64_t s_t[7][256];                 // s_t[k - 1][c] = (c + 1) * base^k
+  __shared__ uint32_t s_anc[kRecWords * 32];       // anchor positions of the CTA, in order
+  __shared__ uint32_t s_off[kRecStrings + 1];     // offsets[sid0 .. sid0 + cap]
+  __shared__ uint32_t s_warp[kRecThreads / 32];
+  __shared__ uint32_t s_tile0[kRecWords / kRecTileWords];   // list index of each tile's first anchor
+  __shared__ uint32_t s_total;
+  uint64_t b4 = 0, b8 = key_base;   // base^4 and base^8
   {
     const uint64_t c1 = (uint64_t)threadIdx.x + 1;
-    s_t[0][threadIdx.x] = mulmod61(c1, key_base);
-    s_t[1][threadIdx.x] = mulmod61(c1, b2);
-    s_t[2][threadIdx.x] = mulmod61(c1, b3);
+    uint64_t bk = key_base;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      s_t[k][threadIdx.x] = mulmod61(c1, bk);
+      if (k == 3) b4 = bk;
+      bk = mulmod61(bk, key_base);
+    }
+    b8 = bk;
+  }
+  const uint64_t w0 = (uint64_t)blockIdx.x * kRecWords;
+  const uint64_t word = w0 + threadIdx.x;
+  const uint32_t bits = word < nwords ? __ldg(bitmap + word) : 0u;
+  const uint32_t sid0 = __ldg(tile_first + w0 / kRecTileWords);
+  const uint32_t cap = min((uint32_t)kRecStrings, a.n - sid0);
+  for (uint32_t t = threadIdx.x; t <= cap; t += kRecThreads) s_off[t] = (uint32_t)__ldg(a.offsets + sid0 + t);
+  // block exclusive scan of the anchor counts, then the anchor list
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t c = __popc(bits);
+  uint32_t x = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[wid] = x;
+  __syncthreads();
+  uint32_t excl = x - c;
+  for (int w = 0; w < wid; ++w) excl += s_warp[w];
+  if (threadIdx.x % kRecTileWords == 0) s_tile0[threadIdx.x / kRecTileWords] = excl;
+  if (threadIdx.x == kRecThreads - 1) s_total = excl + c;
+  {
+    uint32_t f = bits, at = excl;
+    const uint32_t gw = (uint32_t)(word * 32);
+    while (f) {
+      s_anc[at++] = gw + (uint32_t)(__ffs(f) - 1);
+      f &= f - 1;
+    }
   }
   __syncthreads();
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_anchor;
-       t += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t g = anchor_pos[t], sid = anchor_sid[t];
-    const int64_t s_off = __ldg(offsets + sid), s_end = __ldg(offsets + sid + 1);
-    int64_t end = s_end;
-    if (t + 1 < n_anchor && anchor_sid[t + 1] == sid) end = anchor_pos[t + 1];
-    const uint8_t* p = bytes + g;
-    const uint32_t len = (uint32_t)(end - (int64_t)g);
+  const uint32_t total = s_total;
+  const bool all_cached = sid0 + cap == a.n;
+  const uint32_t nbytes = (uint32_t)a.nbytes;
+  for (uint32_t t = threadIdx.x; t < total; t += kRecThreads) {
+    const uint32_t g = s_anc[t];
+    // the string holding g
+    uint32_t k;
+    if (all_cached || s_off[cap] > g) {
+      uint32_t lo = 0, hi = cap;   // s_off[lo] <= g < s_off[hi]
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_off[mid] <= g) lo = mid; else hi = mid;
+      }
+      k = sid0 + lo;
+    } else {
+      k = string_of(a.offsets, a.n, g);
+    }
+    const uint32_t s_o = k - sid0 <= cap ? s_off[k - sid0] : (uint32_t)__ldg(a.offsets + k);
+    const uint32_t s_e = k + 1 - sid0 <= cap ? s_off[k + 1 - sid0] : (uint32_t)__ldg(a.offsets + k + 1);
+    // the next anchor: in the list, else in the words after the CTA's
+    uint32_t end = s_e;
+    if (t + 1 < total) {
+      end = s_anc[t + 1];
+    } else {
+      for (uint64_t ww = w0 + kRecWords; ww < nwords && ww * 32 < s_e; ++ww) {
+        const uint32_t y = __ldg(bitmap + ww);
+        if (y) {
+          end = (uint32_t)(ww * 32) + (uint32_t)(__ffs(y) - 1);
+          break;
+        }
+      }
+    }
+    end = min(end, min(s_e, nbytes));
+    const uint8_t* p = a.bytes + g;
+    const uint32_t len = end - g;
     const uint32_t head = len & 3u;
     uint64_t h = 0;
-    for (uint32_t x = 0; x < head; ++x) h = addmod61(mulmod61(h, key_base), (uint64_t)__ldg(p + x) + 1);
-    for (uint32_t x = head; x < len; x += 4) {
-      const uint32_t c0 = __ldg(p + x), c1 = __ldg(p + x + 1), c2 = __ldg(p + x + 2), c3 = __ldg(p + x + 3);
-      uint64_t u = s_t[2][c0] + s_t[1][c1];     // < 2^62
-      u = (u & kM61) + (u >> 61);
-      u += s_t[0][c2] + (uint64_t)c3 + 1;       // < 2^63
-      u = (u & kM61) + (u >> 61);
-      h = addmod61(mulmod61(h, b4), u >= kM61 ? u - kM61 : u);
+    for (uint32_t x2 = 0; x2 < head; ++x2) h = addmod61(mulmod61(h, key_base), (uint64_t)__ldg(p + x2) + 1);
+    uint32_t x2 = head;
+    if (len & 4u) {
+      const uint64_t u = s_t[2][__ldg(p + x2)] + s_t[1][__ldg(p + x2 + 1)] + s_t[0][__ldg(p + x2 + 2)] +
+                         (uint64_t)__ldg(p + x2 + 3) + 1;   // < 2^63
+      const uint64_t v = (u & kM61) + (u >> 61);
+      h = addmod61(mulmod61(h, b4), v >= kM61 ? v - kM61 : v);
+      x2 += 4;
     }
-    rec_sid[t] = sid;
-    rec_pos[t] = (uint32_t)((int64_t)g - s_off);
-    rec_len[t] = len;
-    rec_slen[t] = (uint32_t)(s_end - s_off);
-    rec_h61[t] = h;
+    for (; x2 < len; x2 += 8) {
+      uint64_t u = (uint64_t)__ldg(p + x2 + 7) + 1;   // seven terms < 2^61 and one < 2^9: < 2^64
+#pragma unroll
+      for (int e = 0; e < 7; ++e) u += s_t[6 - e][__ldg(p + x2 + e)];
+      const uint64_t v = (u & kM61) + (u >> 61);
+      h = addmod61(mulmod61(h, b8), v >= kM61 ? v - kM61 : v);
+    }
+    PRec r;
+    r.h61 = h;
+    r.run = 0;
+    r.slen = s_e - s_o;
+    r.len = len;
+    r.sid = k;
+    r.pos = g - s_o;
+    r.pad = 0;
+    const uint32_t tile = g / kPartTile - (uint32_t)(w0 / kRecTileWords);   // tile within the CTA
+    store_rec(recs, (uint64_t)__ldg(tile_offset + w0 / kRecTileWords + tile) + t - s_tile0[tile], r);
   }
 }
 
@@ -661,24 +704,14 @@ int launch_anchor_flags(const PartitionArgs& a, uint32_t* bitmap, uint32_t* tile
   return MJ_OK;
 }
 
-int launch_anchor_emit(const PartitionArgs& a, const uint32_t* bitmap, const uint32_t* tile_offset,
-                       const uint32_t* tile_first, uint32_t* anchor_pos, uint32_t* anchor_sid, cudaStream_t s) {
+int launch_partition_records(const PartitionArgs& a, const uint32_t* bitmap, const uint32_t* tile_offset,
+                             const uint32_t* tile_first, uint64_t key_base, PRec* recs, cudaStream_t s) {
   const uint64_t tiles = partition_num_tiles(a.nbytes);
   if (tiles == 0) return MJ_OK;
-  anchor_emit_kernel<<<(unsigned)tiles, kThreads, 0, s>>>(a, bitmap, tile_offset, tile_first, anchor_pos,
-                                                            anchor_sid);
-  MJ_KERNEL_DONE();
-  return MJ_OK;
-}
-
-int launch_partition_records(const uint8_t* bytes, const int64_t* offsets, const uint32_t* anchor_pos,
-                             const uint32_t* anchor_sid, uint32_t n_anchor, uint64_t key_base, uint32_t* rec_sid,
-                             uint32_t* rec_pos, uint32_t* rec_len, uint32_t* rec_slen, uint64_t* rec_h61,
-                             cudaStream_t s) {
-  if (n_anchor == 0) return MJ_OK;
-  unsigned grid = (unsigned)std::min<uint64_t>((n_anchor + 255) / 256, (uint64_t)kNumSMsHint * 16);
-  partition_records_kernel<<<grid, kRecThreads, 0, s>>>(bytes, offsets, anchor_pos, anchor_sid, n_anchor, key_base,
-                                                rec_sid, rec_pos, rec_len, rec_slen, rec_h61);
+  const uint64_t nwords = tiles * kRecTileWords;
+  const uint64_t grid = (nwords + kRecWords - 1) / kRecWords;
+  partition_records_kernel<<<(unsigned)grid, kRecThreads, 0, s>>>(a, bitmap, nwords, tile_offset, tile_first,
+                                                                  key_base, recs);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }

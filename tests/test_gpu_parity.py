@@ -61,15 +61,17 @@ def test_partition_parity(ctx, name, factory):
     want = np.stack([parts.sid, parts.pos, parts.len], axis=1)
     assert got.shape == want.shape, (got.shape, want.shape)
     assert np.array_equal(got, want)
-    # equal partition substrings get equal keys, and (len, key) separates different ones
+    # (len, key) separates different partition substrings, and equal
+    # substrings (at any offset and alignment) get equal keys
     k = key.cpu().numpy()
-    seen = {}
+    seen, by_sub = {}, {}
     for t in range(0, got.shape[0], max(1, got.shape[0] // 4000)):
         sub = s.bytes[s.offsets[got[t, 0]] + got[t, 1]: s.offsets[got[t, 0]] + got[t, 1] + got[t, 2]].tobytes()
         kk = (int(got[t, 2]), int(k[t]))
         if kk in seen:
             assert seen[kk] == sub
         seen[kk] = sub
+        assert by_sub.setdefault(sub, kk) == kk
 
 
 def test_partition_worked_example(ctx):
