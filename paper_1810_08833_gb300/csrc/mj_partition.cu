@@ -531,20 +531,21 @@ __device__ __forceinline__ uint64_t addmod61(uint64_t a, uint64_t b) {
 // T7[b0] + T6[b1] + ... + T1[b6] + (b7+1) to h * base^8 (the leading len mod 8
 // bytes go first, one at a time or as one block of four).  The key equals the
 // byte-at-a-time polynomial.
-// A CTA takes kRecWords bitmap words (whole kPartTile tiles).  It lists their
-// anchors in shared memory (a block scan of the words' counts), then its
-// threads take one anchor at a time; an anchor's record goes to its tile's
-// list offset plus its rank within the tile.
+// A CTA takes chunks of kRecWords bitmap words (whole kPartTile tiles) in
+// turn, and builds its tables once.  For a chunk it lists the anchors in
+// shared memory (a block scan of the words' counts), then its threads take
+// one anchor at a time; an anchor's record goes to its tile's list offset
+// plus its rank within the tile.
 constexpr int kRecThreads = 256;
 constexpr int kRecWords = kRecThreads;                 // 8,192 positions: 4 tiles
 constexpr int kRecTileWords = kPartTile / 32;          // 64 words per tile
-constexpr int kRecStrings = 256;                       // string offsets cached per CTA
+constexpr int kRecStrings = 256;                       // string offsets cached per chunk
 
 __global__ void __launch_bounds__(kRecThreads) partition_records_kernel(
     PartitionArgs a, const uint32_t* __restrict__ bitmap, uint64_t nwords, const uint32_t* __restrict__ tile_offset,
     const uint32_t* __restrict__ tile_first, uint64_t key_base, PRec* __restrict__ recs) {
   __shared__ uint64_t s_t[7][256];                 // s_t[k - 1][c] = (c + 1) * base^k
-  __shared__ uint32_t s_anc[kRecWords * 32];       // anchor positions of the CTA, in order
+  __shared__ uint16_t s_anc[kRecWords * 32];       // anchor offsets in the chunk, in order
   __shared__ uint32_t s_off[kRecStrings + 1];     // offsets[sid0 .. sid0 + cap]
   __shared__ uint32_t s_warp[kRecThreads / 32];
   __shared__ uint32_t s_tile0[kRecWords / kRecTileWords];   // list index of each tile's first anchor
@@ -561,99 +562,116 @@ __global__ void __launch_bounds__(kRecThreads) partition_records_kernel(
     }
     b8 = bk;
   }
-  const uint64_t w0 = (uint64_t)blockIdx.x * kRecWords;
-  const uint64_t word = w0 + threadIdx.x;
-  const uint32_t bits = word < nwords ? __ldg(bitmap + word) : 0u;
-  const uint32_t sid0 = __ldg(tile_first + w0 / kRecTileWords);
-  const uint32_t cap = min((uint32_t)kRecStrings, a.n - sid0);
-  for (uint32_t t = threadIdx.x; t <= cap; t += kRecThreads) s_off[t] = (uint32_t)__ldg(a.offsets + sid0 + t);
-  // block exclusive scan of the anchor counts, then the anchor list
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t c = __popc(bits);
-  uint32_t x = c;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_warp[wid] = x;
-  __syncthreads();
-  uint32_t excl = x - c;
-  for (int w = 0; w < wid; ++w) excl += s_warp[w];
-  if (threadIdx.x % kRecTileWords == 0) s_tile0[threadIdx.x / kRecTileWords] = excl;
-  if (threadIdx.x == kRecThreads - 1) s_total = excl + c;
-  {
-    uint32_t f = bits, at = excl;
-    const uint32_t gw = (uint32_t)(word * 32);
-    while (f) {
-      s_anc[at++] = gw + (uint32_t)(__ffs(f) - 1);
-      f &= f - 1;
-    }
-  }
-  __syncthreads();
-  const uint32_t total = s_total;
-  const bool all_cached = sid0 + cap == a.n;
   const uint32_t nbytes = (uint32_t)a.nbytes;
-  for (uint32_t t = threadIdx.x; t < total; t += kRecThreads) {
-    const uint32_t g = s_anc[t];
-    // the string holding g
-    uint32_t k;
-    if (all_cached || s_off[cap] > g) {
-      uint32_t lo = 0, hi = cap;   // s_off[lo] <= g < s_off[hi]
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (s_off[mid] <= g) lo = mid; else hi = mid;
-      }
-      k = sid0 + lo;
-    } else {
-      k = string_of(a.offsets, a.n, g);
+  const uint64_t nchunks = (nwords + kRecWords - 1) / kRecWords;
+  for (uint64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const uint64_t w0 = chunk * kRecWords;
+    const uint32_t g0 = (uint32_t)(w0 * 32);
+    const uint64_t word = w0 + threadIdx.x;
+    const uint32_t bits = word < nwords ? __ldg(bitmap + word) : 0u;
+    const uint32_t sid0 = __ldg(tile_first + w0 / kRecTileWords);
+    const uint32_t cap = min((uint32_t)kRecStrings, a.n - sid0);
+    __syncthreads();   // the previous chunk's lists are no longer read
+    for (uint32_t t = threadIdx.x; t <= cap; t += kRecThreads) s_off[t] = (uint32_t)__ldg(a.offsets + sid0 + t);
+    // block exclusive scan of the anchor counts, then the anchor list
+    const uint32_t c = __popc(bits);
+    uint32_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
-    const uint32_t s_o = k - sid0 <= cap ? s_off[k - sid0] : (uint32_t)__ldg(a.offsets + k);
-    const uint32_t s_e = k + 1 - sid0 <= cap ? s_off[k + 1 - sid0] : (uint32_t)__ldg(a.offsets + k + 1);
-    // the next anchor: in the list, else in the words after the CTA's
-    uint32_t end = s_e;
-    if (t + 1 < total) {
-      end = s_anc[t + 1];
-    } else {
-      for (uint64_t ww = w0 + kRecWords; ww < nwords && ww * 32 < s_e; ++ww) {
-        const uint32_t y = __ldg(bitmap + ww);
-        if (y) {
-          end = (uint32_t)(ww * 32) + (uint32_t)(__ffs(y) - 1);
-          break;
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    uint32_t excl = x - c;
+    for (int w = 0; w < wid; ++w) excl += s_warp[w];
+    if (threadIdx.x % kRecTileWords == 0) s_tile0[threadIdx.x / kRecTileWords] = excl;
+    if (threadIdx.x == kRecThreads - 1) s_total = excl + c;
+    {
+      uint32_t f = bits, at = excl;
+      while (f) {
+        s_anc[at++] = (uint16_t)(32 * threadIdx.x + (__ffs(f) - 1));
+        f &= f - 1;
+      }
+    }
+    __syncthreads();
+    const uint32_t total = s_total;
+    const bool all_cached = sid0 + cap == a.n;
+    for (uint32_t t = threadIdx.x; t < total; t += kRecThreads) {
+      const uint32_t g = g0 + s_anc[t];
+      // the string holding g
+      uint32_t k;
+      if (all_cached || s_off[cap] > g) {
+        uint32_t lo = 0, hi = cap;   // s_off[lo] <= g < s_off[hi]
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (s_off[mid] <= g) lo = mid; else hi = mid;
+        }
+        k = sid0 + lo;
+      } else {
+        k = string_of(a.offsets, a.n, g);
+      }
+      const uint32_t s_o = k - sid0 <= cap ? s_off[k - sid0] : (uint32_t)__ldg(a.offsets + k);
+      const uint32_t s_e = k + 1 - sid0 <= cap ? s_off[k + 1 - sid0] : (uint32_t)__ldg(a.offsets + k + 1);
+      // the next anchor: in the list, else in the words after the chunk's
+      uint32_t end = s_e;
+      if (t + 1 < total) {
+        end = g0 + s_anc[t + 1];
+      } else {
+        for (uint64_t ww = w0 + kRecWords; ww < nwords && ww * 32 < s_e; ++ww) {
+          const uint32_t y = __ldg(bitmap + ww);
+          if (y) {
+            end = (uint32_t)(ww * 32) + (uint32_t)(__ffs(y) - 1);
+            break;
+          }
         }
       }
-    }
-    end = min(end, min(s_e, nbytes));
-    const uint8_t* p = a.bytes + g;
-    const uint32_t len = end - g;
-    const uint32_t head = len & 3u;
-    uint64_t h = 0;
-    for (uint32_t x2 = 0; x2 < head; ++x2) h = addmod61(mulmod61(h, key_base), (uint64_t)__ldg(p + x2) + 1);
-    uint32_t x2 = head;
-    if (len & 4u) {
-      const uint64_t u = s_t[2][__ldg(p + x2)] + s_t[1][__ldg(p + x2 + 1)] + s_t[0][__ldg(p + x2 + 2)] +
-                         (uint64_t)__ldg(p + x2 + 3) + 1;   // < 2^63
-      const uint64_t v = (u & kM61) + (u >> 61);
-      h = addmod61(mulmod61(h, b4), v >= kM61 ? v - kM61 : v);
-      x2 += 4;
-    }
-    for (; x2 < len; x2 += 8) {
-      uint64_t u = (uint64_t)__ldg(p + x2 + 7) + 1;   // seven terms < 2^61 and one < 2^9: < 2^64
+      end = min(end, min(s_e, nbytes));
+      const uint8_t* p = a.bytes + g;
+      const uint32_t len = end - g;
+      const uint32_t head = len & 3u;
+      uint64_t h = 0;
+      for (uint32_t x2 = 0; x2 < head; ++x2) h = addmod61(mulmod61(h, key_base), (uint64_t)__ldg(p + x2) + 1);
+      uint32_t x2 = head;
+      if (len & 4u) {
+        const uint64_t u = s_t[2][__ldg(p + x2)] + s_t[1][__ldg(p + x2 + 1)] + s_t[0][__ldg(p + x2 + 2)] +
+                           (uint64_t)__ldg(p + x2 + 3) + 1;   // < 2^63
+        const uint64_t v = (u & kM61) + (u >> 61);
+        h = addmod61(mulmod61(h, b4), v >= kM61 ? v - kM61 : v);
+        x2 += 4;
+      }
+      if (x2 < len) {
+        // blocks of eight, the next block's bytes loaded one step ahead
+        uint32_t nb[8];
 #pragma unroll
-      for (int e = 0; e < 7; ++e) u += s_t[6 - e][__ldg(p + x2 + e)];
-      const uint64_t v = (u & kM61) + (u >> 61);
-      h = addmod61(mulmod61(h, b8), v >= kM61 ? v - kM61 : v);
+        for (int e = 0; e < 8; ++e) nb[e] = __ldg(p + x2 + e);
+        for (;;) {
+          uint64_t u = (uint64_t)nb[7] + 1;   // seven terms < 2^61 and one < 2^9: < 2^64
+#pragma unroll
+          for (int e = 0; e < 7; ++e) u += s_t[6 - e][nb[e]];
+          x2 += 8;
+          const bool more = x2 < len;
+          if (more) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) nb[e] = __ldg(p + x2 + e);
+          }
+          const uint64_t v = (u & kM61) + (u >> 61);
+          h = addmod61(mulmod61(h, b8), v >= kM61 ? v - kM61 : v);
+          if (!more) break;
+        }
+      }
+      PRec r;
+      r.h61 = h;
+      r.run = 0;
+      r.slen = s_e - s_o;
+      r.len = len;
+      r.sid = k;
+      r.pos = g - s_o;
+      r.pad = 0;
+      const uint32_t tile = (uint32_t)(s_anc[t] / kPartTile);   // tile within the chunk
+      store_rec(recs, (uint64_t)__ldg(tile_offset + w0 / kRecTileWords + tile) + t - s_tile0[tile], r);
     }
-    PRec r;
-    r.h61 = h;
-    r.run = 0;
-    r.slen = s_e - s_o;
-    r.len = len;
-    r.sid = k;
-    r.pos = g - s_o;
-    r.pad = 0;
-    const uint32_t tile = g / kPartTile - (uint32_t)(w0 / kRecTileWords);   // tile within the CTA
-    store_rec(recs, (uint64_t)__ldg(tile_offset + w0 / kRecTileWords + tile) + t - s_tile0[tile], r);
   }
 }
 
@@ -709,7 +727,12 @@ int launch_partition_records(const PartitionArgs& a, const uint32_t* bitmap, con
   const uint64_t tiles = partition_num_tiles(a.nbytes);
   if (tiles == 0) return MJ_OK;
   const uint64_t nwords = tiles * kRecTileWords;
-  const uint64_t grid = (nwords + kRecWords - 1) / kRecWords;
+  int dev = 0, sms = 0, per_sm = 0;
+  MJ_CUDA_TRY(cudaGetDevice(&dev));
+  MJ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  MJ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, partition_records_kernel, kRecThreads, 0));
+  const uint64_t grid = std::min<uint64_t>((nwords + kRecWords - 1) / kRecWords,
+                                           (uint64_t)std::max(1, sms) * std::max(1, per_sm));
   partition_records_kernel<<<(unsigned)grid, kRecThreads, 0, s>>>(a, bitmap, nwords, tile_offset, tile_first,
                                                                   key_base, recs);
   MJ_KERNEL_DONE();
