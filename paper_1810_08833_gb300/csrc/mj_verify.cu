@@ -160,6 +160,18 @@ __device__ __forceinline__ bool pair_init(PairState<W, P>& st, const VerifyArgs&
     const uint32_t loMask = a0 >= 32 ? 0xffffffffu : ((1u << a0) - 1u);
     st.M1[w] = a1 > a0 ? (hiMask & ~loMask) : 0u;
   }
+  // the state is kept one row down, ready for the next column: the band's
+  // vectors (and the diagonal mask) shifted right by one bit, Pv's new bottom
+  // row +1
+#pragma unroll
+  for (int w = 0; w < W - 1; ++w) {
+    st.Pv[w] = __funnelshift_r(st.Pv[w], st.Pv[w + 1], 1);
+    st.Mv[w] = __funnelshift_r(st.Mv[w], st.Mv[w + 1], 1);
+    st.M1[w] = __funnelshift_r(st.M1[w], st.M1[w + 1], 1);
+  }
+  st.Pv[W - 1] = (st.Pv[W - 1] >> 1) | 0x80000000u;
+  st.Mv[W - 1] >>= 1;
+  st.M1[W - 1] >>= 1;
   st.score = -dlo;                       // D[dlo][0] = -dlo
   st.abit = (uint64_t)(oA + dlo + 32 * (int64_t)GW);   // plane bit of row 1 + dlo (column 1)
   st.bpos = (uint64_t)(oB + 32 * (int64_t)GW);
@@ -294,14 +306,7 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
 #pragma unroll
     for (int w = 0; w < W; ++w) Eq[w] = __funnelshift_r(EqF[w], EqF[w + 1], (uint32_t)c);
 
-    // band slides down one row: the new bottom row gets a +1 vertical delta
-#pragma unroll
-    for (int w = 0; w < W - 1; ++w) {
-      st.Pv[w] = __funnelshift_r(st.Pv[w], st.Pv[w + 1], 1);
-      st.Mv[w] = __funnelshift_r(st.Mv[w], st.Mv[w + 1], 1);
-    }
-    st.Pv[W - 1] = (st.Pv[W - 1] >> 1) | 0x80000000u;
-    st.Mv[W - 1] = st.Mv[W - 1] >> 1;
+    // the band has slid down one row already (the vectors are kept shifted)
     const int32_t sv = (int32_t)(st.Pv[0] & 1u) - (int32_t)(st.Mv[0] & 1u);
 
     uint32_t Xv[W], Ph[W], Mh[W], EP[W], SUM[W];
@@ -316,23 +321,24 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
       Mh[w] = st.Pv[w] & Xh;
     }
     st.score += sv + (int32_t)(Ph[0] & 1u) - (int32_t)(Mh[0] & 1u);
-#pragma unroll
-    for (int w = W - 1; w > 0; --w) {
-      Ph[w] = __funnelshift_l(Ph[w - 1], Ph[w], 1);
-      Mh[w] = __funnelshift_l(Mh[w - 1], Mh[w], 1);
-    }
-    Ph[0] = Ph[0] * 2u + 1u;
-    Mh[0] = Mh[0] * 2u;
+    // Myers' update Pv' = (Mh << 1) | ~(Xv | (Ph << 1) | 1), Mv' = ((Ph << 1) | 1)
+    // & Xv, followed by the next column's slide (>> 1, Pv's new bottom row +1),
+    // is Pv = Mh | ~((Xv >> 1) | Ph) | top, Mv = Ph & (Xv >> 1): one shift
+    // instead of four per word.
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-      st.Pv[w] = Mh[w] | ~(Xv[w] | Ph[w]);
-      st.Mv[w] = Ph[w] & Xv[w];
+      const uint32_t xs = w + 1 < W ? __funnelshift_r(Xv[w], Xv[w + 1], 1) : Xv[w] >> 1;
+      st.Pv[w] = Mh[w] | ~(xs | Ph[w]);
+      st.Mv[w] = Ph[w] & xs;
     }
+    st.Pv[W - 1] |= 0x80000000u;
   }
   const int32_t jend = j0 + cnt - 1;
   st.j = jend + 1;
   st.bpos += (uint64_t)cnt;
-  // D on diagonal d0 at column jend: a lower bound of D[m][n] (exact at n)
+  // D on diagonal d0 at column jend: a lower bound of D[m][n] (exact at n);
+  // M1 (kept shifted like the vectors) selects the rows below the top row
+  // down to diagonal d0
   int32_t diag = st.score;
 #pragma unroll
   for (int w = 0; w < W; ++w) diag += (int32_t)__popc(st.Pv[w] & st.M1[w]) - (int32_t)__popc(st.Mv[w] & st.M1[w]);
