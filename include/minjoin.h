@@ -110,7 +110,15 @@ typedef struct {
  *  flags   MJ_FLAG_KEY_CHECK: check every group of equal partition keys for
  *          byte equality (mismatches counted in mj_stats.key_collisions);
  *          MJ_FLAG_FEATURES: keep the candidates' band features;
- *          MJ_FLAG_FIRST_PASS: run the learned first passes however few pairs they hold. */
+ *          MJ_FLAG_FIRST_PASS: run the learned first passes however few pairs they hold.
+ *  repeats parallel repetition (Sec. 2.2, Thm 1): R = 1..64 independent random
+ *          functions Pi_0 .. Pi_{R-1}; every string is partitioned under each,
+ *          and the join matches the union of the R partition sets.  Pi_k has
+ *          the seed  seed + k * 0x9E3779B97F4A7C15  (mod 2^64); the partition
+ *          key keeps the base seed, so equal substrings get equal keys under
+ *          every Pi_k.  Partition records come repetition by repetition, each
+ *          in position order.  1 (the default) is the plain method; an
+ *          explicit Pi table allows only 1.  Other values: MJ_ERR_ARG. */
 typedef struct {
   uint32_t K;
   uint32_t T;
@@ -119,6 +127,7 @@ typedef struct {
   uint64_t seed;
   uint32_t verify_mode;
   uint32_t flags;
+  uint32_t repeats;
 } mj_params;
 
 /* Parameters as derived for an input (Sec. 2.2, Alg. 2). */

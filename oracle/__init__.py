@@ -8,6 +8,12 @@ benchmark may import this package; the product path never does.
 Threading: partitioning (per string) and verification (per pair) are split
 into chunks run on a thread pool; ctypes releases the GIL during each call.
 The hash join of Alg. 3 runs sequentially, as in the paper.
+
+Parallel repetition (Sec. 2.2, Thm 1) is the union of the partitions made
+under R independent random functions Pi; `partition_repeated` builds it from
+R calls of `partition`.  It is pinned by properties, not by printed values:
+R = 1 is the plain partition, every repetition tiles every string, and the
+candidates and the recall never shrink as R grows.
 """
 from __future__ import annotations
 
@@ -231,6 +237,28 @@ def partition(data: np.ndarray, offsets: np.ndarray, p: Params, table: np.ndarra
                       np.concatenate([r[2] for r in res]), np.concatenate([r[3] for r in res]))
 
 
+REPETITION_STEP = 0x9E3779B97F4A7C15   # Weyl step between the seeds of repeated Pi functions
+
+
+def repetition_seed(seed: int, k: int) -> int:
+    """Seed of Pi_k under parallel repetition: seed + k * 0x9E3779B97F4A7C15
+    modulo 2^64 (k = 0 is the base seed; the partition key keeps it)."""
+    return (seed + k * REPETITION_STEP) % (1 << 64)
+
+
+def partition_repeated(data: np.ndarray, offsets: np.ndarray, p: Params, repeats: int,
+                       threads: int | None = None) -> Partitions:
+    """Sec. 2.2's parallel repetition: the union of the partitions of every
+    string under Pi_0 .. Pi_{R-1}, ordered by string, then repetition, then
+    position.  n_anchor sums the anchors of the R partitionings."""
+    parts = [partition(data, offsets, dataclasses.replace(p, seed=repetition_seed(p.seed, k)), threads=threads)
+             for k in range(repeats)]
+    sid = np.concatenate([q.sid for q in parts])
+    order = np.argsort(sid, kind="stable")
+    return Partitions(sid[order], np.concatenate([q.pos for q in parts])[order],
+                      np.concatenate([q.len for q in parts])[order], sum(q.n_anchor for q in parts))
+
+
 # ---------------------------------------------------------------- join
 
 def candidates(data: np.ndarray, offsets: np.ndarray, K: int, parts: Partitions) -> np.ndarray:
@@ -303,14 +331,21 @@ class JoinResult:
 
 
 def minjoin(data: np.ndarray, offsets: np.ndarray, K: int, T: int = 0, q: int = 0, r_min: int = 1,
-            seed: int = 0x5EED, table: np.ndarray | None = None, threads: int | None = None) -> JoinResult:
-    """Alg. 3 end to end: partition every string (Alg. 1-2), hash join with
-    the length and position filters, dedup, then verify every candidate with
+            seed: int = 0x5EED, table: np.ndarray | None = None, threads: int | None = None,
+            repeats: int = 1) -> JoinResult:
+    """Alg. 3 end to end: partition every string (Alg. 1-2; with repeats > 1
+    the union under independent Pi functions, Sec. 2.2), hash join with the
+    length and position filters, dedup, then verify every candidate with
     Ukkonen's banded DP and keep the pairs with ED <= K."""
     data = _u8(data)
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
     p = derive_params(data, offsets, K, T, q, r_min, seed)
-    parts = partition(data, offsets, p, table=table, threads=threads)
+    if repeats > 1:
+        if table is not None:
+            raise ValueError("an explicit Pi table allows no repetition")
+        parts = partition_repeated(data, offsets, p, repeats, threads=threads)
+    else:
+        parts = partition(data, offsets, p, table=table, threads=threads)
     C = candidates(data, offsets, K, parts)
     ed = ed_band_pairs(data, offsets, C, K, threads=threads)
     keep = ed <= K

@@ -36,7 +36,7 @@ class MinJoinError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_uint32), ("T", ctypes.c_uint32), ("q", ctypes.c_uint32),
                 ("r_min", ctypes.c_int32), ("seed", ctypes.c_uint64), ("verify_mode", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("repeats", ctypes.c_uint32)]
 
 
 class Derived(ctypes.Structure):
@@ -154,10 +154,11 @@ def _check(status: int, where: str):
 
 
 def params(K: int, T: int = 0, q: int = 0, r_min: int = 1, seed: int = 0x5EED,
-           verify_mode: int = MJ_VERIFY_PLAIN, flags: int = 0) -> Params:
+           verify_mode: int = MJ_VERIFY_PLAIN, flags: int = 0, repeats: int = 1) -> Params:
     p = Params()
     library().mj_params_default(ctypes.byref(p), K)
     p.T, p.q, p.r_min, p.seed, p.verify_mode, p.flags = T, q, r_min, seed, verify_mode, flags
+    p.repeats = repeats
     return p
 
 

@@ -45,6 +45,29 @@ int Buf::reserve(size_t need, cudaStream_t s) {
   return MJ_OK;
 }
 
+int Buf::grow_keep(size_t need, size_t keep, cudaStream_t s) {
+  if (need <= bytes && p) return MJ_OK;
+  void* old = p;
+  const size_t old_bytes = bytes;
+  const size_t alloc = need < 256 ? 256 : need + need / 8;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, alloc);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return MJ_ERR_OOM;
+  }
+  if (old) {
+    const size_t n = keep < old_bytes ? keep : old_bytes;
+    if (n) MJ_CUDA_TRY(cudaMemcpyAsync(q, old, n, cudaMemcpyDeviceToDevice, s));
+    // the old buffer may still be read by queued work on `s`
+    MJ_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaFree(old);
+  }
+  p = q;
+  bytes = alloc;
+  return MJ_OK;
+}
+
 void Buf::release() {
   if (p) cudaFree(p);
   p = nullptr;
@@ -198,6 +221,7 @@ int check_inputs(const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, c
     // an all-empty input may pass a null byte pointer; it is checked later
   }
   if (p->K > (1u << 20) || p->r_min < 0) return MJ_ERR_ARG;
+  if (p->repeats < 1 || p->repeats > 64) return MJ_ERR_ARG;
   return MJ_OK;
 }
 
@@ -241,6 +265,7 @@ int derive(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t
   d.r_min = p->r_min;
   d.r_max = radius_rule((int64_t)d.N, d.q, d.T, d.r_min);
   d.seed = p->seed;
+  d.repeats = p->repeats;
   c->stats.n_strings = n;
   c->stats.n_bytes = nbytes;
   return MJ_OK;
@@ -251,7 +276,7 @@ uint64_t key_base_for(uint64_t seed) {
   return 257 + splitmix(seed ^ 0x6b6579626173650aull) % (M61 - 1024);
 }
 
-// a2-a4 (after derive): records in c->rec_*.
+// a2-a4 (after derive): partition records in c->recs (n_part of them).
 // plane_kmax > 0: also write the verifier's bit-planes (guard sized for bands
 // up to plane_kmax).
 int partition(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const uint64_t* d_table,
@@ -300,31 +325,45 @@ int partition(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
       MJ_CUDA_TRY(cudaMemsetAsync(planes + from, 0, words * 4, s));
     }
   }
-  tstart(c, 0, s);
-  MJ_TRY(launch_anchor_flags(a, c->bitmap.as<uint32_t>(), c->tile_count.as<uint32_t>(),
-                             c->dev_flags.as<uint32_t>(), planes, PW, GW, c->tile_first.as<uint32_t>(), s));
-  tstop(c, 0, s);
-  if (planes) {
-    c->planes_ready = true;
-    c->planes_pw = PW;
-    c->planes_gw = GW;
+  // parallel repetition (Sec. 2.2): Pi_k has the seed d.seed + k * 0x9E3779B97F4A7C15;
+  // the records of repetition k follow those of repetitions 0 .. k-1
+  const uint32_t R = d.repeats;
+  if (d_table && R > 1) return MJ_ERR_ARG;
+  uint64_t n_total = 0;
+  for (uint32_t k = 0; k < R; ++k) {
+    const uint64_t seed_k = d.seed + (uint64_t)k * 0x9E3779B97F4A7C15ull;
+    a.seed32 = (uint32_t)seed_k ^ (uint32_t)(seed_k >> 32);
+    a.seed64 = seed_k;
+    tstart(c, 0, s);
+    MJ_TRY(launch_anchor_flags(a, c->bitmap.as<uint32_t>(), c->tile_count.as<uint32_t>(),
+                               c->dev_flags.as<uint32_t>(), k == 0 ? planes : nullptr, PW, GW,
+                               c->tile_first.as<uint32_t>(), s));
+    tstop(c, 0, s);
+    if (planes && k == 0) {
+      c->planes_ready = true;
+      c->planes_pw = PW;
+      c->planes_gw = GW;
+    }
+    uint32_t* total = c->tile_off.as<uint32_t>() + tiles;
+    MJ_TRY(launch_exclusive_scan_u32(c->tile_count.as<uint32_t>(), c->tile_off.as<uint32_t>(), tiles,
+                                     c->scan_tmp.p, total, s));
+    MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small, total, 4, cudaMemcpyDeviceToHost, s));
+    MJ_CUDA_TRY(cudaMemcpyAsync((char*)c->h_small + 8, c->dev_flags.p, 4, cudaMemcpyDeviceToHost, s));
+    MJ_CUDA_TRY(cudaStreamSynchronize(s));
+    const uint32_t n_anchor = *(uint32_t*)c->h_small;
+    c->stats.device_flags |= *(uint32_t*)((char*)c->h_small + 8);
+    if (c->stats.device_flags) return MJ_ERR_DEVICE;
+    if (n_total + n_anchor >= (1ull << 32)) return MJ_ERR_UNSUPPORTED;   // record indexes are 32-bit
+    MJ_TRY(c->recs.grow_keep((n_total + n_anchor + 1) * sizeof(PRec), n_total * sizeof(PRec), s));
+    tstart(c, 1, s);
+    MJ_TRY(launch_partition_records(a, c->bitmap.as<uint32_t>(), c->tile_off.as<uint32_t>(),
+                                    c->tile_first.as<uint32_t>(), key_base_for(d.seed),
+                                    c->recs.as<PRec>() + n_total, s));
+    tstop(c, 1, s);
+    n_total += n_anchor;
   }
-  uint32_t* total = c->tile_off.as<uint32_t>() + tiles;
-  MJ_TRY(launch_exclusive_scan_u32(c->tile_count.as<uint32_t>(), c->tile_off.as<uint32_t>(), tiles,
-                                   c->scan_tmp.p, total, s));
-  MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small, total, 4, cudaMemcpyDeviceToHost, s));
-  MJ_CUDA_TRY(cudaMemcpyAsync((char*)c->h_small + 8, c->dev_flags.p, 4, cudaMemcpyDeviceToHost, s));
-  MJ_CUDA_TRY(cudaStreamSynchronize(s));
-  const uint32_t n_anchor = *(uint32_t*)c->h_small;
-  c->stats.device_flags |= *(uint32_t*)((char*)c->h_small + 8);
-  if (c->stats.device_flags) return MJ_ERR_DEVICE;
-  MJ_TRY(c->recs.reserve((size_t)n_anchor * sizeof(PRec) + sizeof(PRec), s));
-  tstart(c, 1, s);
-  MJ_TRY(launch_partition_records(a, c->bitmap.as<uint32_t>(), c->tile_off.as<uint32_t>(),
-                                  c->tile_first.as<uint32_t>(), key_base_for(d.seed), c->recs.as<PRec>(), s));
-  tstop(c, 1, s);
-  c->n_part = n_anchor;
-  c->stats.n_partitions = n_anchor;
+  c->n_part = n_total;
+  c->stats.n_partitions = n_total;
   return MJ_OK;
 }
 
@@ -728,6 +767,7 @@ void mj_params_default(mj_params* p, uint32_t K) {
   p->seed = 0x5EED;
   p->verify_mode = MJ_VERIFY_PLAIN;
   p->flags = 0;
+  p->repeats = 1;
 }
 
 const char* mj_strerror(int status) {
@@ -924,12 +964,12 @@ int mj_verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
     // one band for every pair: longest first, with the context's kernel plan
     if (m) MJ_TRY(verify_ordered_graph(c, d_bytes, d_offsets, d_i, d_j, m, K, d_ed, s));
   } else {
-    // the widest per-pair band sizes the kernel
-    std::vector<uint32_t> hk(m);
-    MJ_CUDA_TRY(cudaMemcpyAsync(hk.data(), d_k, m * 4, cudaMemcpyDeviceToHost, s));
-    MJ_CUDA_TRY(cudaStreamSynchronize(s));
-    uint32_t kmax = 0;
-    for (uint32_t v : hk) kmax = std::max(kmax, v);
+    // the widest per-pair band sizes the kernel (a device reduction, 4 bytes read back)
+    MJ_TRY(c->small.reserve(64, s));
+    unsigned int* dmax = reinterpret_cast<unsigned int*>(c->small.as<unsigned long long>() + 6);
+    MJ_TRY(launch_max_u32(d_k, m, dmax, s));
+    MJ_TRY(readback(c, dmax, 4, s));
+    const uint32_t kmax = *(uint32_t*)c->h_small;
     MJ_TRY(verify(c, d_bytes, d_offsets, d_i, d_j, d_k, m, K, kmax, d_ed, true, s));
   }
   c->stats.n_launches = launch_count() - c->launches_at_start;

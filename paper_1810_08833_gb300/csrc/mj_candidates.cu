@@ -52,6 +52,14 @@ __global__ void max_len_kernel(const int64_t* __restrict__ off, uint32_t n, unsi
   if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
 }
 
+__global__ void max_u32_kernel(const uint32_t* __restrict__ v, uint64_t n, unsigned int* __restrict__ out) {
+  uint32_t m = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    m = max(m, v[i]);
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 __device__ __forceinline__ uint64_t mix64(uint64_t k) {  // MurmurHash3 fmix64
   k ^= k >> 33;
   k *= 0xff51afd7ed558ccdull;
@@ -61,7 +69,7 @@ __device__ __forceinline__ uint64_t mix64(uint64_t k) {  // MurmurHash3 fmix64
   return k;
 }
 
-// Group key: 32 hash bits of (len, key) above slen_bits bits of string length.
+// Group key: hash bits of (len, key) above slen_bits bits of string length.
 __global__ void group_keys_kernel(const PRec* __restrict__ recs, uint32_t n, int slen_bits, int hash_bits,
                                   uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
@@ -210,23 +218,15 @@ __global__ void multiplicity_kernel(const uint32_t* __restrict__ run_start, uint
   }
 }
 
-// parts[s] = number of anchors (= partitions) of string s: the anchor list
-// is in string order, so it is the width of s's run, found by two binary
-// searches per string
-// First record of string >= v among n records in string order.
-__device__ __forceinline__ uint64_t first_rec_of(const PRec* __restrict__ r, uint64_t n, uint32_t v) {
-  uint64_t lo = 0, hi = n;
-  while (lo < hi) {
-    const uint64_t mid = (lo + hi) >> 1;
-    if (__ldg(&r[mid].sid) < v) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
+// parts[s] = number of partitions of string s, counted over all records
+// (with parallel repetition the records come repetition by repetition, so
+// they are counted, not searched)
 __global__ void partition_counts_kernel(const PRec* __restrict__ recs, uint64_t n_rec, uint32_t n,
                                         uint32_t* __restrict__ parts) {
-  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (uint64_t)gridDim.x * blockDim.x)
-    parts[s] = (uint32_t)(first_rec_of(recs, n_rec, (uint32_t)s + 1) - first_rec_of(recs, n_rec, (uint32_t)s));
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_rec; t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t sid = __ldg(&recs[t].sid);
+    if (sid < n) atomicAdd(parts + sid, 1u);
+  }
 }
 
 // First-pass bucket of a learned band k (0: no first pass).  Band widths
@@ -344,6 +344,14 @@ int launch_byte_histogram(const uint8_t* bytes, uint64_t nbytes, unsigned long l
   return MJ_OK;
 }
 
+int launch_max_u32(const uint32_t* v, uint64_t n, unsigned int* out, cudaStream_t s) {
+  MJ_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(unsigned int), s));
+  if (!n) return MJ_OK;
+  max_u32_kernel<<<grid_for(n), 256, 0, s>>>(v, n, out);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
 int launch_max_length(const int64_t* offsets, uint32_t n, unsigned long long* out, cudaStream_t s) {
   MJ_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(unsigned long long), s));
   if (!n) return MJ_OK;
@@ -444,7 +452,9 @@ int launch_multiplicity(const uint32_t* run_start, uint64_t nc, uint64_t raw, ui
 
 int launch_partition_counts(const PRec* recs, uint64_t n_rec, uint32_t n, uint32_t* parts, cudaStream_t s) {
   if (!n) return MJ_OK;
-  partition_counts_kernel<<<grid_for(n), 256, 0, s>>>(recs, n_rec, n, parts);
+  MJ_CUDA_TRY(cudaMemsetAsync(parts, 0, (size_t)n * sizeof(uint32_t), s));
+  if (!n_rec) return MJ_OK;
+  partition_counts_kernel<<<grid_for(n_rec), 256, 0, s>>>(recs, n_rec, n, parts);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }

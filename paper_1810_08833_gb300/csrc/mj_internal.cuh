@@ -55,6 +55,8 @@ struct Buf {
   void* p = nullptr;
   size_t bytes = 0;
   int reserve(size_t need, cudaStream_t s);
+  // as reserve, but the first `keep` bytes survive a reallocation
+  int grow_keep(size_t need, size_t keep, cudaStream_t s);
   template <class T>
   T* as() const { return static_cast<T*>(p); }
   void release();
@@ -65,6 +67,7 @@ struct Derived {
   uint32_t sigma = 0, bits = 1, q = 1, T = 1, K = 0;
   int32_t r_min = 1, r_max = 0;
   uint64_t N = 0, seed = 0;
+  uint32_t repeats = 1;   // parallel repetition: independent Pi functions
   uint8_t rank[256] = {0};
 };
 
@@ -75,6 +78,8 @@ struct Derived {
 int launch_byte_histogram(const uint8_t* bytes, uint64_t nbytes, unsigned long long* hist,
                           cudaStream_t s);
 int launch_max_length(const int64_t* offsets, uint32_t n, unsigned long long* out, cudaStream_t s);
+// *out = max of v[0 .. n-1] (0 when n = 0)
+int launch_max_u32(const uint32_t* v, uint64_t n, unsigned int* out, cudaStream_t s);
 
 // A partition record, packed in two 16-byte words: Karp-Rabin key, group
 // run (the hash bits of the grouping sort key; 0 until the records are put
@@ -247,7 +252,7 @@ int launch_band_rule(const float* yhat, const uint32_t* ci, const uint32_t* cj, 
                      uint32_t K, uint32_t margin, uint32_t* kband, cudaStream_t s);
 
 // multiplicity of every candidate from the run starts written by the pair
-// compaction; partitions per string from the records (in string order)
+// compaction; partitions per string counted over the records
 int launch_multiplicity(const uint32_t* run_start, uint64_t nc, uint64_t raw, uint32_t* mult, cudaStream_t s);
 int launch_partition_counts(const PRec* recs, uint64_t n_rec, uint32_t n, uint32_t* parts, cudaStream_t s);
 // Learned first passes: the pairs of every first-pass bucket b = 1 .. nb

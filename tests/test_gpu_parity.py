@@ -155,6 +155,41 @@ def test_join_parity(ctx, name, factory):
     assert st["band_cells"] == cells
 
 
+REPEAT_SETS = [x for x in SETS if x[0] in ("config1", "config4_400roots", "random_mixed", "edge")]
+
+
+@pytest.mark.parametrize("name,factory", REPEAT_SETS, ids=[n for n, _ in REPEAT_SETS])
+def test_repetition_parity(ctx, name, factory):
+    """Parallel repetition (Sec. 2.2): the partitions under R seeds equal the
+    oracle's union, and the join over that union equals the oracle's."""
+    import paper_1810_08833_gb300 as mj
+    s, p = get_set(name, factory)
+    data, off = to_device(s)
+    want = oracle.partition_repeated(s.bytes, s.offsets, p, 3)
+    sid, pos, ln, _ = ctx.partition(data, off, mj.params(s.K, T=s.T, repeats=3))
+    got = np.stack([t.cpu().numpy().astype(np.int64) for t in (sid, pos, ln)], axis=1)
+    w = np.stack([want.sid, want.pos, want.len], axis=1)
+    got, w = got[np.lexsort(got.T[::-1])], w[np.lexsort(w.T[::-1])]
+    assert got.shape == w.shape and np.array_equal(got, w)
+    ref = oracle.minjoin(s.bytes, s.offsets, K=s.K, T=s.T, repeats=2)
+    ctx.band_init(seed=5)   # any network gives the plain output
+    for mode in (mj.MJ_VERIFY_PLAIN, mj.MJ_VERIFY_LEARNED):
+        oi, oj, oe = ctx.join(data, off, mj.params(s.K, T=s.T, repeats=2, verify_mode=mode))
+        res = np.stack([t.cpu().numpy() for t in (oi, oj, oe)], axis=1).astype(np.int64)
+        assert np.array_equal(res, np.concatenate([ref.pairs, ref.ed[:, None]], axis=1))
+        st = ctx.stats()
+        assert st["n_candidates"] == ref.candidates.shape[0] and st["device_flags"] == 0
+
+
+def test_repetition_rejects_bad_counts(ctx):
+    import paper_1810_08833_gb300 as mj
+    s = synth.make_config(1, n_roots=2)
+    data, off = to_device(s)
+    for r in (0, 65):
+        with pytest.raises(mj.MinJoinError):
+            ctx.join(data, off, mj.params(s.K, T=s.T, repeats=r))
+
+
 def test_join_host_matches_device(ctx):
     import paper_1810_08833_gb300 as mj
     s, p = get_set("config1", SETS[0][1])
