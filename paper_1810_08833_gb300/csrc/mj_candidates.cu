@@ -221,11 +221,18 @@ __global__ void multiplicity_kernel(const uint32_t* __restrict__ run_start, uint
 // parts[s] = number of partitions of string s, counted over all records
 // (with parallel repetition the records come repetition by repetition, so
 // they are counted, not searched)
+// Records of one string are mostly consecutive, so the lanes of a warp that
+// hold the same string add their count in one atomic (from the lowest lane).
 __global__ void partition_counts_kernel(const PRec* __restrict__ recs, uint64_t n_rec, uint32_t n,
                                         uint32_t* __restrict__ parts) {
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_rec; t += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t sid = __ldg(&recs[t].sid);
-    if (sid < n) atomicAdd(parts + sid, 1u);
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) - lane;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t base = warp0; base < n_rec; base += stride) {   // warp-uniform
+    const uint64_t t = base + lane;
+    const uint32_t sid = t < n_rec ? __ldg(&recs[t].sid) : 0xffffffffu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, sid);
+    if (sid < n && lane == __ffs(peers) - 1) atomicAdd(parts + sid, (uint32_t)__popc(peers));
   }
 }
 
