@@ -156,8 +156,8 @@ typedef struct {
   float ms_derive, ms_partition, ms_join_filter, ms_verify, ms_total;
   uint64_t n_launches;         /* kernels the library launched during the call */
   /* device time (CUDA events on the call's stream) of the sections of the
-   * last mj_join, in this order: 0 anchor test (Alg. 2), 1 anchor list and
-   * partition records (Alg. 1), 2 record grouping sort, 3 pair emission
+   * last mj_join, in this order: 0 anchor test (Alg. 2), 1 partition
+   * records from the anchors (Alg. 1), 2 record grouping sort, 3 pair emission
    * (filters of Alg. 3), 4 pair dedup, 5 equality bit-planes, 6 verification
    * kernel(s), 7 output compaction */
   float ms_section[8];
@@ -188,7 +188,8 @@ int mj_derive(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_offsets, uin
               const mj_params* p, void* stream, mj_derived* out);
 
 /* Steps a2-a4 (Alg. 1-2): partitions of every string.  *count receives the
- * number of partitions; mj_partition_copy writes them in string order, each
+ * number of partitions; mj_partition_copy writes them in string order (with
+ * p->repeats = R > 1: repetition by repetition, each in string order), each
  * (sid, pos, len, key) with key the 64-bit partition-substring hash
  * (Alg. 3's partition hash f).  `d_qgram_table` (nullable) replaces Pi by a table of
  * 2^(q*bits) 64-bit values indexed by the packed rank code of a q-gram (first

@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(kRecThreads) partition_records_kernel(
     const uint32_t cap = min((uint32_t)kRecStrings, a.n - sid0);
     __syncthreads();   // the previous chunk's lists are no longer read
     for (uint32_t t = threadIdx.x; t <= cap; t += kRecThreads) s_off[t] = (uint32_t)__ldg(a.offsets + sid0 + t);
-    // block exclusive scan of the anchor counts, then the anchor list
+    // block exclusive scan of the anchor counts, then the chunk's anchor list
     const uint32_t c = __popc(bits);
     uint32_t x = c;
 #pragma unroll
