@@ -190,12 +190,16 @@ def test_repetition_rejects_bad_counts(ctx):
             ctx.join(data, off, mj.params(s.K, T=s.T, repeats=r))
 
 
-def test_join_host_matches_device(ctx):
+@pytest.mark.parametrize("which", ["config1", "config2_400roots"])
+def test_join_host_matches_device(ctx, which):
+    """Host buffers in (a small input, and config 2 with 400 families, 20 MB)
+    give the device join's output."""
     import paper_1810_08833_gb300 as mj
-    s, p = get_set("config1", SETS[0][1])
+    s = get_set("config1", SETS[0][1])[0] if which == "config1" else synth.make_config(2, n_roots=400)
     data, off = to_device(s)
     oi, oj, oe = ctx.join(data, off, mj.params(s.K, T=s.T))
     hi, hj, he = ctx.join_host(s.bytes, s.offsets, mj.params(s.K, T=s.T))
+    assert oi.numel() > 0
     assert np.array_equal(hi, oi.cpu().numpy().astype(np.uint32))
     assert np.array_equal(hj, oj.cpu().numpy().astype(np.uint32))
     assert np.array_equal(he, oe.cpu().numpy().astype(np.uint32))
