@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t
 // D of its bottom row; the bottom row of the block holding row m at column n
 // gives D[m][n], and the block holding row j + d0 at column j gives the
 // diagonal lower bound used for the early exit.
-constexpr int kWaveSteps = 16;   // wavefront steps between refills and votes (unrolled)
+constexpr int kWaveSteps = 32;   // wavefront steps between refills and votes (<= 32: B's bits per reload)
 
 // Each lane publishes one word per wavefront step for the lane holding the
 // next block of rows:
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(128, P <= 2 ? 8 : 1) verify_wave_kernel(Verify
     // outside its block's steps computes on stale state (rebuilt at the
     // block's first column) that no other lane reads.  First and last
     // columns and the diagonal test take one rarely divergent branch.
-#pragma unroll
+#pragma unroll 8   // a quarter of the steps: a smaller loop body is fetched better (measured)
     for (int it = 0; it < kWaveSteps; ++it) {
       const uint32_t w_in = __shfl_sync(0xffffffffu, pub, prev_lane);
       ++u;
