@@ -47,7 +47,11 @@ RECORD_BYTES = 24            # one partition record written: sid, pos, len, stri
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current
 # kernel, keyed by (section, workload number); absent (reported as null)
 # where no capture of the current kernel exists
-TRAFFIC_BYTES = {}
+# Read-length DNA: verify_diag_kernel<4, 2> (32-column chunks, loop unrolled
+# by 8) captured on 3,000 of the 5,000 families (32.1 MB per launch), scaled
+# by the candidates (x 1.666) to the full workload: the bit-planes and pair
+# arrays it reads grow with them.
+TRAFFIC_BYTES = {("verify_kernel", 2): 53.5e6}
 
 
 def band_cells(m: np.ndarray, n: np.ndarray, K: int) -> int:
