@@ -54,6 +54,26 @@ RECORD_BYTES = 24            # one partition record written: sid, pos, len, stri
 TRAFFIC_BYTES = {("verify_kernel", 2): 53.5e6}
 
 
+def replica_seed(cfg: int, rank: int) -> int:
+    """Seed of the workload instance rank `rank` joins: the workload's own on
+    rank 0, a distinct one on every other rank (weak scaling)."""
+    return cfg if rank == 0 else cfg + 7919 * rank
+
+
+def reduce_over_ranks(times_ms: list, cells: int, device) -> tuple:
+    """The job's step times (max over ranks, element-wise) and its work (sum
+    of the ranks' cells); the identity with one process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(x) for x in times_ms], float(cells)
+    t = torch.tensor([float(x) for x in times_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(cells)], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t.tolist()], float(c[0])
+
+
 def band_cells(m: np.ndarray, n: np.ndarray, K: int) -> int:
     """K-band cells of pairs with lengths m >= n: sum over j = 1..n of
     min(m, j+K) - max(1, j-K) + 1, in closed form."""
@@ -205,7 +225,7 @@ def run_native(args):
     import synth
 
     cfg = args.config
-    seed = cfg if rank == 0 else cfg + 7919 * rank
+    seed = replica_seed(cfg, rank)
     s = synth.make_config(cfg, seed=seed)
     data = torch.from_numpy(s.bytes).to(dev)
     off = torch.from_numpy(s.offsets).to(dev)
@@ -306,15 +326,7 @@ def run_native(args):
     sec_ms = {k: statistics.median([st["ms_section"][k] for st in stats]) for k in mj.SECTIONS}
     launches = int(sum(st["n_launches"] for st in stats))
 
-    if world > 1:
-        t = torch.tensor([ms, ms_e2e, ms_plain], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e, ms_plain = float(t[0]), float(t[1]), float(t[2])
-        c = torch.tensor([cells], dtype=torch.float64, device=dev)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        cells_all = float(c[0])
-    else:
-        cells_all = float(cells)
+    (ms, ms_e2e, ms_plain), cells_all = reduce_over_ranks([ms, ms_e2e, ms_plain], cells, dev)
 
     if rank == 0:
         peaks = measured_peaks()
