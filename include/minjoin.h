@@ -187,7 +187,11 @@ int mj_autotune_verify(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_off
 int mj_derive(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n,
               const mj_params* p, void* stream, mj_derived* out);
 
-/* Steps a2-a4 (Alg. 1-2): partitions of every string.  *count receives the
+/* Steps a2-a4 (Alg. 1-2): partitions of every string.  The anchor test holds
+ * a 4,096-position tile and halos of r_max positions in shared memory, so
+ * r_max is limited to about 7,400 (32-bit Pi values; about 2,600 when Pi is
+ * 64-bit, q * bits > 32, or given as a table); beyond, this and mj_join
+ * return MJ_ERR_UNSUPPORTED.  *count receives the
  * number of partitions; mj_partition_copy writes them in string order (with
  * p->repeats = R > 1: repetition by repetition, each in string order), each
  * (sid, pos, len, key) with key the 64-bit partition-substring hash
