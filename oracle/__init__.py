@@ -74,6 +74,11 @@ def _bind(path: str):
     lib.mjo_ed_band_pairs.restype = None
     lib.mjo_ed_band_pairs.argtypes = [U8P, I64P, I64P, ctypes.c_int64, ctypes.c_int64,
                                       ctypes.c_int64, I64P]
+    lib.mjo_ed_band_cutoff.restype = ctypes.c_int64
+    lib.mjo_ed_band_cutoff.argtypes = [U8P, ctypes.c_int64, U8P, ctypes.c_int64, ctypes.c_int64]
+    lib.mjo_ed_band_cutoff_pairs.restype = None
+    lib.mjo_ed_band_cutoff_pairs.argtypes = [U8P, I64P, I64P, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_int64, I64P]
     return lib
 
 
@@ -297,9 +302,18 @@ def ed_band(a: bytes, b: bytes, k: int) -> int:
                                _p(y, U8P) if y.shape[0] else None, y.shape[0], k))
 
 
+def ed_band_cutoff(a: bytes, b: bytes, k: int) -> int:
+    """ed_band with Ukkonen's cut-off (stops once a whole band row exceeds k)."""
+    lib = _load()
+    x, y = _u8(a), _u8(b)
+    return int(lib.mjo_ed_band_cutoff(_p(x, U8P) if x.shape[0] else None, x.shape[0],
+                                      _p(y, U8P) if y.shape[0] else None, y.shape[0], k))
+
+
 def ed_band_pairs(data: np.ndarray, offsets: np.ndarray, pairs: np.ndarray, k: int,
-                  threads: int | None = None) -> np.ndarray:
-    """min(ED, k+1) of every pair (banded DP), chunked over threads."""
+                  threads: int | None = None, cutoff: bool = False) -> np.ndarray:
+    """min(ED, k+1) of every pair (banded DP), chunked over threads; with
+    cutoff=True each DP stops once a whole band row exceeds k (same values)."""
     lib = _load()
     data = _u8(data)
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
@@ -312,8 +326,10 @@ def ed_band_pairs(data: np.ndarray, offsets: np.ndarray, pairs: np.ndarray, k: i
     bounds = np.unique(np.linspace(0, m, num=min(m, threads * 16) + 1).astype(np.int64))
     dp = _p(data, U8P) if data.shape[0] else None
 
+    fn = lib.mjo_ed_band_cutoff_pairs if cutoff else lib.mjo_ed_band_pairs
+
     def run(a, b):
-        lib.mjo_ed_band_pairs(dp, _p(offsets, I64P), _p(pairs, I64P), a, b, k, _p(out, I64P))
+        fn(dp, _p(offsets, I64P), _p(pairs, I64P), a, b, k, _p(out, I64P))
 
     with ThreadPoolExecutor(max_workers=threads) as ex:
         list(ex.map(lambda ab: run(*ab), zip(bounds[:-1], bounds[1:])))

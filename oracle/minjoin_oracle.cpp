@@ -292,6 +292,40 @@ int64_t mjo_ed_band(const uint8_t* a, int64_t m, const uint8_t* b, int64_t n, in
     return std::min(prev[n], INF);
 }
 
+// mjo_ed_band with the cut-off of Ukkonen's method (Sec. 3 names Ukkonen's
+// algorithm for the verification): the dynamic program stops as soon as every
+// band cell of a row exceeds k and returns k + 1.  That is exact: each cell of
+// row i is reached from a cell of row i - 1 (diagonal or vertical step) or
+// from a cell of row i to its left, and no step lowers the cost, so the
+// smallest band value of a row never falls below that of the row above, and
+// the final cell (m, n) can no longer be within k.  Otherwise the same
+// recurrence, boundary and band as mjo_ed_band.
+int64_t mjo_ed_band_cutoff(const uint8_t* a, int64_t m, const uint8_t* b, int64_t n, int64_t k) {
+    if (iabs(m - n) > k) return k + 1;
+    const int64_t INF = k + 1;
+    std::vector<int64_t> prev(n + 1, INF), cur(n + 1, INF);
+    for (int64_t j = 0; j <= std::min(n, k); ++j) prev[j] = j;
+    for (int64_t i = 1; i <= m; ++i) {
+        int64_t jlo = std::max<int64_t>(0, i - k), jhi = std::min(n, i + k);
+        int64_t row_min = INF;
+        for (int64_t j = jlo; j <= jhi; ++j) {
+            int64_t v = INF;
+            if (j == 0) {
+                v = i;
+            } else {
+                v = prev[j - 1] + (a[i - 1] != b[j - 1] ? 1 : 0);
+                if (iabs((i - 1) - j) <= k) v = std::min(v, prev[j] + 1);
+                if (j - 1 >= jlo) v = std::min(v, cur[j - 1] + 1);
+            }
+            cur[j] = std::min(v, INF);
+            row_min = std::min(row_min, cur[j]);
+        }
+        if (row_min > k) return k + 1;
+        std::swap(prev, cur);
+    }
+    return std::min(prev[n], INF);
+}
+
 // mjo_ed_band over pairs [lo, hi) of a pair list (pairs[2t], pairs[2t+1]).
 void mjo_ed_band_pairs(const uint8_t* bytes, const int64_t* offsets, const int64_t* pairs,
                        int64_t lo, int64_t hi, int64_t k, int64_t* out) {
@@ -299,6 +333,16 @@ void mjo_ed_band_pairs(const uint8_t* bytes, const int64_t* offsets, const int64
         int64_t x = pairs[2 * t], y = pairs[2 * t + 1];
         out[t] = mjo_ed_band(bytes + offsets[x], offsets[x + 1] - offsets[x], bytes + offsets[y],
                              offsets[y + 1] - offsets[y], k);
+    }
+}
+
+// mjo_ed_band_cutoff over pairs [lo, hi) of a pair list, as mjo_ed_band_pairs.
+void mjo_ed_band_cutoff_pairs(const uint8_t* bytes, const int64_t* offsets, const int64_t* pairs,
+                              int64_t lo, int64_t hi, int64_t k, int64_t* out) {
+    for (int64_t t = lo; t < hi; ++t) {
+        int64_t x = pairs[2 * t], y = pairs[2 * t + 1];
+        out[t] = mjo_ed_band_cutoff(bytes + offsets[x], offsets[x + 1] - offsets[x], bytes + offsets[y],
+                                    offsets[y + 1] - offsets[y], k);
     }
 }
 

@@ -8,8 +8,10 @@ Linear(64, 64) -> ReLU -> Linear(64, 1).  Parameters are one flat vector in
 the order W1[64][8], b1[64], W2[64][64], b2[64], W3[64], b3.  Loss: mean
 squared error (tau == 0) or the pinball loss at quantile tau.
 
-Pinned by central finite differences of `loss` (tests/test_oracle_mlp.py),
-which share nothing with the explicit backpropagation below.
+Pinned by a hand-worked network (outputs, both losses and gradient entries
+computed by hand, with the parameter layout checked one weight per block) and
+by central finite differences of `loss`, which share nothing with the explicit
+backpropagation below (tests/mlp_pins.py, tests/test_oracle_mlp.py).
 """
 import numpy as np
 

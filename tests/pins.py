@@ -70,6 +70,31 @@ def pin_ed_textbook():
             assert oracle.ed_band(a, b, k) == (d if d <= k else k + 1), (a, b, k)
 
 
+def pin_ed_band_cutoff(seed: int = 17):
+    """The banded DP with Ukkonen's cut-off returns min(ED, k + 1): against
+    the breadth-first-search distances of all strings of length <= 5 over
+    {A, C}, against the textbook cases, and against the full DP on planted
+    pairs of DNA at several bands."""
+    strings, dist = bfs_distances(b"AC", 5)
+    for i, a in enumerate(strings):
+        for j, b in enumerate(strings):
+            d = int(dist[i, j])
+            for k in (0, 1, 2, 3):
+                assert oracle.ed_band_cutoff(a, b, k) == min(d, k + 1), (a, b, k, d)
+    for a, b, d in load_ed_cases():
+        for k in range(0, d + 3):
+            assert oracle.ed_band_cutoff(a, b, k) == min(d, k + 1), (a, b, k)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    for _ in range(40):
+        L = int(rng.integers(30, 160))
+        a = synth.DNA[rng.integers(0, 4, size=L)]
+        b = synth.mutate(rng, a, float(rng.uniform(0.02, 0.3)), synth.DNA)
+        d = oracle.ed_full(a.tobytes(), b.tobytes())
+        for k in (0, d // 2, d - 1, d, d + 1, 2 * d + 3):
+            if k >= 0:
+                assert oracle.ed_band_cutoff(a.tobytes(), b.tobytes(), k) == min(d, k + 1), (d, k)
+
+
 def bfs_distances(alphabet: bytes, maxlen: int) -> tuple[list[bytes], np.ndarray]:
     """Edit distance between all strings of length <= maxlen over `alphabet`,
     by breadth-first search over single insertions, deletions and
@@ -297,6 +322,33 @@ def pin_candidates_definition(seed: int = 21):
         seed += 1
 
 
+def pin_join_eviction_order():
+    """Alg. 3 visits the strings in length order, which is what makes its
+    eviction (an entry whose string length differs from the probing string's
+    by more than K leaves the bucket for good) lose no pair.  Hand-worked case
+    with q = 1 and Pi(A) = 1 < Pi(D) = 4, T = 10, K = 6:
+      x = DDDDA + D*15 (|x| = 20, r = max(floor(10/22), 1) = 1)
+      y = DDDDA + D*95 (|y| = 100, r = floor(90/22) = 4)
+      z = DDDDA + D*16 (|z| = 21, r = 1)
+    In each string the only interior anchor is the A at position 4 (runs of
+    D tie), so each starts with the partition DDDD at position 0.  x and z
+    pass both filters (|20 - 21| = 1 <= 6); y is 80 longer than x.  In length
+    order (x, z, y) the pair (x, z) is found; in id order y would evict x
+    before z probes.  The only candidate is (0, 2)."""
+    strings = [b"DDDDA" + b"D" * 15, b"DDDDA" + b"D" * 95, b"DDDDA" + b"D" * 16]
+    s = synth.from_strings(strings, K=6, T=10)
+    p = oracle.derive_params(s.bytes, s.offsets, K=6, T=10, q=1)
+    tab = np.zeros(1 << p.bits, dtype=np.uint64)
+    tab[p.rank[ord("A")]] = 1
+    tab[p.rank[ord("D")]] = 4
+    parts = oracle.partition(s.bytes, s.offsets, p, table=tab, threads=1)
+    for sid, st in enumerate(strings):
+        sel = parts.sid == sid
+        assert parts.pos[sel].tolist() == [0, 4] and parts.len[sel].tolist() == [4, len(st) - 4], sid
+    C = oracle.candidates(s.bytes, s.offsets, 6, parts)
+    assert [tuple(x) for x in C.tolist()] == [(0, 2)], C
+
+
 def pin_join_precision(seed: int = 31):
     """MinJoin never outputs a false positive (Sec. 3): the output is a subset
     of the brute-force all-pairs truth, with the true edit distances."""
@@ -319,11 +371,13 @@ ALL_PINS = [
     ("ed_textbook", pin_ed_textbook),
     ("ed_bfs", pin_ed_bfs),
     ("ed_planted", pin_ed_planted),
+    ("ed_band_cutoff", pin_ed_band_cutoff),
     ("q_rule", pin_q_rule),
     ("radius", pin_radius),
     ("anchor_shape", pin_anchor_shape),
     ("anchor_edges", pin_anchor_edges),
     ("hash_injective", pin_hash_is_injective),
     ("candidates_definition", pin_candidates_definition),
+    ("join_eviction_order", pin_join_eviction_order),
     ("join_precision", pin_join_precision),
 ]

@@ -40,6 +40,12 @@ MUTANTS = [
      "for (int64_t j = 0; j <= std::min(n, k); ++j) prev[j] = 0;"),
     ("band_edge", "if (iabs(m - n) > k) return k + 1;", "if (iabs(m - n) >= k) return k + 1;"),
     ("q_rule_boundary", "while (p * t3 < n3) {", "while (p * t3 <= n3) {"),
+    ("cutoff_at_k", "if (row_min > k) return k + 1;", "if (row_min >= k) return k + 1;"),
+    ("cutoff_row_min_first_cell", "row_min = std::min(row_min, cur[j]);", "row_min = cur[jlo];"),
+    ("eviction_of_unpaired_entries",
+     "C.emplace_back(std::min(i, e.j), std::max(i, e.j));\n                    kept.push_back(e);",
+     "{ C.emplace_back(std::min(i, e.j), std::max(i, e.j)); kept.push_back(e); }"),
+    ("join_in_id_order", "for (int64_t i : order) {", "for (int64_t i = 0; i < n; ++i) {"),
 ]
 
 
