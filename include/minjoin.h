@@ -48,6 +48,16 @@ extern "C" {
 #define MJ_FLAG_FIRST_PASS 32u   /* learned mode: run the first passes however few pairs they hold (by default
                                     they run only with at least 384 pairs per SM, below which their latency
                                     exceeds what they save, and every pair goes to band K) */
+/* Deduplication of the candidate pairs (last step of Alg. 3's join).  By
+ * default the library picks per call: a bitmap with one bit per pair i < j
+ * (n^2/16 bytes, cleared, set by every raw pair, then compacted row by row
+ * into the sorted list) when sweeping it costs less than sorting the raw
+ * pairs and it fits in device memory, else a radix sort of the raw pairs.
+ * Learned mode and MJ_FLAG_FEATURES always sort (they need each candidate's
+ * multiplicity).  Both give the same candidate set. */
+#define MJ_FLAG_DEDUP_SORT 64u     /* always sort the raw pairs */
+#define MJ_FLAG_DEDUP_BITMAP 128u  /* use the pair bitmap whenever multiplicities are not needed (an allocation
+                                      failure is then MJ_ERR_OOM) */
 
 /* verification modes (mj_params.verify_mode) */
 #define MJ_VERIFY_PLAIN 0        /* one pass with band K */
@@ -110,7 +120,8 @@ typedef struct {
  *  flags   MJ_FLAG_KEY_CHECK: check every group of equal partition keys for
  *          byte equality (mismatches counted in mj_stats.key_collisions);
  *          MJ_FLAG_FEATURES: keep the candidates' band features;
- *          MJ_FLAG_FIRST_PASS: run the learned first passes however few pairs they hold.
+ *          MJ_FLAG_FIRST_PASS: run the learned first passes however few pairs they hold;
+ *          MJ_FLAG_DEDUP_SORT / MJ_FLAG_DEDUP_BITMAP: how candidates are deduplicated.
  *  repeats parallel repetition (Sec. 2.2, Thm 1): R = 1..64 independent random
  *          functions Pi_0 .. Pi_{R-1}; every string is partitioned under each,
  *          and the join matches the union of the R partition sets.  Pi_k has

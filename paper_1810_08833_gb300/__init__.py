@@ -53,6 +53,8 @@ class BandTrainParams(ctypes.Structure):
 MJ_FLAG_KEY_CHECK = 1
 MJ_FLAG_FEATURES = 16
 MJ_FLAG_FIRST_PASS = 32
+MJ_FLAG_DEDUP_SORT = 64
+MJ_FLAG_DEDUP_BITMAP = 128
 BAND_FEATURES = 8
 BAND_PARAMS = 4801
 

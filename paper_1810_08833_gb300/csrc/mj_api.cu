@@ -129,6 +129,7 @@ struct mj_ctx {
   Buf srec;   // partition records in group order (PRec)
   Buf pair_count, pair_off, pairs, pairs_alt;
   Buf uflags, uoffs, cand_i, cand_j;
+  Buf pairbm;  // pair bitmap of the candidate dedup (bit per pair i < j)
   Buf planes, ed, eflags, eoffs;
   Buf out_i, out_j, out_ed;
   Buf in_bytes, in_offsets;  // staging for mj_join_host
@@ -376,30 +377,41 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   c->stats.n_raw_pairs = 0;
   c->stats.key_collisions = 0;
   if (nr == 0) return MJ_OK;
-  const int slen_bits = bits_for(d.N);
-  // Group runs only need to separate most (len, key) classes: the pair walk
-  // compares len and key itself.  So the hash takes the bits that fill whole
-  // 8-bit radix passes above the length, at least 24 and at most 32.
-  const int sort_passes = (24 + slen_bits + 7) / 8;
-  const int hash_bits = std::min(32, 8 * sort_passes - slen_bits);
+  // Group key shape: the hash bits fill whole 8-bit radix passes above the
+  // position bucket and the string length, at least 24 and at most 32 (runs
+  // only need to separate most (len, key) classes: the pair walk compares
+  // len and key itself).  The bucket width W is K, or wider when the
+  // position and length bits would leave fewer than 24 hash bits.
+  GroupKeyShape g;
+  g.slen_bits = bits_for(d.N);
+  const int pb_room = std::max(0, 40 - g.slen_bits);
+  g.W = std::max<uint32_t>(d.K, 1u);
+  if (pb_room == 0) {
+    g.pb_bits = 0;
+  } else {
+    if (bits_for(d.N / g.W) > pb_room) g.W = (uint32_t)std::min<uint64_t>((d.N >> pb_room) + 1, 0xffffffffull);
+    g.pb_bits = bits_for(d.N / g.W);
+  }
+  const int low_bits = g.pb_bits + g.slen_bits;
+  const int sort_passes = (24 + low_bits + 7) / 8;
+  g.hash_bits = std::min(32, 8 * sort_passes - low_bits);
   MJ_TRY(c->keys.reserve((size_t)nr * 8, s));
   MJ_TRY(c->keys_alt.reserve((size_t)nr * 8, s));
   MJ_TRY(c->idx.reserve((size_t)nr * 4, s));
   MJ_TRY(c->idx_alt.reserve((size_t)nr * 4, s));
   MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(nr), s));
   tstart(c, 2, s);
-  MJ_TRY(launch_make_group_keys(c->recs.as<PRec>(), nr, slen_bits, hash_bits, c->keys.as<uint64_t>(),
-                                c->idx.as<uint32_t>(), s));
+  MJ_TRY(launch_make_group_keys(c->recs.as<PRec>(), nr, g, c->keys.as<uint64_t>(), c->idx.as<uint32_t>(), s));
   bool alt = false;
   MJ_TRY(radix_sort_u64(c->keys.as<uint64_t>(), c->keys_alt.as<uint64_t>(), c->idx.as<uint32_t>(),
-                        c->idx_alt.as<uint32_t>(), nr, 0, hash_bits + slen_bits, c->sort_tmp.p, &alt, s));
+                        c->idx_alt.as<uint32_t>(), nr, 0, g.hash_bits + low_bits, c->sort_tmp.p, &alt, s));
   const uint64_t* skeys = alt ? c->keys_alt.as<uint64_t>() : c->keys.as<uint64_t>();
   const uint32_t* sidx = alt ? c->idx_alt.as<uint32_t>() : c->idx.as<uint32_t>();
   MJ_TRY(c->srec.reserve((size_t)nr * sizeof(PRec), s));
   const PRec* r = c->srec.as<PRec>();
-  MJ_TRY(launch_gather_records(sidx, skeys, nr, slen_bits, c->recs.as<PRec>(), c->srec.as<PRec>(), s));
+  MJ_TRY(launch_gather_records(sidx, skeys, nr, g, c->recs.as<PRec>(), c->srec.as<PRec>(), s));
   tstop(c, 2, s);
-  if (flags & 1u) {
+  if (flags & MJ_FLAG_KEY_CHECK) {
     MJ_TRY(c->small.reserve(64, s));
     MJ_CUDA_TRY(cudaMemsetAsync(c->small.p, 0, 8, s));
     MJ_TRY(launch_key_check(r, d_bytes, d_offsets, nr, c->small.as<unsigned long long>(), s));
@@ -410,7 +422,7 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   MJ_TRY(c->pair_off.reserve((size_t)nr * 8 + 16, s));
   MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(nr), s));
   tstart(c, 3, s);
-  MJ_TRY(launch_count_pairs(r, nr, d.K, c->pair_count.as<uint32_t>(), s));
+  MJ_TRY(launch_count_pairs(r, nr, d.K, g, c->pair_count.as<uint32_t>(), s));
   uint64_t* total = c->pair_off.as<uint64_t>() + nr;
   MJ_TRY(launch_exclusive_scan_u32_to_u64(c->pair_count.as<uint32_t>(), c->pair_off.as<uint64_t>(), nr,
                                           c->scan_tmp.p, total, s));
@@ -420,11 +432,50 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   c->stats.n_raw_pairs = raw;
   if (raw == 0) return MJ_OK;
   if (raw >= (1ull << 32)) return MJ_ERR_UNSUPPORTED;
+  // Dedup by the pair bitmap when its sweep (clear, count, write: three
+  // passes over n^2/16 bytes) costs less than sorting the raw pairs (about
+  // 80 bytes of traffic per pair over the radix passes), unless the
+  // candidates' multiplicities are wanted (only the sort gives them) or a
+  // flag forces one way.
+  const uint64_t bm_bytes = pair_bitmap_words(n) * 4;
+  bool use_bitmap = !want_run_start && bm_bytes > 0 && !(flags & MJ_FLAG_DEDUP_SORT) &&
+                    ((flags & MJ_FLAG_DEDUP_BITMAP) || (bm_bytes <= raw * 80 && bm_bytes <= (48ull << 30)));
+  if (use_bitmap) {
+    const int st = c->pairbm.reserve(bm_bytes, s);
+    if (st == MJ_ERR_OOM && !(flags & MJ_FLAG_DEDUP_BITMAP)) {
+      use_bitmap = false;   // not enough device memory: sort instead
+    } else if (st != MJ_OK) {
+      return st;
+    }
+  }
+  if (use_bitmap) {
+    tstart(c, 4, s);
+    MJ_TRY(c->small.reserve(64, s));
+    MJ_TRY(launch_mark_pairs(r, nr, d.K, g, n, c->pairbm.as<uint32_t>(), c->small.as<unsigned long long>() + 7, s));
+    MJ_TRY(c->uflags.reserve((size_t)n * 4, s));
+    MJ_TRY(c->uoffs.reserve((size_t)n * 4 + 16, s));
+    MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(n), s));
+    MJ_TRY(launch_bitmap_rows(c->pairbm.as<uint32_t>(), n, c->uflags.as<uint32_t>(), s));
+    uint32_t* ctotal = c->uoffs.as<uint32_t>() + n;
+    MJ_TRY(launch_exclusive_scan_u32(c->uflags.as<uint32_t>(), c->uoffs.as<uint32_t>(), n, c->scan_tmp.p, ctotal, s));
+    MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small + 1, c->small.as<unsigned long long>() + 7, 8, cudaMemcpyDeviceToHost, s));
+    MJ_TRY(readback(c, ctotal, 4, s));
+    const uint32_t nc = *(uint32_t*)c->h_small;
+    if (c->h_small[1] != raw) return MJ_ERR_DEVICE;   // both walks must see the same pairs
+    MJ_TRY(c->cand_i.reserve((size_t)nc * 4 + 16, s));
+    MJ_TRY(c->cand_j.reserve((size_t)nc * 4 + 16, s));
+    MJ_TRY(launch_bitmap_write(c->pairbm.as<uint32_t>(), n, c->uoffs.as<uint32_t>(), c->cand_i.as<uint32_t>(),
+                               c->cand_j.as<uint32_t>(), s));
+    tstop(c, 4, s);
+    c->n_cand = nc;
+    c->stats.n_candidates = nc;
+    return MJ_OK;
+  }
   MJ_TRY(c->pairs.reserve(raw * 8, s));
   MJ_TRY(c->pairs_alt.reserve(raw * 8, s));
   tstart(c, 4, s);
   const int nb = bits_for(n ? n - 1 : 0);   // pair (i, j) packed as i << nb | j
-  MJ_TRY(launch_fill_pairs(r, nr, d.K, nb, c->pair_off.as<uint64_t>(), c->pairs.as<uint64_t>(), s));
+  MJ_TRY(launch_fill_pairs(r, nr, d.K, g, nb, c->pair_off.as<uint64_t>(), c->pairs.as<uint64_t>(), s));
   MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(raw), s));
   MJ_TRY(radix_sort_u64(c->pairs.as<uint64_t>(), c->pairs_alt.as<uint64_t>(), nullptr, nullptr, raw, 0, 2 * nb,
                         c->sort_tmp.p, &alt, s));
@@ -839,7 +890,7 @@ void mj_destroy(mj_ctx* c) {
   Buf* bufs[] = {&c->hist, &c->dev_flags, &c->small, &c->bitmap, &c->tile_count, &c->tile_off, &c->scan_tmp,
                  &c->tile_first,
                  &c->recs, &c->keys, &c->keys_alt, &c->idx, &c->idx_alt, &c->sort_tmp, &c->srec, &c->pair_count, &c->pair_off, &c->pairs, &c->pairs_alt,
-                 &c->uflags, &c->uoffs, &c->cand_i, &c->cand_j, &c->planes, &c->ed, &c->eflags, &c->eoffs,
+                 &c->uflags, &c->uoffs, &c->cand_i, &c->cand_j, &c->pairbm, &c->planes, &c->ed, &c->eflags, &c->eoffs,
                  &c->out_i, &c->out_j, &c->out_ed, &c->in_bytes, &c->in_offsets, &c->branges,
                  &c->band, &c->feat_x, &c->mult, &c->run_start, &c->parts, &c->yhat, &c->kband, &c->lvals,
                  &c->franges, &c->fnext, &c->fcnt, &c->ed_first};

@@ -5,12 +5,24 @@
 // The paper's sequential hash join visits strings in length order and evicts
 // bucket entries whose length differs by more than K.  Its result is the set
 // of pairs (i != j) holding byte-identical partitions that pass both filters.
-// Here that set is produced by sorting the partition records by a group key
-// (a hash of (len, substring key) in the high bits, the string length in the
-// low bits), so equal partitions are adjacent and ordered by string length
-// within the run; every record then walks forward through its run while the
-// length difference stays <= K, testing the exact (len, key) equality, i != j,
-// and the position filter.  Count -> scan -> fill.
+// Here that set is produced by sorting the partition records by a group key:
+// a hash of (len, substring key) in the high bits, then the partition's
+// position bucket (position / W with W >= K), then the string length.  Equal
+// partitions are adjacent; inside a run they are ordered by position bucket
+// and, within a bucket, by string length.  The position filter implies
+// |pos_x - pos_y| <= K, so a partner lies in the same bucket or the next one;
+// every record walks forward through its own bucket while the length
+// difference stays <= K, then through the length window [slen - K, slen + K]
+// of the next bucket (found by a galloping search), testing the exact
+// (len, key) equality, i != j and the position filter.  Frequent partitions
+// (a common word in text) make runs of 10^5 records; the position buckets cut
+// each walk to the records that can pass both filters.
+//
+// Deduplication: either the raw pairs are written (count -> scan -> fill),
+// radix-sorted and made unique (which also gives every candidate's
+// multiplicity), or every pair sets its bit in a triangular bitmap over all
+// pairs i < j, whose rows are then counted and compacted into the sorted
+// candidate list.
 #include "mj_internal.cuh"
 
 namespace mj {
@@ -69,22 +81,29 @@ __device__ __forceinline__ uint64_t mix64(uint64_t k) {  // MurmurHash3 fmix64
   return k;
 }
 
-// Group key: hash bits of (len, key) above slen_bits bits of string length.
-__global__ void group_keys_kernel(const PRec* __restrict__ recs, uint32_t n, int slen_bits, int hash_bits,
-                                  uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+// Group key: hash bits of (len, key), then pb_bits bits of position bucket
+// (pos / W), then slen_bits bits of string length.
+__global__ void group_keys_kernel(const PRec* __restrict__ recs, uint32_t n, int slen_bits, int pb_bits, uint32_t W,
+                                  int hash_bits, uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+  const uint32_t pb_max = pb_bits ? (1u << pb_bits) - 1u : 0u;
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
     const PRec r = load_rec(recs, t);
     uint64_t g = mix64(r.h61 ^ ((uint64_t)r.len * 0x9e3779b97f4a7c15ull));
-    keys[t] = ((g >> (64 - hash_bits)) << slen_bits) | (uint64_t)r.slen;
+    const uint32_t pb = min(r.pos / W, pb_max);
+    keys[t] = (((g >> (64 - hash_bits)) << pb_bits | pb) << slen_bits) | (uint64_t)r.slen;
     idx[t] = (uint32_t)t;
   }
 }
 
+// Records in group order; run = the hash bits, pad = the position bucket.
 __global__ void gather_kernel(const uint32_t* __restrict__ idx, const uint64_t* __restrict__ keys, uint32_t n,
-                              int slen_bits, const PRec* __restrict__ recs, PRec* __restrict__ o) {
+                              int slen_bits, int pb_bits, const PRec* __restrict__ recs, PRec* __restrict__ o) {
+  const uint64_t pb_mask = pb_bits ? (1ull << pb_bits) - 1ull : 0ull;
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
     PRec r = load_rec(recs, idx[t]);
-    r.run = (uint32_t)(keys[t] >> slen_bits);
+    const uint64_t k = keys[t];
+    r.run = (uint32_t)(k >> (slen_bits + pb_bits));
+    r.pad = (uint32_t)((k >> slen_bits) & pb_mask);
     store_rec(o, t, r);
   }
 }
@@ -101,32 +120,154 @@ __global__ void unpack_records_kernel(const PRec* __restrict__ recs, uint64_t n,
   }
 }
 
-// Walks the run of record t; EMIT=false counts, EMIT=true writes pairs.
-template <bool EMIT>
-__global__ void pairs_kernel(const PRec* __restrict__ r, uint32_t n, uint32_t K, int nb, uint32_t* __restrict__ count,
-                             const uint64_t* __restrict__ offs, uint64_t* __restrict__ pairs) {
+// Sort key of a record in group order (the key group_keys_kernel made).
+__device__ __forceinline__ uint64_t rec_key(const PRec& o, int pb_shift, int run_shift) {
+  return ((uint64_t)o.run << run_shift) | ((uint64_t)o.pad << pb_shift) | (uint64_t)o.slen;
+}
+
+// First index u >= lo (u < n) whose sort key is >= target, n if none:
+// galloping steps from lo, then a binary search.
+__device__ uint64_t key_lower_bound(const PRec* __restrict__ r, uint64_t lo, uint64_t n, uint64_t target, int pb_shift,
+                                    int run_shift) {
+  uint64_t a = lo, b = lo, step = 1;
+  while (b < n && rec_key(load_rec(r, b), pb_shift, run_shift) < target) {
+    a = b + 1;
+    b = a + step;
+    step <<= 1;
+  }
+  if (b > n) b = n;
+  while (a < b) {   // every index < a is below target; b is n or at/above it
+    const uint64_t mid = a + (b - a) / 2;
+    if (rec_key(load_rec(r, mid), pb_shift, run_shift) < target) a = mid + 1;
+    else b = mid;
+  }
+  return a;
+}
+
+enum : int { WALK_COUNT = 0, WALK_FILL = 1, WALK_MARK = 2 };
+
+__device__ __forceinline__ uint64_t tri_words(uint64_t x) {   // sum over y = 1 .. x of ceil(y / 32)
+  const uint64_t k = x >> 5, r = x & 31u;
+  return 16u * k * (k + 1) + r * (k + 1);
+}
+
+// Word offset of row a of the pair bitmap over n strings: row a holds the
+// pairs (a, b), a < b < n, as bits b - a - 1 in ceil((n - 1 - a) / 32) words.
+__device__ __forceinline__ uint64_t bitmap_row(uint64_t a, uint64_t n) {
+  return tri_words(n - 1) - tri_words(n - 1 - a);
+}
+
+// Walks the pairs of record t (see the file comment).  WALK_COUNT: count[t]
+// = pairs found; WALK_FILL: writes them packed (i << nb | j, i < j) from
+// offs[t]; WALK_MARK: sets their bits in the pair bitmap and adds their number
+// to *raw_total.
+template <int MODE>
+__global__ void walk_kernel(const PRec* __restrict__ r, uint32_t n, uint32_t K, int pb_shift, int run_shift, int nb,
+                            uint32_t* __restrict__ count, const uint64_t* __restrict__ offs,
+                            uint64_t* __restrict__ pairs, uint32_t* __restrict__ bm, uint32_t n_str,
+                            unsigned long long* __restrict__ raw_total) {
+  unsigned long long raw = 0;
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
     const PRec me = load_rec(r, t);
     const int32_t pos = (int32_t)me.pos, slen = (int32_t)me.slen;
     uint32_t c = 0;
-    uint64_t out = EMIT ? offs[t] : 0;
-    for (uint64_t u = t + 1; u < n; ++u) {
-      const PRec o = load_rec(r, u);
-      if (o.run != me.run) break;
-      if ((int32_t)o.slen - slen > (int32_t)K) break;      // length filter (run sorted by length)
-      if (o.len != me.len || o.h61 != me.h61) continue;    // same partition substring
-      if (o.sid == me.sid) continue;                       // i != j
+    uint64_t out = MODE == WALK_FILL ? offs[t] : 0;
+    auto visit = [&](const PRec& o) {
+      if (o.len != me.len || o.h61 != me.h61) return;    // same partition substring
+      if (o.sid == me.sid) return;                       // i != j
       const int32_t pos_u = (int32_t)o.pos;
       const int32_t dl = pos - pos_u, dr = (slen - pos) - ((int32_t)o.slen - pos_u);
-      if (abs(dl) + abs(dr) > (int32_t)K) continue;       // position filter
-      if (EMIT) {
-        const uint32_t a = me.sid < o.sid ? me.sid : o.sid, b = me.sid < o.sid ? o.sid : me.sid;
+      if (abs(dl) + abs(dr) > (int32_t)K) return;       // position filter
+      ++c;
+      const uint32_t a = me.sid < o.sid ? me.sid : o.sid, b = me.sid < o.sid ? o.sid : me.sid;
+      if (MODE == WALK_FILL) {
         pairs[out++] = ((uint64_t)a << nb) | b;
-      } else {
-        ++c;
+      } else if (MODE == WALK_MARK) {
+        const uint64_t bit = (uint64_t)(b - a - 1);
+        atomicOr(bm + bitmap_row(a, n_str) + (bit >> 5), 1u << (bit & 31u));
+      }
+    };
+    // this bucket: later records with string length up to slen + K (the
+    // length filter; lengths ascend within a bucket)
+    uint64_t u = t + 1;
+    bool next = false;
+    while (u < n) {
+      const PRec o = load_rec(r, u);
+      if (o.run != me.run) break;
+      if (o.pad != me.pad) {
+        next = o.pad == me.pad + 1;
+        break;
+      }
+      if ((int32_t)o.slen - slen > (int32_t)K) {
+        next = true;
+        ++u;
+        break;
+      }
+      visit(o);
+      ++u;
+    }
+    // the next bucket: string lengths in [slen - K, slen + K]
+    if (next) {
+      const uint32_t lo_len = me.slen > K ? me.slen - K : 0u;
+      const uint64_t target = ((uint64_t)me.run << run_shift) | ((uint64_t)(me.pad + 1) << pb_shift) | lo_len;
+      u = key_lower_bound(r, u, n, target, pb_shift, run_shift);
+      while (u < n) {
+        const PRec o = load_rec(r, u);
+        if (o.run != me.run || o.pad != me.pad + 1 || (int32_t)o.slen - slen > (int32_t)K) break;
+        visit(o);
+        ++u;
       }
     }
-    if (!EMIT) count[t] = c;
+    if (MODE == WALK_COUNT) count[t] = c;
+    raw += c;
+  }
+  if (MODE == WALK_MARK) {
+    for (int o = 16; o > 0; o >>= 1) raw += __shfl_down_sync(0xffffffffu, raw, o);
+    if ((threadIdx.x & 31) == 0 && raw) atomicAdd(raw_total, raw);
+  }
+}
+
+// cnt[a] = candidates in row a of the pair bitmap (one warp per row).
+__global__ void bitmap_rows_kernel(const uint32_t* __restrict__ bm, uint32_t n, uint32_t* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t a = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < n; a += warps) {
+    const uint64_t w0 = bitmap_row(a, n), w1 = a + 1 < n ? bitmap_row(a + 1, n) : w0;
+    uint32_t c = 0;
+    for (uint64_t w = w0 + lane; w < w1; w += 32) c += __popc(__ldcs(bm + w));
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0) cnt[a] = c;
+  }
+}
+
+// The candidates (a, b) of every row, in (a, b) order, from the row offsets.
+__global__ void bitmap_write_kernel(const uint32_t* __restrict__ bm, uint32_t n, const uint32_t* __restrict__ off,
+                                    uint32_t* __restrict__ oi, uint32_t* __restrict__ oj) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t a = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < n; a += warps) {
+    const uint64_t w0 = bitmap_row(a, n), w1 = a + 1 < n ? bitmap_row(a + 1, n) : w0;
+    uint32_t base = off[a];
+    for (uint64_t w = w0; w < w1; w += 32) {
+      const uint64_t lw = w + lane;
+      uint32_t v = lw < w1 ? __ldcs(bm + lw) : 0u;
+      const uint32_t p = __popc(v);
+      uint32_t incl = p;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      uint32_t at = base + incl - p;
+      const uint32_t b0 = (uint32_t)a + 1u + 32u * (uint32_t)(lw - w0);
+      while (v) {
+        const uint32_t bit = __ffs(v) - 1;
+        v &= v - 1;
+        oi[at] = (uint32_t)a;
+        oj[at] = b0 + bit;
+        ++at;
+      }
+      base += __shfl_sync(0xffffffffu, incl, 31);
+    }
   }
 }
 
@@ -367,19 +508,21 @@ int launch_max_length(const int64_t* offsets, uint32_t n, unsigned long long* ou
   return MJ_OK;
 }
 
-int launch_make_group_keys(const PRec* recs, uint32_t n, int slen_bits, int hash_bits, uint64_t* keys,
-                           uint32_t* idx, cudaStream_t s) {
+int launch_make_group_keys(const PRec* recs, uint32_t n, const GroupKeyShape& g, uint64_t* keys, uint32_t* idx,
+                           cudaStream_t s) {
   if (!n) return MJ_OK;
-  if (hash_bits < 1 || hash_bits > 32 || slen_bits < 1 || slen_bits + hash_bits > 64) return MJ_ERR_ARG;
-  group_keys_kernel<<<grid_for(n), 256, 0, s>>>(recs, n, slen_bits, hash_bits, keys, idx);
+  if (g.hash_bits < 1 || g.hash_bits > 32 || g.slen_bits < 1 || g.pb_bits < 0 || g.W < 1 ||
+      g.slen_bits + g.pb_bits + g.hash_bits > 64)
+    return MJ_ERR_ARG;
+  group_keys_kernel<<<grid_for(n), 256, 0, s>>>(recs, n, g.slen_bits, g.pb_bits, g.W, g.hash_bits, keys, idx);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
-int launch_gather_records(const uint32_t* idx, const uint64_t* keys, uint32_t n, int slen_bits, const PRec* recs,
-                          PRec* o, cudaStream_t s) {
+int launch_gather_records(const uint32_t* idx, const uint64_t* keys, uint32_t n, const GroupKeyShape& g,
+                          const PRec* recs, PRec* o, cudaStream_t s) {
   if (!n) return MJ_OK;
-  gather_kernel<<<grid_for(n), 256, 0, s>>>(idx, keys, n, slen_bits, recs, o);
+  gather_kernel<<<grid_for(n), 256, 0, s>>>(idx, keys, n, g.slen_bits, g.pb_bits, recs, o);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }
@@ -392,17 +535,53 @@ int launch_unpack_records(const PRec* recs, uint64_t n, uint32_t* sid, uint32_t*
   return MJ_OK;
 }
 
-int launch_count_pairs(const PRec* r, uint32_t n, uint32_t K, uint32_t* count, cudaStream_t s) {
+int launch_count_pairs(const PRec* r, uint32_t n, uint32_t K, const GroupKeyShape& g, uint32_t* count,
+                       cudaStream_t s) {
   if (!n) return MJ_OK;
-  pairs_kernel<false><<<grid_for(n), 256, 0, s>>>(r, n, K, 0, count, nullptr, nullptr);
+  walk_kernel<WALK_COUNT><<<grid_for(n), 256, 0, s>>>(r, n, K, g.slen_bits, g.slen_bits + g.pb_bits, 0, count,
+                                                      nullptr, nullptr, nullptr, 0, nullptr);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }
 
-int launch_fill_pairs(const PRec* r, uint32_t n, uint32_t K, int nb, const uint64_t* offs, uint64_t* pairs,
-                      cudaStream_t s) {
+int launch_fill_pairs(const PRec* r, uint32_t n, uint32_t K, const GroupKeyShape& g, int nb, const uint64_t* offs,
+                      uint64_t* pairs, cudaStream_t s) {
   if (!n) return MJ_OK;
-  pairs_kernel<true><<<grid_for(n), 256, 0, s>>>(r, n, K, nb, nullptr, offs, pairs);
+  walk_kernel<WALK_FILL><<<grid_for(n), 256, 0, s>>>(r, n, K, g.slen_bits, g.slen_bits + g.pb_bits, nb, nullptr,
+                                                     offs, pairs, nullptr, 0, nullptr);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
+uint64_t pair_bitmap_words(uint32_t n_str) {
+  if (n_str < 2) return 0;
+  const uint64_t x = n_str - 1, k = x >> 5, r = x & 31u;
+  return 16u * k * (k + 1) + r * (k + 1);
+}
+
+int launch_mark_pairs(const PRec* r, uint32_t n, uint32_t K, const GroupKeyShape& g, uint32_t n_str, uint32_t* bm,
+                      unsigned long long* raw_total, cudaStream_t s) {
+  MJ_CUDA_TRY(cudaMemsetAsync(raw_total, 0, sizeof(unsigned long long), s));
+  const uint64_t words = pair_bitmap_words(n_str);
+  if (words) MJ_CUDA_TRY(cudaMemsetAsync(bm, 0, words * 4, s));
+  if (!n || !words) return MJ_OK;
+  walk_kernel<WALK_MARK><<<grid_for(n), 256, 0, s>>>(r, n, K, g.slen_bits, g.slen_bits + g.pb_bits, 0, nullptr,
+                                                     nullptr, nullptr, bm, n_str, raw_total);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
+int launch_bitmap_rows(const uint32_t* bm, uint32_t n_str, uint32_t* cnt, cudaStream_t s) {
+  if (!n_str) return MJ_OK;
+  bitmap_rows_kernel<<<grid_for((uint64_t)n_str * 32), 256, 0, s>>>(bm, n_str, cnt);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
+int launch_bitmap_write(const uint32_t* bm, uint32_t n_str, const uint32_t* off, uint32_t* oi, uint32_t* oj,
+                        cudaStream_t s) {
+  if (!n_str) return MJ_OK;
+  bitmap_write_kernel<<<grid_for((uint64_t)n_str * 32), 256, 0, s>>>(bm, n_str, off, oi, oj);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }

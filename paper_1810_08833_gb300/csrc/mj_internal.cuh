@@ -158,17 +158,39 @@ int radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t*
                    uint64_t n, int bit_lo, int bit_hi, void* temp, bool* result_in_alt,
                    cudaStream_t s);
 
-// a5-a6: grouping keys and pair emission.  A key is hash_bits (<= 32) bits
-// of a hash of (len, Karp-Rabin key) above slen_bits bits of string length.
-int launch_make_group_keys(const PRec* recs, uint32_t n_rec, int slen_bits, int hash_bits, uint64_t* keys,
-                           uint32_t* idx, cudaStream_t s);
-// Records in group order: out[t] = recs[idx[t]] with run = keys[t] >> slen_bits.
-int launch_gather_records(const uint32_t* idx, const uint64_t* keys, uint32_t n_rec, int slen_bits,
+// a5-a6: grouping keys and pair emission.  A group key is hash_bits (<= 32)
+// bits of a hash of (len, Karp-Rabin key), then pb_bits bits of the
+// position bucket pos / W (W >= K, so the partner of a record under the
+// position filter lies in its bucket or the next), then slen_bits bits of
+// string length.
+struct GroupKeyShape {
+  int hash_bits, pb_bits, slen_bits;
+  uint32_t W;
+};
+int launch_make_group_keys(const PRec* recs, uint32_t n_rec, const GroupKeyShape& g, uint64_t* keys, uint32_t* idx,
+                           cudaStream_t s);
+// Records in group order: out[t] = recs[idx[t]] with run = the hash bits of
+// keys[t] and pad = its position bucket.
+int launch_gather_records(const uint32_t* idx, const uint64_t* keys, uint32_t n_rec, const GroupKeyShape& g,
                           const PRec* recs, PRec* out, cudaStream_t s);
-int launch_count_pairs(const PRec* r, uint32_t n_rec, uint32_t K, uint32_t* count, cudaStream_t s);
+int launch_count_pairs(const PRec* r, uint32_t n_rec, uint32_t K, const GroupKeyShape& g, uint32_t* count,
+                       cudaStream_t s);
 // pairs are packed as (i << nb) | j, i < j
-int launch_fill_pairs(const PRec* r, uint32_t n_rec, uint32_t K, int nb, const uint64_t* offs, uint64_t* pairs,
-                      cudaStream_t s);
+int launch_fill_pairs(const PRec* r, uint32_t n_rec, uint32_t K, const GroupKeyShape& g, int nb,
+                      const uint64_t* offs, uint64_t* pairs, cudaStream_t s);
+// a7 by the pair bitmap: bit (a, b), a < b < n_str, in row a (ceil((n_str - 1
+// - a) / 32) words, rows back to back); pair_bitmap_words(n_str) words in all.
+// launch_mark_pairs clears the bitmap, sets the bit of every pair the walk
+// finds and counts them (raw pairs, duplicates included) into *raw_total;
+// launch_bitmap_rows writes the candidates per row, launch_bitmap_write the
+// candidates (i, j) sorted, at the row offsets `off` (exclusive scan of the
+// row counts).
+uint64_t pair_bitmap_words(uint32_t n_str);
+int launch_mark_pairs(const PRec* r, uint32_t n_rec, uint32_t K, const GroupKeyShape& g, uint32_t n_str, uint32_t* bm,
+                      unsigned long long* raw_total, cudaStream_t s);
+int launch_bitmap_rows(const uint32_t* bm, uint32_t n_str, uint32_t* cnt, cudaStream_t s);
+int launch_bitmap_write(const uint32_t* bm, uint32_t n_str, const uint32_t* off, uint32_t* oi, uint32_t* oj,
+                        cudaStream_t s);
 int launch_key_check(const PRec* r, const uint8_t* bytes, const int64_t* offsets, uint32_t n_rec,
                      unsigned long long* mismatches, cudaStream_t s);
 // a7: unique of sorted u64 pairs -> flags; then compaction.

@@ -1,28 +1,58 @@
-"""Parity at the full workload sizes, in the launch configuration the benchmark
-times (plain and learned verification on a side stream; for the long noisy
-DNA workload also the autotuned, graph-captured plan).
+"""Exact parity at the full workload sizes, in the launch configuration the
+benchmark times (plain and learned verification on a side stream; for the
+long noisy DNA workload also the autotuned, graph-captured plan).
 
-The oracle cannot run these joins end to end in seconds, so the checks are
-per sample, or properties that hold at any size:
-  * the partitions of sampled strings equal the oracle's (Alg. 1-2);
-  * every sampled candidate shares an identical partition substring with its
-    partner that passes the length and position filters (Alg. 3);
-  * the candidate partners of sampled strings are exactly the strings that
-    share such a partition with them;
-  * sampled candidates get the oracle's banded distance, and a candidate is
-    in the output iff that distance is <= K, with that distance;
-  * the learned first-pass band returns exactly the plain output.
+The CPU oracle's complete results on the five workloads are stored as SHA-256
+digests and counts in tests/golden/fullsize_digests.json, written by
+tests/golden/make_fullsize_digests.py, which calls only the oracle and the
+input generators.  Here the GPU path's results on the same generated inputs
+are hashed the same way and must match exactly:
+  * the partitions of Alg. 1-2 ((sid, pos, len) in string order);
+  * the candidate set C of Alg. 3 ((i, j), sorted);
+  * min(ED, K + 1) of every candidate (mj_verify, band K, in the order of C);
+  * the output of the join ((i, j, ED), sorted), in plain and learned mode.
 """
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
-import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
 
-# workload -> (sampled strings for partitions and partners, sampled candidates for distances)
-CASES = {2: (200, 3000), 3: (60, 300), 4: (300, 3000), 5: (200, 2000)}
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = os.path.join(HERE, "golden", "fullsize_digests.json")
+
+
+def _golden() -> dict:
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def digest_rows(*cols, chunk=1 << 24) -> str:
+    """SHA-256 of the rows (c0[t], c1[t], ...) as little-endian int64, the
+    byte layout of the stored digests; the columns are device or host
+    tensors, copied to the host a chunk of rows at a time."""
+    import torch
+    h = hashlib.sha256()
+    m = int(cols[0].shape[0])
+    for lo in range(0, m, chunk):
+        hi = min(m, lo + chunk)
+        parts = [c[lo:hi].to("cpu", torch.int64).numpy() if torch.is_tensor(c) else
+                 np.asarray(c[lo:hi], dtype=np.int64) for c in cols]
+        rows = np.stack(parts, axis=1) if len(parts) > 1 else parts[0]
+        h.update(np.ascontiguousarray(rows.astype("<i8", copy=False)).tobytes())
+    return h.hexdigest()
+
+
+def input_digest(s) -> str:
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(s.bytes, dtype=np.uint8).tobytes())
+    h.update(np.ascontiguousarray(s.offsets, dtype="<i8").tobytes())
+    return h.hexdigest()
 
 
 @pytest.fixture(scope="module")
@@ -50,114 +80,65 @@ def _train_band(ctx, mj, cfg, stream):
     ctx.band_train(x, ed, K=tr.K, steps=300, batch=1024, lr=2e-3, tau=0.9, seed=13, stream=stream)
 
 
-class PartitionIndex:
-    """Partition records grouped by (length, key) for lookups by value."""
-
-    def __init__(self, sid, pos, ln, key):
-        self.sid, self.pos, self.ln, self.key = sid, pos, ln, key
-        self.order = np.lexsort((key, ln))
-        self.ln_s = ln[self.order]
-        self.key_s = key[self.order]
-
-    def same(self, r):
-        """Records with the length and key of record r."""
-        lo = np.searchsorted(self.ln_s, self.ln[r], "left")
-        hi = np.searchsorted(self.ln_s, self.ln[r], "right")
-        ks = self.key_s[lo:hi]
-        a = lo + np.searchsorted(ks, self.key[r], "left")
-        b = lo + np.searchsorted(ks, self.key[r], "right")
-        return self.order[a:b]
-
-    def partners(self, L, K, i):
-        """Strings sharing a partition (same length and key; key collisions
-        are excluded by the device key check) with string i, where |L_i - L_j|
-        <= K and the position filter holds for that partition pair."""
-        out = set()
-        lo, hi = np.searchsorted(self.sid, i, "left"), np.searchsorted(self.sid, i, "right")
-        for r in range(lo, hi):
-            t = self.same(r)
-            j = self.sid[t]
-            pi, pj = self.pos[r], self.pos[t]
-            ok = (j != i) & (np.abs(L[i] - L[j]) <= K)
-            ok &= np.abs(pi - pj) + np.abs((L[i] - pi) - (L[j] - pj)) <= K
-            out.update(j[ok].tolist())
-        return out
-
-
-@pytest.mark.parametrize("cfg", sorted(CASES))
-def test_fullsize_sampled_parity(ctx, cfg):
+@pytest.mark.parametrize("cfg", [1, 2, 3, 4, 5])
+def test_fullsize_exact_parity(ctx, cfg):
     import torch
     import paper_1810_08833_gb300 as mj
-    n_str, n_pairs = CASES[cfg]
-    s = synth.make_config(cfg)
+    gold = _golden().get(str(cfg))
+    assert gold is not None, f"no stored oracle digests for workload {cfg}"
+    s = synth.make_config(cfg, n_roots=gold["roots"])
+    assert input_digest(s) == gold["input_sha256"], \
+        "the input generator made a different string set from the one the digests were made from"
     K = s.K
-    L = s.lengths().astype(np.int64)
-    rng = np.random.Generator(np.random.PCG64(1000 + cfg))
-    p = oracle.derive_params(s.bytes, s.offsets, K=K, T=s.T)
     stream = torch.cuda.Stream()
     data = torch.from_numpy(s.bytes).cuda()
     off = torch.from_numpy(s.offsets).cuda()
-    plain = mj.params(K, T=s.T, flags=mj.MJ_FLAG_KEY_CHECK)
+    checked = mj.params(K, T=s.T, flags=mj.MJ_FLAG_KEY_CHECK)
     with torch.cuda.stream(stream):
-        _train_band(ctx, mj, cfg, stream)
-        pi_, pj_, pe_ = ctx.join(data, off, mj.params(K, T=s.T), stream=stream)
-        li_, lj_, le_ = ctx.join(data, off, mj.params(K, T=s.T, verify_mode=mj.MJ_VERIFY_LEARNED), stream=stream)
+        d = ctx.derive(data, off, checked, stream=stream)
+        assert {k: d[k] for k in ("sigma", "bits", "q", "N")} == gold["derived"]
+
+        sid, pos, ln, _ = ctx.partition(data, off, checked, stream=stream)
+        stream.synchronize()
+        assert int(sid.shape[0]) == gold["n_partitions"]
+        assert digest_rows(sid, pos, ln) == gold["partitions_sha256"]
+        del sid, pos, ln
+
+        ci, cj = ctx.candidates(data, off, checked, stream=stream)
+        stream.synchronize()
+        st = ctx.stats()
+        assert st["key_collisions"] == 0 and st["device_flags"] == 0
+        assert int(ci.shape[0]) == gold["n_candidates"]
+        assert digest_rows(ci, cj) == gold["candidates_sha256"]
+        ced = ctx.verify(data, off, ci, cj, K, stream=stream)
+        stream.synchronize()
+        assert digest_rows(ced) == gold["candidate_ed_sha256"]
+        del ci, cj, ced
+
+        oi, oj, oe = ctx.join(data, off, mj.params(K, T=s.T), stream=stream)
         stream.synchronize()
         assert ctx.stats()["device_flags"] == 0
-        for a, b in ((pi_, li_), (pj_, lj_), (pe_, le_)):
-            assert torch.equal(a, b), "learned band changed the output"
+        assert int(oi.shape[0]) == gold["n_output"]
+        assert digest_rows(oi, oj, oe) == gold["output_sha256"]
+
+        _train_band(ctx, mj, cfg, stream)
+        for flags in (0, mj.MJ_FLAG_FIRST_PASS):
+            li, lj, le = ctx.join(data, off, mj.params(K, T=s.T, verify_mode=mj.MJ_VERIFY_LEARNED, flags=flags),
+                                  stream=stream)
+            stream.synchronize()
+            assert ctx.stats()["device_flags"] == 0
+            assert digest_rows(li, lj, le) == gold["output_sha256"], f"learned mode (flags {flags})"
+            del li, lj, le
+
         if cfg == 3:   # the autotuned per-bucket plan, captured in a graph
-            ci, cj = ctx.candidates(data, off, plain, stream=stream)
+            ci, cj = ctx.candidates(data, off, checked, stream=stream)
             ctx.autotune_verify(data, off, ci, cj, K, sample=2048, stream=stream)
+            del ci, cj
             ctx.set_verify_config(mj.MJ_VERIFY_KERNEL_TUNED, 0, 0, 1)
-            for _ in range(3):   # uncaptured, captured, replayed
-                ti, tj, te = ctx.join(data, off, mj.params(K, T=s.T), stream=stream)
-                stream.synchronize()
-                for a, b in ((pi_, ti), (pj_, tj), (pe_, te)):
-                    assert torch.equal(a, b), "tuned graph plan changed the output"
-            ctx.set_verify_config(0, 0, 0, 0)
-        sid, pos, ln, key = ctx.partition(data, off, plain, stream=stream)
-        ci, cj = ctx.candidates(data, off, plain, stream=stream)
-        stream.synchronize()
-    st = ctx.stats()
-    assert st["key_collisions"] == 0 and st["device_flags"] == 0
-    sid, pos, ln, key = (t.cpu().numpy().astype(np.int64) for t in (sid, pos, ln, key))
-    assert np.all(np.diff(sid) >= 0)   # records come in string order
-    index = PartitionIndex(sid, pos, ln, key)
-
-    # partitions of sampled strings
-    sample = np.sort(rng.choice(s.n, size=min(n_str, s.n), replace=False))
-    for i in sample.tolist():
-        want = oracle.partition(s.bytes, s.offsets, p, lo=i, hi=i + 1)
-        sel = slice(np.searchsorted(sid, i, "left"), np.searchsorted(sid, i, "right"))
-        assert np.array_equal(pos[sel], want.pos) and np.array_equal(ln[sel], want.len), i
-
-    # candidate partners of sampled strings, by the definition
-    for i in sample[: max(1, len(sample) // 4)].tolist():
-        got = set(cj[ci == i].cpu().tolist()) | set(ci[cj == i].cpu().tolist())
-        assert got == index.partners(L, K, i), i
-
-    # sampled candidates: definition, oracle distance, output membership
-    m = ci.shape[0]
-    assert m > 0
-    idx = torch.from_numpy(rng.choice(m, size=min(n_pairs, m), replace=False)).cuda()
-    pairs = torch.stack([ci[idx], cj[idx]], 1).cpu().numpy().astype(np.int64)
-    assert np.all(pairs[:, 0] < pairs[:, 1])
-    for a, b in pairs[: min(200, len(pairs))].tolist():
-        assert b in index.partners(L, K, a), (a, b)
-    ed = oracle.ed_band_pairs(s.bytes, s.offsets, pairs, K)
-    out = {(a, b): e for a, b, e in zip(pi_.cpu().tolist(), pj_.cpu().tolist(), pe_.cpu().tolist())}
-    for (a, b), e in zip(pairs.tolist(), ed.tolist()):
-        if e <= K:
-            assert out.get((a, b)) == e, (a, b, e, out.get((a, b)))
-        else:
-            assert (a, b) not in out, (a, b)
-
-    # sampled outputs: oracle distance within K, pairs unique and ordered
-    outp = np.stack([pi_.cpu().numpy(), pj_.cpu().numpy()], 1).astype(np.int64)
-    assert np.all(outp[:, 0] < outp[:, 1])
-    assert np.unique(outp, axis=0).shape[0] == outp.shape[0]
-    if outp.shape[0]:
-        k = rng.choice(outp.shape[0], size=min(n_pairs, outp.shape[0]), replace=False)
-        want = oracle.ed_band_pairs(s.bytes, s.offsets, outp[k], K)
-        assert np.array_equal(want, pe_.cpu().numpy()[k].astype(np.int64))
+            try:
+                for _ in range(3):   # uncaptured, captured, replayed
+                    ti, tj, te = ctx.join(data, off, mj.params(K, T=s.T), stream=stream)
+                    stream.synchronize()
+                    assert digest_rows(ti, tj, te) == gold["output_sha256"], "tuned graph plan"
+            finally:
+                ctx.set_verify_config(0, 0, 0, 0)

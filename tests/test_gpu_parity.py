@@ -115,14 +115,18 @@ def test_partition_anchor_edges(ctx):
         assert [st[a:a + b] for a, b in zip(pos[sel], ln[sel])] == expect
 
 
+DEDUP = {"auto": 0, "sort": 64, "bitmap": 128}   # MJ_FLAG_DEDUP_SORT, MJ_FLAG_DEDUP_BITMAP
+
+
+@pytest.mark.parametrize("dedup", sorted(DEDUP))
 @pytest.mark.parametrize("name,factory", SETS, ids=IDS)
-def test_candidates_parity(ctx, name, factory):
+def test_candidates_parity(ctx, name, factory, dedup):
     import paper_1810_08833_gb300 as mj
     s, p = get_set(name, factory)
     parts = oracle.partition(s.bytes, s.offsets, p)
     want = oracle.candidates(s.bytes, s.offsets, s.K, parts)
     data, off = to_device(s)
-    ci, cj = ctx.candidates(data, off, mj.params(s.K, T=s.T, flags=1))
+    ci, cj = ctx.candidates(data, off, mj.params(s.K, T=s.T, flags=mj.MJ_FLAG_KEY_CHECK | DEDUP[dedup]))
     got = np.stack([ci.cpu().numpy(), cj.cpu().numpy()], axis=1).astype(np.int64)
     assert got.shape == want.shape, (got.shape, want.shape)
     assert np.array_equal(got, want)
@@ -131,13 +135,14 @@ def test_candidates_parity(ctx, name, factory):
     assert st["device_flags"] == 0
 
 
+@pytest.mark.parametrize("dedup", sorted(DEDUP))
 @pytest.mark.parametrize("name,factory", SETS, ids=IDS)
-def test_join_parity(ctx, name, factory):
+def test_join_parity(ctx, name, factory, dedup):
     import paper_1810_08833_gb300 as mj
     s, p = get_set(name, factory)
     ref = oracle.minjoin(s.bytes, s.offsets, K=s.K, T=s.T)
     data, off = to_device(s)
-    oi, oj, oe = ctx.join(data, off, mj.params(s.K, T=s.T))
+    oi, oj, oe = ctx.join(data, off, mj.params(s.K, T=s.T, flags=DEDUP[dedup]))
     got = np.stack([t.cpu().numpy() for t in (oi, oj, oe)], axis=1).astype(np.int64)
     want = np.concatenate([ref.pairs, ref.ed[:, None]], axis=1)
     assert got.shape == want.shape, (got.shape, want.shape)
