@@ -66,7 +66,8 @@ extern "C" {
 /* verification kernels (mj_verify_config.kernel) */
 #define MJ_VERIFY_KERNEL_AUTO 0       /* diagonal for K <= 255, wavefront above */
 #define MJ_VERIFY_KERNEL_DIAGONAL 1   /* one thread per pair, band as ceil((K+1)/32) words */
-#define MJ_VERIFY_KERNEL_WAVEFRONT 2  /* G lanes per pair, 32-row blocks, skewed wavefront */
+#define MJ_VERIFY_KERNEL_WAVEFRONT 2  /* G lanes per pair, 32-row blocks, skewed wavefront: within one warp up
+                                         to 32 lanes, one CTA of several warps from 64 to 1,024 lanes */
 #define MJ_VERIFY_KERNEL_TUNED 3      /* per length bucket, as chosen by mj_autotune_verify */
 
 typedef struct mj_ctx mj_ctx;
@@ -76,8 +77,12 @@ typedef struct mj_ctx mj_ctx;
  * bucket (floor(log2) of the shorter length) uses the kernel the autotuner
  * picked for it.
  *  kernel    MJ_VERIFY_KERNEL_*.
- *  lanes     wavefront only: lanes per pair (2, 4, 8, 16 or 32); 0 = the fewest
- *            that hold the band.  Too few lanes for a band is MJ_ERR_UNSUPPORTED.
+ *  lanes     wavefront only: lanes per pair, 2, 4, 8, 16 or 32 (one warp) or
+ *            64, 128, 256, 512 or 1024 (one CTA per pair, its warps handing
+ *            block boundaries over through shared memory); 0 = the fewest that
+ *            hold the band: one warp holds bands up to K = 1,024, a CTA of G
+ *            lanes bands with 34 G >= K + 32 (K up to 34,784 with 1,024).  Too
+ *            few lanes for a band is MJ_ERR_UNSUPPORTED.
  *  batching  TUNED only: 0 = one persistent launch per run of consecutive
  *            buckets that share a kernel; 1 = one launch per length bucket.
  *  graph     1 = capture the plain verification stage (ordering, bucketing,
@@ -224,10 +229,24 @@ int mj_candidates_copy(mj_ctx* ctx, uint32_t* d_i, uint32_t* d_j, void* stream);
  * (d_i[t], d_j[t]), t < m, writes d_ed[t] = ED if ED <= k_t, else k_t + 1,
  * where k_t = d_k[t] if d_k is non-null, else K.  Any pair of strings is
  * allowed (equal ids, empty strings).  Stream-ordered; does not synchronise.
- * Rank codes are derived from the n strings given. */
+ * Rank codes are derived from the n strings given.  Bands: the diagonal
+ * kernel holds K <= 255, one warp's wavefront K <= 1,024 and a CTA's up to
+ * K = 34,784 (lanes of mj_verify_config); a wider band (or K >= 65,536)
+ * returns MJ_ERR_UNSUPPORTED and writes nothing.  A pair id >= n yields
+ * k_t + 1 and sets bit 0 of the context's device flags: mj_device_flags
+ * reads them once the stream has run the call. */
 int mj_verify(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n,
               const uint32_t* d_i, const uint32_t* d_j, const uint32_t* d_k, uint64_t m, uint32_t K,
               void* stream, uint32_t* d_ed);
+
+/* Device-side check flags of the context's last call (bit 0: an index
+ * outside its buffer, e.g. a pair id >= n, was skipped and its pair given
+ * k + 1; bit 1: a bounded wait gave up; bit 2: an output buffer was too
+ * small; bit 3: a string too long for 32-bit column indexing).  Synchronises
+ * `stream`, copies the flags into *flags and into mj_stats.device_flags.
+ * Calls that return a count check these flags themselves (MJ_ERR_DEVICE);
+ * mj_verify does not synchronise, so its flags are read here. */
+int mj_device_flags(mj_ctx* ctx, void* stream, uint32_t* flags);
 
 /* mj_verify for callers that cannot allocate device memory.  No counterpart
  * in the paper: it exists for code that may not call cudaMalloc, such as a

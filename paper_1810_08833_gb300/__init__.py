@@ -110,6 +110,7 @@ _SIGS = {
     "mj_candidates_copy": (ctypes.c_int, [VP, VP, VP, VP]),
     "mj_verify": (ctypes.c_int, [VP, VP, VP, U32, VP, VP, VP, U64, U32, VP, VP]),
     "mj_verify_static": (ctypes.c_int, [VP, VP, U32, VP, VP, U64, U32, VP, VP]),
+    "mj_device_flags": (ctypes.c_int, [VP, VP, ctypes.POINTER(U32)]),
     "mj_join": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, ctypes.POINTER(U64)]),
     "mj_result_copy": (ctypes.c_int, [VP, VP, VP, VP, VP]),
     "mj_join_host": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, ctypes.POINTER(U64)]),
@@ -286,6 +287,11 @@ class Context:
         _check(self._lib.mj_verify(self._h, _ptr(data), _ptr(offsets), n, _ptr(i), _ptr(j), _ptr(k), m, K,
                                    _stream(stream), _ptr(ed)), "mj_verify")
         return ed
+
+    def device_flags(self, stream=None) -> int:
+        f = U32()
+        _check(self._lib.mj_device_flags(self._h, _stream(stream), ctypes.byref(f)), "mj_device_flags")
+        return f.value
 
     def join(self, data, offsets, p: Params, stream=None):
         import torch

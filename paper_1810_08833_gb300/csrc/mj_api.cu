@@ -912,7 +912,8 @@ void mj_destroy(mj_ctx* c) {
 int mj_set_verify_config(mj_ctx* c, const mj_verify_config* cfg) {
   if (!c || !cfg) return MJ_ERR_ARG;
   if (cfg->kernel > MJ_VERIFY_KERNEL_TUNED || cfg->batching > 1 || cfg->graph > 1) return MJ_ERR_ARG;
-  if (cfg->lanes && (cfg->lanes > 32 || (cfg->lanes & (cfg->lanes - 1)) || cfg->lanes < 2)) return MJ_ERR_ARG;
+  if (cfg->lanes && (cfg->lanes > (uint32_t)kMaxCtaLanes || (cfg->lanes & (cfg->lanes - 1)) || cfg->lanes < 2))
+    return MJ_ERR_ARG;
   c->vcfg = *cfg;
   return MJ_OK;
 }
@@ -1001,6 +1002,17 @@ int mj_candidates_copy(mj_ctx* c, uint32_t* d_i, uint32_t* d_j, void* stream) {
   return MJ_OK;
 }
 
+int mj_device_flags(mj_ctx* c, void* stream, uint32_t* flags) {
+  if (!c || !flags) return MJ_ERR_ARG;
+  DeviceGuard g(c->device);
+  *flags = 0;
+  if (!c->dev_flags.p) return MJ_OK;   // no device work yet
+  MJ_TRY(readback(c, c->dev_flags.p, 4, S(stream)));
+  *flags = *(uint32_t*)c->h_small;
+  c->stats.device_flags |= *flags;
+  return MJ_OK;
+}
+
 int mj_verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const uint32_t* d_i,
               const uint32_t* d_j, const uint32_t* d_k, uint64_t m, uint32_t K, void* stream, uint32_t* d_ed) {
   if (!c || !d_offsets) return MJ_ERR_ARG;
@@ -1039,13 +1051,15 @@ int mj_autotune_verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offse
   MJ_TRY(derive(c, d_bytes, d_offsets, n, &p, s));
   if (rep) memset(rep, 0, sizeof(*rep));
   // candidates: the diagonal kernel when its band fits 8 words, then the
-  // wavefront with 1x, 2x, 4x ... the fewest lanes
+  // wavefront with 1x, 2x, 4x ... the fewest lanes (one warp up to 32 lanes,
+  // a CTA of several warps above)
   uint32_t ck[MJ_TUNE_CANDIDATES], cl[MJ_TUNE_CANDIDATES], nc = 0;
   if (verify_words_for(K) <= 8) {
     ck[nc] = MJ_VERIFY_KERNEL_DIAGONAL;
     cl[nc++] = 0;
   }
-  for (int lanes = wave_lanes_for(K); lanes <= 32 && nc < MJ_TUNE_CANDIDATES; lanes *= 2) {
+  if (fewest_lanes_for(K) > kMaxCtaLanes) return MJ_ERR_UNSUPPORTED;
+  for (int lanes = fewest_lanes_for(K); lanes <= kMaxCtaLanes && nc < MJ_TUNE_CANDIDATES; lanes *= 2) {
     ck[nc] = MJ_VERIFY_KERNEL_WAVEFRONT;
     cl[nc++] = (uint32_t)lanes;
   }

@@ -234,6 +234,11 @@ int launch_build_planes(const uint8_t* bytes, uint64_t nbytes, const RankTable& 
 int launch_verify(const VerifyArgs& a, uint64_t plane_words, uint32_t guard_words, uint32_t kmax,
                   unsigned long long* next, cudaStream_t s, int kernel = MJ_VERIFY_KERNEL_AUTO, int lanes = 0);
 int wave_lanes_for(uint32_t kmax);
+// lanes of the CTA wavefront (several warps per pair) for bands up to kmax,
+// and the fewest lanes of either wavefront form; at most kMaxCtaLanes
+constexpr int kMaxCtaLanes = 1024;
+int cta_lanes_for(uint32_t kmax);
+int fewest_lanes_for(uint32_t kmax);
 
 // length buckets of the verification order (bucket of a pair: floor(log2 of
 // its shorter length), 0..31); keys are the sorted work keys N - n, so the

@@ -728,6 +728,226 @@ __global__ void __launch_bounds__(128, P <= 2 ? 8 : 1) verify_wave_kernel(Verify
   }
 }
 
+// ---------------------------------------------------------------- bands wider than one warp
+// One CTA of V warps (G = 32 V lanes) per pair, for bands whose wavefront
+// needs more than 32 lanes (K >= 1025).  Blocks, lanes and the column step
+// are those of verify_wave_kernel (lane g owns blocks b = g mod G), with one
+// change to the schedule: block b computes column j at step
+//     j + b + 32 floor(b / 32),
+// i.e. every group of 32 blocks runs one window of kWaveSteps (= 32) steps
+// behind the group above it.  Inside a group the predecessor block b - 1 is
+// the next lane down in the same warp and hands its word over by a shuffle,
+// one step earlier as before.  The first block of a group (lane 0 of its
+// warp) takes its predecessor's word from the last lane of the previous warp,
+// written 33 steps earlier into a ring in shared memory: the CTA synchronises
+// once per window (__syncthreads), after which the previous window's words
+// are visible.  The extra skew also spaces a lane's consecutive blocks b and
+// b + G by 2G steps instead of G, so G lanes hold any band with
+//     34 G >= 32 + (dhi - dlo),  dhi - dlo <= K.
+// Pair fetch, the early exit and the result are CTA-wide decisions taken at
+// the window barrier; every loop bound is uniform over the CTA.
+constexpr int kRing = 128;   // words per warp in the ring: steps s - 128 .. s - 1 (reads reach s - 33)
+
+template <int V, int P>
+__global__ void __launch_bounds__(32 * V) verify_cta_kernel(VerifyArgs a, uint64_t PW, uint32_t GW,
+                                                            unsigned long long* __restrict__ next) {
+  constexpr int G = 32 * V;
+  constexpr int S = kWaveSteps;
+  static_assert(S == 32 && kRing >= 2 * S + 2 && (kRing & (kRing - 1)) == 0, "window and ring sizes");
+  __shared__ uint32_t ring[V][kRing];
+  __shared__ unsigned long long s_t;   // pair of the CTA (~0: none left)
+  __shared__ int s_flag[3];            // per window (mod 3): 1 = finished, 2 = rejected
+  __shared__ int32_t s_result[3];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int prev_warp = (warp + V - 1) % V;
+  const uint64_t q_lo = a.range_lo ? *a.range_lo : 0;
+  const uint64_t q_hi = a.range_hi ? *a.range_hi : a.m;
+  if (tid < 3) s_flag[tid] = 0;
+  uint32_t k = 0;
+  int64_t oA = 0, oB = 0;
+  int32_t m = 0, n = 0, d0 = 0, dlo = 0, dhi = 0, bm = 0;
+  int32_t b = 0, u = kDeadU, span = 0, u_valid = -1, dg = 0x40000000, colbase = 0;
+  uint32_t T = 0, Pv = 0, Mv = 0;
+  uint32_t pa[P], bw[P];
+  uint32_t pub = kIdle;
+  bool done = false, reject = false;
+  int32_t result = 0;
+  uint32_t win = 0;   // windows run by the CTA (selects the flag slot)
+  uint64_t work = 0, cells = 0, nskip = 0;
+#pragma unroll
+  for (int p = 0; p < P; ++p) pa[p] = bw[p] = 0u;
+
+  // Take block nb after s steps.  Its columns are [jf, jl]; it computes
+  // column j at step j + colbase (colbase = nb + 32 floor(nb / 32)).
+  auto take_block = [&](int32_t nb, int32_t s) {
+    b = nb;
+    if (b <= bm) {
+      const int32_t jf = max(1, 32 * b + 1 - dhi);
+      const int32_t jl = min(n, 32 * b + 32 - dlo);
+      colbase = b + S * (b >> 5);
+      u = s - (jf + colbase);
+      span = jl - jf;
+      u_valid = b == 0 ? -1 : min(n, 32 * b - dlo) - jf;   // last column of block b - 1
+      dg = jf - 32 * b - 1 + d0;
+    } else {
+      u = kDeadU;
+      span = 0;
+      u_valid = -1;
+      dg = 0x40000000;
+      colbase = 0;
+    }
+  };
+
+  while (true) {
+    // ---- thread 0 takes pairs until one needs the wavefront
+    if (tid == 0) {
+      unsigned long long got = ~0ull;
+      while (true) {
+        const uint64_t q = q_lo + atomicAdd(next, 1ull);
+        if (q >= q_hi) break;
+        const uint64_t t = a.order ? a.order[q] : q;
+        const uint32_t x = a.pi[t], y = a.pj[t];
+        const uint32_t kt = a.pk ? a.pk[t] : a.K;
+        const uint32_t* fed = a.first_ed ? a.first_ed : a.ed;
+        if (a.skip_kband && a.skip_kband[t] < a.K && fed[t] <= a.skip_kband[t]) {
+          if (a.first_ed) a.ed[t] = fed[t];
+          ++nskip;
+          continue;
+        }
+        if (x >= a.n_strings || y >= a.n_strings) {
+          atomicOr(a.dev_flags, FLAG_BOUNDS);
+          a.ed[t] = kt + 1;
+          continue;
+        }
+        const int64_t lx = __ldg(a.offsets + x + 1) - __ldg(a.offsets + x);
+        const int64_t ly = __ldg(a.offsets + y + 1) - __ldg(a.offsets + y);
+        const int64_t mm = lx >= ly ? lx : ly, nn = lx >= ly ? ly : lx;
+        if (a.cells) cells += band_cells(mm, nn, a.K);
+        if (mm >= (int64_t)kMaxLen) {
+          atomicOr(a.dev_flags, FLAG_LENGTH);
+          a.ed[t] = kt + 1;
+          continue;
+        }
+        if (mm - nn > (int64_t)kt) {
+          a.ed[t] = kt + 1;
+          continue;
+        }
+        if (nn == 0) {
+          a.ed[t] = (uint32_t)mm;
+          continue;
+        }
+        got = t;
+        break;
+      }
+      s_t = got;
+    }
+    __syncthreads();
+    const unsigned long long t = s_t;
+    if (t == ~0ull) break;
+    {
+      const uint32_t x = a.pi[t], y = a.pj[t];
+      k = a.pk ? a.pk[t] : a.K;
+      const int64_t ox = __ldg(a.offsets + x), lx = __ldg(a.offsets + x + 1) - ox;
+      const int64_t oy = __ldg(a.offsets + y), ly = __ldg(a.offsets + y + 1) - oy;
+      const bool xa = lx >= ly;
+      oA = xa ? ox : oy;
+      oB = xa ? oy : ox;
+      m = (int32_t)(xa ? lx : ly);
+      n = (int32_t)(xa ? ly : lx);
+      d0 = m - n;
+      dlo = -(int32_t)((k - (uint32_t)d0) >> 1);
+      dhi = d0 + (int32_t)((k - (uint32_t)d0) >> 1);
+      if (dhi - dlo < 63) dlo = dhi - 63;
+      bm = (m - 1) >> 5;
+    }
+    take_block(tid, 0);
+    pub = kIdle;
+    done = reject = false;
+    const int32_t last_step = n + bm + S * (bm >> 5);   // block bm's last column
+    int32_t sbase = 0;
+    while (true) {
+#pragma unroll 8
+      for (int it = 0; it < S; ++it) {
+        const int32_t s1 = sbase + it + 1;   // this step, counted from 1
+        uint32_t w_in = __shfl_up_sync(0xffffffffu, pub, 1);
+        if (lane == 0) w_in = ring[prev_warp][(uint32_t)(s1 - 1 - S) & (kRing - 1)];
+        ++u;
+        const uint32_t wv = u <= u_valid ? w_in : kIdle;
+        uint32_t Ph, hn;
+        wave_column<P>(pa, bw, wv, Pv, Mv, T, Ph, hn);
+        pub = ((Ph & 0x80000000u) | T) + hn;
+        const bool diag_here = it == S - 1 && (uint32_t)(u + dg) < 32u;
+        if (u == 0 || u == span || diag_here) {
+          if (u == 0) {   // first column: load the block's symbols, rows start from +1 deltas
+            const int32_t jf = s1 - colbase;
+            wave_load_bits<P>(a, PW, (uint64_t)(oA + 32 * (int64_t)b + 32 * (int64_t)GW), pa, false);
+            wave_load_bits<P>(a, PW, (uint64_t)(oB + jf - 1 + 32 * (int64_t)GW), bw, true);
+            Pv = 0xffffffffu;
+            Mv = 0u;
+            wave_column<P>(pa, bw, wv, Pv, Mv, T, Ph, hn);
+            const int32_t above = b == 0 ? 1 : (int32_t)((w_in >> 1) & 0x3fffffffu);
+            const int32_t score = above + (int32_t)__popc(Pv) - (int32_t)__popc(Mv);
+            T = (uint32_t)score << 1;
+            pub = ((Ph & 0x80000000u) | T) + hn;
+          }
+          if (diag_here && (uint32_t)u <= (uint32_t)span) {   // row j + d0 of diagonal d0
+            const int tr = u + dg;
+            const uint32_t below = tr == 31 ? 0u : (0xffffffffu << (tr + 1));
+            const int32_t diag = (int32_t)(T >> 1) - (int32_t)__popc(Pv & below) + (int32_t)__popc(Mv & below);
+            if (diag > (int32_t)k) reject = true;
+          }
+          if (u == span) {   // the block leaves the band
+            if (b == bm) {
+              const int tm = (m - 1) & 31;
+              const uint32_t below = tm == 31 ? 0u : (0xffffffffu << (tm + 1));
+              result = (int32_t)(T >> 1) - (int32_t)__popc(Pv & below) + (int32_t)__popc(Mv & below);
+              done = true;
+            }
+            work += (uint64_t)(span + 1);
+            take_block(b + G, s1);
+          }
+        }
+        if (lane == 31) ring[warp][(uint32_t)s1 & (kRing - 1)] = pub;
+      }
+      sbase += S;
+      if (u >= 0 && u <= span)   // B's symbols of the next 32 columns
+        wave_load_bits<P>(a, PW, (uint64_t)(oB + (sbase - colbase) + 32 * (int64_t)GW), bw, true);
+      const uint32_t slot = win % 3;
+      if (done) {
+        s_result[slot] = result;
+        atomicOr(&s_flag[slot], 1);
+      }
+      if (reject) atomicOr(&s_flag[slot], 2);
+      __syncthreads();
+      const int f = s_flag[slot];
+      const int32_t fin = s_result[slot];
+      if (tid == 0) s_flag[(win + 2) % 3] = 0;
+      ++win;
+      const bool overrun = sbase >= last_step;   // finished at the latest in the window of step last_step
+      if (f || overrun) {
+        if (tid == 0) {
+          if (f & 1) {
+            a.ed[t] = fin > (int32_t)k ? k + 1 : (uint32_t)fin;
+          } else if (f & 2) {
+            a.ed[t] = k + 1;
+          } else {
+            atomicOr(a.dev_flags, FLAG_BOUNDS);
+            a.ed[t] = k + 1;
+          }
+        }
+        if (u >= 0 && u <= span) work += (uint64_t)(u + 1);   // block cut short by the exit
+        break;
+      }
+    }
+  }
+  if (a.work) {
+    for (int o = 16; o > 0; o >>= 1) work += __shfl_down_sync(0xffffffffu, work, o);
+    if (lane == 0 && work) atomicAdd(a.work, (unsigned long long)work);
+  }
+  if (tid == 0 && a.cells && cells) atomicAdd(a.cells, (unsigned long long)cells);
+  if (tid == 0 && a.skipped && nskip) atomicAdd(a.skipped, (unsigned long long)nskip);
+}
+
 template <int G, int P>
 int launch_gp(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long* next, cudaStream_t s) {
   int dev = 0, sms = kNumSMsHint, per_sm = 1;
@@ -748,6 +968,27 @@ int launch_g(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long* 
   if (a.bits <= 2) return launch_gp<G, 2>(a, PW, GW, next, s);
   if (a.bits <= 5) return launch_gp<G, 5>(a, PW, GW, next, s);
   return launch_gp<G, 8>(a, PW, GW, next, s);
+}
+
+template <int V, int P>
+int launch_vp(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long* next, cudaStream_t s) {
+  int dev = 0, sms = kNumSMsHint, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, verify_cta_kernel<V, P>, 32 * V, 0);
+  if (per_sm < 1) per_sm = 1;
+  uint64_t grid = (uint64_t)sms * per_sm;
+  if (a.m < grid) grid = a.m;
+  verify_cta_kernel<V, P><<<(unsigned)(grid ? grid : 1), 32 * V, 0, s>>>(a, PW, GW, next);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
+template <int V>
+int launch_v(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long* next, cudaStream_t s) {
+  if (a.bits <= 2) return launch_vp<V, 2>(a, PW, GW, next, s);
+  if (a.bits <= 5) return launch_vp<V, 5>(a, PW, GW, next, s);
+  return launch_vp<V, 8>(a, PW, GW, next, s);
 }
 
 template <int W, int P>
@@ -774,6 +1015,7 @@ template <int W>
 int launch_w(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long* next, cudaStream_t s) {
   if (a.bits <= 2) return launch_wp<W, 2>(a, PW, GW, next, s);
   if (a.bits <= 5) return launch_wp<W, 5>(a, PW, GW, next, s);
+  if (a.bits == 7) return launch_wp<W, 7>(a, PW, GW, next, s);   // printable text (33-128 symbols)
   return launch_wp<W, 8>(a, PW, GW, next, s);
 }
 
@@ -804,12 +1046,41 @@ int wave_lanes_for(uint32_t kmax) {
   return (int)g;
 }
 
+int cta_lanes_for(uint32_t kmax) {
+  // a lane's blocks b and b + G are 2G steps apart in the CTA schedule, so
+  // G lanes hold bands with 34 G >= 32 + (dhi - dlo), dhi - dlo <= max(kmax, 63)
+  const uint32_t w = kmax + 1 < 64 ? 64 : kmax + 1;
+  const uint32_t need = (31 + w + 33) / 34;
+  uint32_t g = 64;
+  while (g < need) g <<= 1;
+  return (int)g;
+}
+
+int fewest_lanes_for(uint32_t kmax) {
+  const int g = wave_lanes_for(kmax);
+  return g <= 32 ? g : cta_lanes_for(kmax);
+}
+
 int launch_verify(const VerifyArgs& a, uint64_t PW, uint32_t GW, uint32_t kmax, unsigned long long* next,
                   cudaStream_t s, int kernel, int lanes) {
   if (a.m == 0) return MJ_OK;
-  MJ_CUDA_TRY(cudaMemsetAsync(next, 0, sizeof(unsigned long long), s));
   const int W = verify_words_for(kmax);
   if (kernel == MJ_VERIFY_KERNEL_AUTO) kernel = W <= 8 ? MJ_VERIFY_KERNEL_DIAGONAL : MJ_VERIFY_KERNEL_WAVEFRONT;
+  if (kernel == MJ_VERIFY_KERNEL_WAVEFRONT && (lanes > 32 || (lanes <= 0 && wave_lanes_for(kmax) > 32))) {
+    // one CTA of several warps per pair
+    const int G = lanes > 0 ? lanes : cta_lanes_for(kmax);
+    if (G < cta_lanes_for(kmax) || G > kMaxCtaLanes || (G & (G - 1))) return MJ_ERR_UNSUPPORTED;
+    MJ_CUDA_TRY(cudaMemsetAsync(next, 0, sizeof(unsigned long long), s));
+    switch (G / 32) {
+      case 2: return launch_v<2>(a, PW, GW, next, s);
+      case 4: return launch_v<4>(a, PW, GW, next, s);
+      case 8: return launch_v<8>(a, PW, GW, next, s);
+      case 16: return launch_v<16>(a, PW, GW, next, s);
+      case 32: return launch_v<32>(a, PW, GW, next, s);
+      default: return MJ_ERR_UNSUPPORTED;
+    }
+  }
+  MJ_CUDA_TRY(cudaMemsetAsync(next, 0, sizeof(unsigned long long), s));
   if (kernel == MJ_VERIFY_KERNEL_WAVEFRONT) {
     const int need = wave_lanes_for(kmax);
     int G = lanes > 0 ? lanes : need;

@@ -1,6 +1,6 @@
 """One join of a synthetic workload on cuda:0, with its statistics.
 
-    python -m paper_1810_08833_gb300.join_once --config 2 [--roots 3000] [--learned]
+    python -m paper_1810_08833_gb300.join_once --config 2 [--roots 3000] [--learned] [--K K --T T]
 
 A small, self-contained invocation of the whole hot path (parameters,
 partition, candidates, verification, output), meant for profilers: it builds
@@ -29,6 +29,8 @@ def main(argv=None) -> dict:
     ap.add_argument("--learned", action="store_true")
     ap.add_argument("--no-warmup", action="store_true")
     ap.add_argument("--band-steps", type=int, default=300)
+    ap.add_argument("--K", type=int, default=None, help="threshold instead of the workload's own")
+    ap.add_argument("--T", type=int, default=None, help="partitions per string instead of the workload's own")
     args = ap.parse_args(argv)
 
     import torch
@@ -38,6 +40,11 @@ def main(argv=None) -> dict:
 
     build.build()
     s = synth.make_config(args.config, n_roots=args.roots)
+    if args.K is not None:
+        s.K = args.K
+        s.T = args.T if args.T is not None else max(1, args.K // 5)
+    elif args.T is not None:
+        s.T = args.T
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream), mj.Context(0) as ctx:
         if args.learned:

@@ -336,6 +336,9 @@ def test_verify_rejects_bad_ids(ctx):
     ed = ctx.verify(data, off, i, j, 2)
     torch.cuda.synchronize()
     assert ed.cpu().tolist() == [1, 3]
+    assert ctx.device_flags() & 1   # the out-of-range id is reported
+    ctx.verify(data, off, j[:1], i[:1], 2)
+    assert ctx.device_flags() == 0
 
 
 KERNEL_CASES = [(K, 1, 0) for K in (5, 40, 100, 255, 600)] + \
