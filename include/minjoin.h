@@ -248,6 +248,14 @@ int mj_verify(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_offsets, uin
  * mj_verify does not synchronise, so its flags are read here. */
 int mj_device_flags(mj_ctx* ctx, void* stream, uint32_t* flags);
 
+/* Failure injection for tests of the error paths (no GPU fault involved):
+ * the nth device allocation the library makes from now on, on the calling
+ * host thread, fails as if the device were out of memory (nth = 1: the next
+ * one); 0 switches the injection off.  The call that hits it returns
+ * MJ_ERR_OOM, frees nothing that it does not own and leaves its context
+ * usable; mj_destroy still releases every buffer. */
+int mj_inject_alloc_failure(int64_t nth);
+
 /* mj_verify for callers that cannot allocate device memory.  No counterpart
  * in the paper: it exists for code that may not call cudaMalloc, such as a
  * plug-in whose host application owns all device memory through its own
@@ -269,11 +277,17 @@ int mj_device_flags(mj_ctx* ctx, void* stream, uint32_t* flags);
  *    the input size, then queues the work and returns.
  *  - All calls share the one array: calls that overlap on the GPU (other
  *    streams, other threads) race and give wrong results; serialise them.
- *    Every call clears what must start at zero. */
+ *    Every call clears what must start at zero.
+ *  - A pair id >= n gives K + 1 (the pair is skipped) and sets bit 0 of the
+ *    call's device flags, kept in the same array: mj_verify_static_flags
+ *    synchronises `stream` and returns them (until the next call). */
 #define MJ_VERIFY_STATIC_SCRATCH_BYTES (16u << 20)
 #define MJ_VERIFY_STATIC_MAX_K 255u
 int mj_verify_static(const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const uint32_t* d_i,
                      const uint32_t* d_j, uint64_t m, uint32_t K, void* stream, uint32_t* d_ed);
+/* Device flags of the last mj_verify_static call on the current device (bits
+ * as in mj_device_flags); allocates nothing and synchronises `stream`. */
+int mj_verify_static_flags(void* stream, uint32_t* flags);
 
 /* The whole path (Alg. 3): *count receives the number of output pairs;
  * mj_result_copy writes them sorted by (i, j) with their edit distances.

@@ -111,6 +111,8 @@ _SIGS = {
     "mj_verify": (ctypes.c_int, [VP, VP, VP, U32, VP, VP, VP, U64, U32, VP, VP]),
     "mj_verify_static": (ctypes.c_int, [VP, VP, U32, VP, VP, U64, U32, VP, VP]),
     "mj_device_flags": (ctypes.c_int, [VP, VP, ctypes.POINTER(U32)]),
+    "mj_verify_static_flags": (ctypes.c_int, [VP, ctypes.POINTER(U32)]),
+    "mj_inject_alloc_failure": (ctypes.c_int, [ctypes.c_int64]),
     "mj_join": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, ctypes.POINTER(U64)]),
     "mj_result_copy": (ctypes.c_int, [VP, VP, VP, VP, VP]),
     "mj_join_host": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, ctypes.POINTER(U64)]),

@@ -21,6 +21,14 @@ void set_last_cuda_error(cudaError_t e, const char* expr, const char* file, int 
   snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s (%s:%d)", cudaGetErrorString(e), expr, file, line);
 }
 
+// Allocation-failure injection (mj_inject_alloc_failure): the countdown of
+// device allocations left before one fails, per host thread; 0 = off.
+static thread_local int64_t g_fail_alloc_in = 0;
+
+static bool injected_failure() {
+  return g_fail_alloc_in > 0 && --g_fail_alloc_in == 0;
+}
+
 int Buf::reserve(size_t need, cudaStream_t s) {
   if (need <= bytes && p) return MJ_OK;
   if (p) {
@@ -35,6 +43,7 @@ int Buf::reserve(size_t need, cudaStream_t s) {
     bytes = 0;
   }
   size_t alloc = need < 256 ? 256 : need + need / 8;
+  if (injected_failure()) return MJ_ERR_OOM;
   cudaError_t e = cudaMalloc(&p, alloc);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -51,6 +60,7 @@ int Buf::grow_keep(size_t need, size_t keep, cudaStream_t s) {
   const size_t old_bytes = bytes;
   const size_t alloc = need < 256 ? 256 : need + need / 8;
   void* q = nullptr;
+  if (injected_failure()) return MJ_ERR_OOM;
   cudaError_t e = cudaMalloc(&q, alloc);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1002,6 +1012,12 @@ int mj_candidates_copy(mj_ctx* c, uint32_t* d_i, uint32_t* d_j, void* stream) {
   return MJ_OK;
 }
 
+int mj_inject_alloc_failure(int64_t nth) {
+  if (nth < 0) return MJ_ERR_ARG;
+  g_fail_alloc_in = nth;
+  return MJ_OK;
+}
+
 int mj_device_flags(mj_ctx* c, void* stream, uint32_t* flags) {
   if (!c || !flags) return MJ_ERR_ARG;
   DeviceGuard g(c->device);
@@ -1132,7 +1148,7 @@ int mj_join(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_
   DeviceGuard g(c->device);
   cudaStream_t s = S(stream);
   begin_call(c, true);
-  c->have_part = c->have_cand = c->have_out = false;
+  c->have_part = c->have_cand = c->have_out = c->have_features = false;
   MJ_CUDA_TRY(cudaEventRecord(c->ev[0], s));
   MJ_TRY(derive(c, d_bytes, d_offsets, n, p, s));
   MJ_CUDA_TRY(cudaEventRecord(c->ev[1], s));

@@ -104,3 +104,19 @@ extern "C" int mj_verify_static(const uint8_t* d_bytes, const int64_t* d_offsets
   a.dev_flags = flags;
   return launch_verify(a, PW, GW, K, next, s);
 }
+
+extern "C" int mj_verify_static_flags(void* stream, uint32_t* flags) {
+  using namespace mj;
+  if (!flags) return MJ_ERR_ARG;
+  *flags = 0;
+  int dev = 0;
+  MJ_CUDA_TRY(cudaGetDevice(&dev));
+  void* scratch = nullptr;
+  MJ_TRY(scratch_address(dev, &scratch));
+  uint32_t f = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MJ_CUDA_TRY(cudaMemcpyAsync(&f, static_cast<char*>(scratch) + 64, sizeof(f), cudaMemcpyDeviceToHost, s));
+  MJ_CUDA_TRY(cudaStreamSynchronize(s));
+  *flags = f;
+  return MJ_OK;
+}
