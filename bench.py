@@ -253,7 +253,11 @@ def run_native(args):
                                     stream=stream)
         train_s = time.perf_counter() - t0
         n_train = int(x.shape[0])
-        del x, ed, tr_data, tr_off
+        del x, ed
+        # learned mode keeps the network only where it was faster than plain
+        # on the held-out instance (timed joins of both modes)
+        calibration = ctx.band_calibrate(tr_data, tr_off, learned, stream=stream)
+        del tr_data, tr_off
 
         def timed(p, steps):
             e0 = torch.cuda.Event(enable_timing=True)
@@ -323,6 +327,14 @@ def run_native(args):
 
     last = stats[-1]
     cells = int(last["band_cells"])
+    # ceiling of any first-pass gain: the band words x columns that pairs with
+    # ED <= K take at band K (they run every column of the shorter string),
+    # as a share of all the plain join's word-columns
+    L = s.lengths().astype(np.int64)
+    oi_h, oj_h = out_p[0].cpu().numpy().astype(np.int64), out_p[1].cpu().numpy().astype(np.int64)
+    words_k = (s.K + 1 + 31) // 32
+    true_wc = int((np.minimum(L[oi_h], L[oj_h]) * words_k).sum())
+    true_share = true_wc / max(1, int(stats_plain[-1]["verify_word_columns"]))
     sec_ms = {k: statistics.median([st["ms_section"][k] for st in stats]) for k in mj.SECTIONS}
     launches = int(sum(st["n_launches"] for st in stats))
 
@@ -359,6 +371,9 @@ def run_native(args):
                                       for k in mj.SECTIONS},
                 "band_training": {"samples": n_train, "steps": args.band_steps, "seconds": round(train_s, 2),
                                   "final_batch_loss": train_loss, "data": "held-out seed, a quarter of the families"},
+                "calibration": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in calibration.items()},
+                "network_runs": bool(calibration["enabled"]),
+                "true_pair_word_column_share": round(true_share, 5),
             },
             "batching": batching,
             "cells_per_step": cells_all,

@@ -355,6 +355,27 @@ int mj_band_grad(mj_ctx* ctx, const float* d_x, const float* d_y, uint64_t m, fl
                  float* d_grad, float* loss);
 int mj_band_get_weights(const mj_ctx* ctx, float* h_w, uint64_t count);
 int mj_band_set_weights(mj_ctx* ctx, const float* h_w, uint64_t count);
+/* Calibration of learned mode on a held-out instance of the workload: the
+ * join of (d_bytes, d_offsets, n) under p runs in plain mode and in learned
+ * mode (one warm-up and three timed runs each, host wall time of the whole
+ * call, median), and learned mode stays on for this context only if it was
+ * faster.  Otherwise later learned-mode joins run the plain path (same
+ * output), unless p->flags has MJ_FLAG_FIRST_PASS.  The network cannot gain
+ * where false candidates carry the verification work: no narrower band can
+ * reject a pair whose distance exceeds K, so only pairs with ED <= K can be
+ * settled sooner, while the network runs on every candidate and learned mode
+ * must sort the raw pairs to count each candidate's matched partitions.
+ * Training, initialising, loading or setting the weights clears the
+ * calibration (learned mode then runs the network).  Synchronises. */
+typedef struct {
+  float plain_ms, learned_ms;          /* median join times */
+  uint64_t plain_word_columns;         /* band words x columns the verifier advanced, plain */
+  uint64_t learned_word_columns;       /* the same in learned mode (first passes included) */
+  uint64_t first_pass_settled;         /* pairs the first passes decided */
+  uint32_t enabled;                    /* 1: learned mode runs the network from now on */
+} mj_band_calibration;
+int mj_band_calibrate(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n,
+                      const mj_params* p, void* stream, mj_band_calibration* out);
 /* Binary file: magic "MJBAND01", margin, min_multiplicity, the parameters. */
 int mj_band_save(const mj_ctx* ctx, const char* path);
 int mj_band_load(mj_ctx* ctx, const char* path);

@@ -50,6 +50,12 @@ class BandTrainParams(ctypes.Structure):
                 ("tau", ctypes.c_float), ("seed", ctypes.c_uint64)]
 
 
+class BandCalibration(ctypes.Structure):
+    _fields_ = [("plain_ms", ctypes.c_float), ("learned_ms", ctypes.c_float),
+                ("plain_word_columns", ctypes.c_uint64), ("learned_word_columns", ctypes.c_uint64),
+                ("first_pass_settled", ctypes.c_uint64), ("enabled", ctypes.c_uint32)]
+
+
 MJ_FLAG_KEY_CHECK = 1
 MJ_FLAG_FEATURES = 16
 MJ_FLAG_FIRST_PASS = 32
@@ -113,6 +119,8 @@ _SIGS = {
     "mj_device_flags": (ctypes.c_int, [VP, VP, ctypes.POINTER(U32)]),
     "mj_verify_static_flags": (ctypes.c_int, [VP, ctypes.POINTER(U32)]),
     "mj_inject_alloc_failure": (ctypes.c_int, [ctypes.c_int64]),
+    "mj_band_calibrate": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP,
+                                         ctypes.POINTER(BandCalibration)]),
     "mj_join": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, ctypes.POINTER(U64)]),
     "mj_result_copy": (ctypes.c_int, [VP, VP, VP, VP, VP]),
     "mj_join_host": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, ctypes.POINTER(U64)]),
@@ -349,6 +357,15 @@ class Context:
         _check(self._lib.mj_band_grad(self._h, _ptr(x), _ptr(y), x.shape[0], tau, _stream(stream), _ptr(g),
                                       ctypes.byref(loss)), "mj_band_grad")
         return g, loss.value
+
+    def band_calibrate(self, data, offsets, p: Params, stream=None) -> dict:
+        """Times plain and learned joins on a held-out instance and keeps
+        learned mode's network on only if it was faster (mj_band_calibrate)."""
+        n = _check_inputs(data, offsets)
+        r = BandCalibration()
+        _check(self._lib.mj_band_calibrate(self._h, _ptr(data), _ptr(offsets), n, ctypes.byref(p), _stream(stream),
+                                           ctypes.byref(r)), "mj_band_calibrate")
+        return {f: getattr(r, f) for f, _ in BandCalibration._fields_}
 
     def band_weights(self) -> np.ndarray:
         w = np.empty(BAND_PARAMS, dtype=np.float32)

@@ -7,6 +7,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <chrono>
+
 #include "mj_internal.cuh"
 
 namespace mj {
@@ -124,6 +126,8 @@ static int bits_for(uint64_t v) {  // bits needed to hold 0..v
 
 using namespace mj;
 
+constexpr int kCalibrationRuns = 3;   // timed joins per mode in mj_band_calibrate (median)
+
 struct mj_ctx {
   int device = 0;
   int sms = 152;   // streaming multiprocessors of the device
@@ -140,8 +144,10 @@ struct mj_ctx {
   Buf pair_count, pair_off, pairs, pairs_alt;
   Buf uflags, uoffs, cand_i, cand_j;
   Buf pairbm;  // pair bitmap of the candidate dedup (bit per pair i < j)
-  Buf planes, ed, eflags, eoffs;
+  Buf planes, ed;
   Buf out_i, out_j, out_ed;
+  Buf out_t;          // indices of the candidates within K, listed by the band-K pass
+  bool out_collect = false;
   Buf in_bytes, in_offsets;  // staging for mj_join_host
   uint64_t n_part = 0, n_cand = 0, n_out = 0;
   // bit-planes written by the partition kernel for the verifier
@@ -153,14 +159,17 @@ struct mj_ctx {
   Buf branges;   // bucket counts [32] then ranges [64]
   // CUDA graph of the plain verification stage
   cudaGraphExec_t graph_exec = nullptr;
-  uint64_t graph_sig[12] = {};
-  uint64_t last_sig[12] = {};
+  uint64_t graph_sig[16] = {};
+  uint64_t last_sig[16] = {};
   uint64_t graph_launches = 0;
   // learned first-pass band: parameters P, Adam moments M and V, gradient G, loss
   Buf band;
   bool band_ready = false;
   uint32_t band_margin = 0, band_min_mult = 2;
   bool band_gate_auto = false;   // set band_min_mult from the training data
+  // learned mode's calibration (mj_band_calibrate): -1 not calibrated (the
+  // network runs), 1 the network runs, 0 learned mode runs the plain path
+  int band_enabled = -1;
   int band_step = 0;
   Buf feat_x, mult, run_start, parts, yhat, kband;
   // learned first passes: bucket-sorted order, per-bucket ranges and work
@@ -422,7 +431,7 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   MJ_TRY(launch_gather_records(sidx, skeys, nr, g, c->recs.as<PRec>(), c->srec.as<PRec>(), s));
   tstop(c, 2, s);
   if (flags & MJ_FLAG_KEY_CHECK) {
-    MJ_TRY(c->small.reserve(64, s));
+    MJ_TRY(c->small.reserve(128, s));
     MJ_CUDA_TRY(cudaMemsetAsync(c->small.p, 0, 8, s));
     MJ_TRY(launch_key_check(r, d_bytes, d_offsets, nr, c->small.as<unsigned long long>(), s));
     MJ_TRY(readback(c, c->small.p, 8, s));
@@ -460,7 +469,7 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   }
   if (use_bitmap) {
     tstart(c, 4, s);
-    MJ_TRY(c->small.reserve(64, s));
+    MJ_TRY(c->small.reserve(128, s));
     MJ_TRY(launch_mark_pairs(r, nr, d.K, g, n, c->pairbm.as<uint32_t>(), c->small.as<unsigned long long>() + 7, s));
     MJ_TRY(c->uflags.reserve((size_t)n * 4, s));
     MJ_TRY(c->uoffs.reserve((size_t)n * 4 + 16, s));
@@ -515,9 +524,11 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
 int verify_prep(mj_ctx* c, cudaStream_t s) {
   MJ_TRY(c->dev_flags.reserve(64, s));
   MJ_CUDA_TRY(cudaMemsetAsync(c->dev_flags.p, 0, 64, s));
-  MJ_TRY(c->small.reserve(64, s));
+  MJ_TRY(c->small.reserve(128, s));
   if (!c->work_started) {
-    MJ_CUDA_TRY(cudaMemsetAsync(c->small.p, 0, 48, s));
+    // counters 0-5 and the output count (8) start at zero once per call;
+    // 6 and 7 hold values read back before verification starts
+    MJ_CUDA_TRY(cudaMemsetAsync(c->small.p, 0, 72, s));
     c->work_started = true;
   }
   return MJ_OK;
@@ -567,6 +578,10 @@ int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const ui
   a.cells = count_cells ? c->small.as<unsigned long long>() : nullptr;
   a.work = c->small.as<unsigned long long>() + 2;
   a.dev_flags = c->dev_flags.as<uint32_t>();
+  if (c->out_collect) {   // the join's band-K pass lists the pairs within K
+    a.out_t = c->out_t.as<uint32_t>();
+    a.out_count = c->small.as<unsigned long long>() + 8;
+  }
   tstart(c, 6, s);
   int kk = kernel >= 0 ? kernel : (int)c->vcfg.kernel;
   int ll = lanes >= 0 ? lanes : (int)c->vcfg.lanes;
@@ -579,25 +594,26 @@ int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const ui
   return MJ_OK;
 }
 
-// Longest-first order of pairs (d_i, d_j): sorted work keys and the order.
+// Longest-first order of pairs (d_i, d_j) (a counting sort of the shorter
+// lengths into c->idx), with the pairs' floor(log2) length buckets: counts in
+// branges words [0, 32), [start, end) ranges in words [32, 96).
+constexpr size_t kOrderScratchAt = 128;   // words of branges before the ordering scratch
+
+// The pairs' K-band cells are summed into small word 9 on the way.
 int pair_order(mj_ctx* c, const uint32_t* ci, const uint32_t* cj, const int64_t* d_offsets, uint64_t m,
-               const uint64_t** skeys, const uint32_t** order, cudaStream_t s) {
-  MJ_TRY(launch_work_keys(ci, cj, d_offsets, m, c->d.N, c->keys.as<uint64_t>(), c->idx.as<uint32_t>(), s));
-  bool oalt = false;
-  MJ_TRY(radix_sort_u64(c->keys.as<uint64_t>(), c->keys_alt.as<uint64_t>(), c->idx.as<uint32_t>(),
-                        c->idx_alt.as<uint32_t>(), m, 0, bits_for(c->d.N), c->sort_tmp.p, &oalt, s));
-  *skeys = oalt ? c->keys_alt.as<uint64_t>() : c->keys.as<uint64_t>();
-  *order = oalt ? c->idx_alt.as<uint32_t>() : c->idx.as<uint32_t>();
+               const uint32_t** order, cudaStream_t s) {
+  if (!c->small.p || !c->branges.p || !c->idx.p) return MJ_ERR_STATE;   // order_buffers comes first
+  uint32_t* counts = c->branges.as<uint32_t>();
+  MJ_TRY(launch_length_order(ci, cj, d_offsets, m, c->d.K, counts + kOrderScratchAt, c->idx.as<uint32_t>(), counts,
+                             counts + kLenBuckets, c->small.as<unsigned long long>() + 9, s));
+  *order = c->idx.as<uint32_t>();
   return MJ_OK;
 }
 
 int order_buffers(mj_ctx* c, uint64_t m, cudaStream_t s) {
-  MJ_TRY(c->keys.reserve(m * 8, s));
-  MJ_TRY(c->keys_alt.reserve(m * 8, s));
+  MJ_TRY(c->small.reserve(128, s));   // word 9: the band cells summed by the ordering
   MJ_TRY(c->idx.reserve(m * 4, s));
-  MJ_TRY(c->idx_alt.reserve(m * 4, s));
-  MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(m), s));
-  MJ_TRY(c->branges.reserve(4 * (kLenBuckets + 2 * kLenBuckets) + 64, s));
+  MJ_TRY(c->branges.reserve(4 * (kOrderScratchAt + kOrderScratchWords) + 64, s));
   return MJ_OK;
 }
 
@@ -605,14 +621,12 @@ int order_buffers(mj_ctx* c, uint64_t m, cudaStream_t s) {
 // context's kernel choice says (TUNED: per length bucket, batched).
 int verify_ordered(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const uint32_t* ci,
                    const uint32_t* cj, uint64_t m, uint32_t K, uint32_t* ed, cudaStream_t s) {
-  const uint64_t* skeys;
   const uint32_t* order;
-  MJ_TRY(pair_order(c, ci, cj, d_offsets, m, &skeys, &order, s));
+  MJ_TRY(pair_order(c, ci, cj, d_offsets, m, &order, s));
   if (c->vcfg.kernel != MJ_VERIFY_KERNEL_TUNED || !c->tuned)
     return verify(c, d_bytes, d_offsets, ci, cj, nullptr, m, K, K, ed, false, s, order);
   uint32_t* counts = c->branges.as<uint32_t>();
   uint32_t* ranges = counts + kLenBuckets;
-  MJ_TRY(launch_bucket_ranges(skeys, m, c->d.N, counts, ranges, s));
   if (c->vcfg.batching == 1) {
     for (int b = kLenBuckets - 1; b >= 0; --b)
       MJ_TRY(verify(c, d_bytes, d_offsets, ci, cj, nullptr, m, K, K, ed, false, s, order, nullptr, ranges + 2 * b,
@@ -646,9 +660,10 @@ int verify_ordered_graph(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_off
   if (c->tuned) {
     for (int b = 0; b < kLenBuckets; ++b) plan = plan * 1000003u + c->tuned_kernel[b] * 64u + c->tuned_lanes[b];
   }
-  const uint64_t sig[12] = {(uint64_t)d_bytes, (uint64_t)d_offsets, (uint64_t)ci, (uint64_t)cj, m, K,
+  const uint64_t sig[16] = {(uint64_t)d_bytes, (uint64_t)d_offsets, (uint64_t)ci, (uint64_t)cj, m, K,
                             (uint64_t)ed, (uint64_t)c->planes.p, c->planes_pw, c->d.bits, plan,
-                            (uint64_t)c->small.p ^ (uint64_t)c->keys.p ^ (uint64_t)c->sort_tmp.p};
+                            (uint64_t)c->small.p, (uint64_t)c->idx.p, (uint64_t)c->branges.p,
+                            (uint64_t)c->dev_flags.p, c->out_collect ? (uint64_t)c->out_t.p : 0};
   if (c->graph_exec && memcmp(sig, c->graph_sig, sizeof(sig)) == 0) {
     tstart(c, 6, s);   // the verify section spans the replay
     MJ_CUDA_TRY(cudaGraphLaunch(c->graph_exec, s));
@@ -701,7 +716,7 @@ int verify_stage(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, ui
   const uint32_t* ci = c->cand_i.as<uint32_t>();
   const uint32_t* cj = c->cand_j.as<uint32_t>();
   MJ_TRY(c->ed.reserve(m * 4, s));
-  MJ_TRY(c->small.reserve(64, s));
+  MJ_TRY(c->small.reserve(128, s));
   const bool want_x = (p->flags & MJ_FLAG_FEATURES) != 0;
   if (want_feat) {
     MJ_TRY(c->parts.reserve((size_t)n * 4 + 16, s));
@@ -715,16 +730,19 @@ int verify_stage(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, ui
                                 c->feat_x.as<float>(), s));
   }
   uint32_t* ed = c->ed.as<uint32_t>();
+  MJ_TRY(c->out_t.reserve(m * 4, s));
   if (!learned) {
     // longest pairs first, so that the persistent verifier does not end on a
     // tail of long pairs
-    MJ_TRY(verify_ordered_graph(c, d_bytes, d_offsets, ci, cj, m, K, ed, s));
+    c->out_collect = true;
+    const int st = verify_ordered_graph(c, d_bytes, d_offsets, ci, cj, m, K, ed, s);
+    c->out_collect = false;
+    MJ_TRY(st);
   } else {
     if (!c->band_ready) return MJ_ERR_STATE;
     MJ_TRY(order_buffers(c, m, s));
-    const uint64_t* skeys;
     const uint32_t* order;
-    MJ_TRY(pair_order(c, ci, cj, d_offsets, m, &skeys, &order, s));
+    MJ_TRY(pair_order(c, ci, cj, d_offsets, m, &order, s));
     MJ_TRY(c->kband.reserve(m * 4, s));
     MJ_TRY(c->lvals.reserve(m * 4 + 16, s));
     MJ_TRY(c->franges.reserve(8 * (kMaxBandBuckets + 2), s));
@@ -779,16 +797,19 @@ int verify_stage(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, ui
         MJ_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[b - 1], 0));
       }
     }
-    MJ_TRY(verify(c, d_bytes, d_offsets, ci, cj, nullptr, m, K, K, ed, false, s, order,
-                  first ? c->kband.as<uint32_t>() : nullptr, nullptr, nullptr, -1, -1, nullptr, false,
-                  first ? c->ed_first.as<uint32_t>() : nullptr));
+    c->out_collect = true;
+    const int st = verify(c, d_bytes, d_offsets, ci, cj, nullptr, m, K, K, ed, false, s, order,
+                          first ? c->kband.as<uint32_t>() : nullptr, nullptr, nullptr, -1, -1, nullptr, false,
+                          first ? c->ed_first.as<uint32_t>() : nullptr);
+    c->out_collect = false;
+    MJ_TRY(st);
     MJ_TRY(readback(c, c->small.as<unsigned long long>() + 4, 16, s));
     const uint64_t settled = c->h_small[0];
     c->stats.first_pass_settled = settled;
     c->stats.fallback_pairs = first ? c->h_small[1] - settled : 0;
   }
   c->have_features = want_x;
-  return launch_band_cells(ci, cj, d_offsets, m, K, c->small.as<unsigned long long>() + 3, s);
+  return MJ_OK;
 }
 
 // He-normal initial weights from a seeded host generator (splitmix64 +
@@ -900,7 +921,7 @@ void mj_destroy(mj_ctx* c) {
   Buf* bufs[] = {&c->hist, &c->dev_flags, &c->small, &c->bitmap, &c->tile_count, &c->tile_off, &c->scan_tmp,
                  &c->tile_first,
                  &c->recs, &c->keys, &c->keys_alt, &c->idx, &c->idx_alt, &c->sort_tmp, &c->srec, &c->pair_count, &c->pair_off, &c->pairs, &c->pairs_alt,
-                 &c->uflags, &c->uoffs, &c->cand_i, &c->cand_j, &c->pairbm, &c->planes, &c->ed, &c->eflags, &c->eoffs,
+                 &c->uflags, &c->uoffs, &c->cand_i, &c->cand_j, &c->pairbm, &c->planes, &c->ed, &c->out_t,
                  &c->out_i, &c->out_j, &c->out_ed, &c->in_bytes, &c->in_offsets, &c->branges,
                  &c->band, &c->feat_x, &c->mult, &c->run_start, &c->parts, &c->yhat, &c->kband, &c->lvals,
                  &c->franges, &c->fnext, &c->fcnt, &c->ed_first};
@@ -1044,7 +1065,7 @@ int mj_verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
     if (m) MJ_TRY(verify_ordered_graph(c, d_bytes, d_offsets, d_i, d_j, m, K, d_ed, s));
   } else {
     // the widest per-pair band sizes the kernel (a device reduction, 4 bytes read back)
-    MJ_TRY(c->small.reserve(64, s));
+    MJ_TRY(c->small.reserve(128, s));
     unsigned int* dmax = reinterpret_cast<unsigned int*>(c->small.as<unsigned long long>() + 6);
     MJ_TRY(launch_max_u32(d_k, m, dmax, s));
     MJ_TRY(readback(c, dmax, 4, s));
@@ -1094,13 +1115,11 @@ int mj_autotune_verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offse
   if (!m) return MJ_OK;
   MJ_TRY(order_buffers(c, m, s));
   MJ_TRY(c->ed.reserve(m * 4, s));
-  const uint64_t* skeys;
   const uint32_t* order;
-  MJ_TRY(pair_order(c, d_i, d_j, d_offsets, m, &skeys, &order, s));
+  MJ_TRY(pair_order(c, d_i, d_j, d_offsets, m, &order, s));
   uint32_t* counts = c->branges.as<uint32_t>();
   uint32_t* ranges = counts + kLenBuckets;
   uint32_t* trial = ranges + 2 * kLenBuckets;   // [lo, hi) of the sample being timed
-  MJ_TRY(launch_bucket_ranges(skeys, m, c->d.N, counts, ranges, s));
   uint32_t h[3 * kLenBuckets];
   MJ_CUDA_TRY(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, s));
   MJ_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1147,6 +1166,12 @@ int mj_join(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_
   if (p->verify_mode == MJ_VERIFY_LEARNED && !c->band_ready) return MJ_ERR_STATE;
   DeviceGuard g(c->device);
   cudaStream_t s = S(stream);
+  // learned mode calibrated as not paying off on this workload runs the plain
+  // path (the same output), unless the first passes are forced
+  mj_params eff = *p;
+  if (eff.verify_mode == MJ_VERIFY_LEARNED && c->band_enabled == 0 && !(eff.flags & MJ_FLAG_FIRST_PASS))
+    eff.verify_mode = MJ_VERIFY_PLAIN;
+  p = &eff;
   begin_call(c, true);
   c->have_part = c->have_cand = c->have_out = c->have_features = false;
   MJ_CUDA_TRY(cudaEventRecord(c->ev[0], s));
@@ -1163,28 +1188,28 @@ int mj_join(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_
   c->n_out = 0;
   if (m) {
     MJ_TRY(verify_stage(c, d_bytes, d_offsets, n, p, s));
-    MJ_TRY(c->eflags.reserve(m * 4, s));
-    MJ_TRY(c->eoffs.reserve(m * 4 + 16, s));
-    MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(m), s));
     tstart(c, 7, s);
-    MJ_TRY(launch_ed_flags(c->ed.as<uint32_t>(), m, p->K, c->eflags.as<uint32_t>(), s));
-    uint32_t* tot = c->eoffs.as<uint32_t>() + m;
-    MJ_TRY(launch_exclusive_scan_u32(c->eflags.as<uint32_t>(), c->eoffs.as<uint32_t>(), m, c->scan_tmp.p, tot, s));
-    MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small, tot, 4, cudaMemcpyDeviceToHost, s));
-    MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small + 1, c->small.as<unsigned long long>() + 3, 8, cudaMemcpyDeviceToHost, s));
+    MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small, c->small.as<unsigned long long>() + 8, 8, cudaMemcpyDeviceToHost, s));
+    MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small + 1, c->small.as<unsigned long long>() + 9, 8, cudaMemcpyDeviceToHost, s));
     MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small + 2, c->dev_flags.p, 4, cudaMemcpyDeviceToHost, s));
     MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small + 3, c->small.as<unsigned long long>() + 2, 8, cudaMemcpyDeviceToHost, s));
     MJ_CUDA_TRY(cudaStreamSynchronize(s));
-    const uint32_t no = *(uint32_t*)c->h_small;
+    const uint64_t no = c->h_small[0];
     c->stats.band_cells = c->h_small[1];
     c->stats.device_flags |= *(uint32_t*)(c->h_small + 2);
     c->stats.verify_word_columns = c->h_small[3];
+    if (no > m) return MJ_ERR_DEVICE;
     MJ_TRY(c->out_i.reserve((size_t)no * 4 + 16, s));
     MJ_TRY(c->out_j.reserve((size_t)no * 4 + 16, s));
     MJ_TRY(c->out_ed.reserve((size_t)no * 4 + 16, s));
-    MJ_TRY(launch_compact_output(c->cand_i.as<uint32_t>(), c->cand_j.as<uint32_t>(), c->ed.as<uint32_t>(),
-                                 c->eflags.as<uint32_t>(), c->eoffs.as<uint32_t>(), m, c->out_i.as<uint32_t>(),
-                                 c->out_j.as<uint32_t>(), c->out_ed.as<uint32_t>(), s));
+    MJ_TRY(c->keys.reserve((size_t)no * 8 + 16, s));
+    MJ_TRY(c->keys_alt.reserve((size_t)no * 8 + 16, s));
+    MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(no), s));
+    // sorted candidate indices are (i, j) order
+    MJ_TRY(launch_gather_output(c->out_t.as<uint32_t>(), no, m, c->cand_i.as<uint32_t>(), c->cand_j.as<uint32_t>(),
+                                c->ed.as<uint32_t>(), c->keys.as<uint64_t>(), c->keys_alt.as<uint64_t>(),
+                                c->sort_tmp.p, c->out_i.as<uint32_t>(), c->out_j.as<uint32_t>(),
+                                c->out_ed.as<uint32_t>(), s));
     tstop(c, 7, s);
     c->n_out = no;
   }
@@ -1227,6 +1252,7 @@ static int band_buffers(mj_ctx* c, cudaStream_t s) {
 
 int mj_band_init(mj_ctx* c, uint64_t seed, uint32_t margin, uint32_t min_multiplicity) {
   if (!c) return MJ_ERR_ARG;
+  c->band_enabled = -1;   // a new model is not calibrated
   DeviceGuard g(c->device);
   MJ_TRY(band_buffers(c, nullptr));
   std::vector<float> w(kBandParams);
@@ -1246,6 +1272,7 @@ int mj_band_train(mj_ctx* c, const float* d_x, const uint32_t* d_ed, uint64_t m,
   if (!c || !tp || (m && (!d_x || !d_ed))) return MJ_ERR_ARG;
   if (!c->band_ready) return MJ_ERR_STATE;
   if (!m || !tp->steps || !tp->batch) return MJ_ERR_ARG;
+  c->band_enabled = -1;   // the model changes: its calibration is stale
   if (tp->tau < 0.f || tp->tau >= 1.f || tp->seed == 0) return MJ_ERR_ARG;
   DeviceGuard g(c->device);
   cudaStream_t s = S(stream);
@@ -1329,6 +1356,7 @@ int mj_band_set_weights(mj_ctx* c, const float* h_w, uint64_t count) {
   if (!c || !h_w || count != (uint64_t)kBandParams) return MJ_ERR_ARG;
   DeviceGuard g(c->device);
   MJ_TRY(band_buffers(c, nullptr));
+  c->band_enabled = -1;
   MJ_CUDA_TRY(cudaMemcpy(c->band.p, h_w, sizeof(float) * kBandParams, cudaMemcpyHostToDevice));
   if (!c->band_ready) {
     MJ_CUDA_TRY(cudaMemset(c->band.as<float>() + kBandParams, 0, sizeof(float) * 2 * kBandParams));
@@ -1356,6 +1384,7 @@ int mj_band_load(mj_ctx* c, const char* path) {
   if (!c || !path) return MJ_ERR_ARG;
   FILE* f = fopen(path, "rb");
   if (!f) return MJ_ERR_ARG;
+  c->band_enabled = -1;
   char magic[8];
   uint32_t hdr[4];
   std::vector<float> w(kBandParams);
@@ -1366,6 +1395,44 @@ int mj_band_load(mj_ctx* c, const char* path) {
   MJ_TRY(mj_band_set_weights(c, w.data(), kBandParams));
   c->band_margin = hdr[2];
   c->band_min_mult = hdr[3];
+  return MJ_OK;
+}
+
+int mj_band_calibrate(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n, const mj_params* p,
+                      void* stream, mj_band_calibration* out) {
+  if (!c || !p) return MJ_ERR_ARG;
+  if (!c->band_ready) return MJ_ERR_STATE;
+  mj_band_calibration r{};
+  mj_params plain = *p, learned = *p;
+  plain.verify_mode = MJ_VERIFY_PLAIN;
+  learned.verify_mode = MJ_VERIFY_LEARNED;
+  plain.flags &= ~(uint32_t)(MJ_FLAG_FEATURES | MJ_FLAG_KEY_CHECK);
+  learned.flags &= ~(uint32_t)(MJ_FLAG_FEATURES | MJ_FLAG_KEY_CHECK);
+  c->band_enabled = 1;   // the learned runs below use the network
+  float t[2][kCalibrationRuns];
+  uint64_t count = 0;
+  for (int mode = 0; mode < 2; ++mode) {
+    const mj_params* q = mode == 0 ? &plain : &learned;
+    MJ_TRY(mj_join(c, d_bytes, d_offsets, n, q, stream, &count));   // warm-up: sizes the buffers
+    for (int k = 0; k < kCalibrationRuns; ++k) {
+      const auto t0 = std::chrono::steady_clock::now();
+      MJ_TRY(mj_join(c, d_bytes, d_offsets, n, q, stream, &count));   // returns after its stream is done
+      t[mode][k] = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (mode == 0) {
+      r.plain_word_columns = c->stats.verify_word_columns;
+    } else {
+      r.learned_word_columns = c->stats.verify_word_columns;
+      r.first_pass_settled = c->stats.first_pass_settled;
+    }
+  }
+  std::sort(t[0], t[0] + kCalibrationRuns);
+  std::sort(t[1], t[1] + kCalibrationRuns);
+  r.plain_ms = t[0][kCalibrationRuns / 2];
+  r.learned_ms = t[1][kCalibrationRuns / 2];
+  r.enabled = r.learned_ms < r.plain_ms ? 1u : 0u;
+  c->band_enabled = (int)r.enabled;
+  if (out) *out = r;
   return MJ_OK;
 }
 

@@ -319,35 +319,19 @@ __global__ void compact_pairs_kernel(const uint64_t* __restrict__ s, const uint3
   }
 }
 
-__global__ void ed_flags_kernel(const uint32_t* __restrict__ ed, uint64_t m, uint32_t K, uint32_t* __restrict__ flags) {
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (uint64_t)gridDim.x * blockDim.x)
-    flags[t] = ed[t] <= K ? 1u : 0u;
+__global__ void out_keys_kernel(const uint32_t* __restrict__ out_t, uint64_t n, uint64_t* __restrict__ keys) {
+  for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (uint64_t)gridDim.x * blockDim.x)
+    keys[u] = out_t[u];
 }
 
-__global__ void compact_out_kernel(const uint32_t* __restrict__ ci, const uint32_t* __restrict__ cj,
-                                   const uint32_t* __restrict__ ed, const uint32_t* __restrict__ flags,
-                                   const uint32_t* __restrict__ offs, uint64_t m, uint32_t* __restrict__ oi,
-                                   uint32_t* __restrict__ oj, uint32_t* __restrict__ oed) {
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (uint64_t)gridDim.x * blockDim.x) {
-    if (flags[t]) {
-      uint32_t o = offs[t];
-      oi[o] = ci[t];
-      oj[o] = cj[t];
-      oed[o] = ed[t];
-    }
-  }
-}
-
-// Work-order key of a candidate: longest pairs first (key = N - min length).
-__global__ void work_keys_kernel(const uint32_t* __restrict__ ci, const uint32_t* __restrict__ cj,
-                                 const int64_t* __restrict__ offsets, uint64_t m, uint64_t N,
-                                 uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t x = ci[t], y = cj[t];
-    const int64_t lx = offsets[x + 1] - offsets[x], ly = offsets[y + 1] - offsets[y];
-    const int64_t n = lx < ly ? lx : ly;
-    keys[t] = N - (uint64_t)n;
-    vals[t] = (uint32_t)t;
+__global__ void gather_out_kernel(const uint64_t* __restrict__ keys, uint64_t n, const uint32_t* __restrict__ ci,
+                                  const uint32_t* __restrict__ cj, const uint32_t* __restrict__ ed,
+                                  uint32_t* __restrict__ oi, uint32_t* __restrict__ oj, uint32_t* __restrict__ oed) {
+  for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t t = keys[u];
+    oi[u] = ci[t];
+    oj[u] = cj[t];
+    oed[u] = ed[t];
   }
 }
 
@@ -431,48 +415,137 @@ __global__ void band_bucket_scatter_kernel(const uint32_t* __restrict__ kband, u
   }
 }
 
-// K-band cells of every candidate, summed (mj_stats.band_cells).
-__global__ void band_cells_kernel(const uint32_t* __restrict__ ci, const uint32_t* __restrict__ cj,
+
+// ---- verification order: longest pairs first, by a counting sort of the
+// pairs' shorter lengths n over 256 length classes: n itself below 8, else
+// floor(log2 n) and the next three bits.  Classes are monotone in n, and the
+// pairs of one floor(log2 n) bucket (the autotuner's unit) are a run of
+// consecutive classes.  Order within a class is arbitrary.
+constexpr int kOrderClasses = 256;
+
+__device__ __forceinline__ uint32_t length_class(uint64_t n) {
+  if (n < 8) return (uint32_t)n;
+  const uint32_t e = 63u - (uint32_t)__clzll(n);   // >= 3
+  return (e - 2u) * 8u + (uint32_t)((n >> (e - 3u)) & 7u);
+}
+
+__device__ __forceinline__ uint64_t pair_min_length(const uint32_t* __restrict__ ci, const uint32_t* __restrict__ cj,
+                                                    const int64_t* __restrict__ offsets, uint64_t t) {
+  const uint32_t x = ci[t], y = cj[t];
+  const int64_t lx = __ldg(offsets + x + 1) - __ldg(offsets + x), ly = __ldg(offsets + y + 1) - __ldg(offsets + y);
+  return (uint64_t)(lx < ly ? lx : ly);
+}
+
+__device__ __forceinline__ uint64_t band_cells_of(int64_t m, int64_t n, int64_t K) {   // m >= n
+  if (n <= 0) return 0;
+  int64_t a = m - K;
+  a = a < 0 ? 0 : (a > n ? n : a);
+  const int64_t smin = a * (a + 1) / 2 + a * K + (n - a) * m;
+  const int64_t b = K < n ? K : n;
+  const int64_t smax = b + (n > K ? (n - K) * (n - K + 1) / 2 : 0);
+  return (uint64_t)(smin - smax + n);
+}
+
+// Class histogram of the pairs; with cells non-null also their K-band cells
+// (mj_stats.band_cells), summed.
+__global__ void order_hist_kernel(const uint32_t* __restrict__ ci, const uint32_t* __restrict__ cj,
                                   const int64_t* __restrict__ offsets, uint64_t m, uint32_t K,
-                                  unsigned long long* __restrict__ out) {
+                                  uint32_t* __restrict__ hist, unsigned long long* __restrict__ cells) {
+  __shared__ uint32_t h[kOrderClasses];
+  for (int c = threadIdx.x; c < kOrderClasses; c += blockDim.x) h[c] = 0;
+  __syncthreads();
   unsigned long long acc = 0;
-  for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < m; u += (uint64_t)gridDim.x * blockDim.x) {
-    const int64_t lx = offsets[ci[u] + 1] - offsets[ci[u]], ly = offsets[cj[u] + 1] - offsets[cj[u]];
-    const int64_t mm = lx > ly ? lx : ly, n = lx > ly ? ly : lx;
-    if (n <= 0) continue;
-    int64_t a = mm - (int64_t)K;
-    a = a < 0 ? 0 : (a > n ? n : a);
-    const int64_t smin = a * (a + 1) / 2 + a * (int64_t)K + (n - a) * mm;
-    const int64_t b = (int64_t)K < n ? (int64_t)K : n;
-    const int64_t smax = b + (n > (int64_t)K ? (n - (int64_t)K) * (n - (int64_t)K + 1) / 2 : 0);
-    acc += (unsigned long long)(smin - smax + n);
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t x = ci[t], y = cj[t];
+    const int64_t lx = __ldg(offsets + x + 1) - __ldg(offsets + x), ly = __ldg(offsets + y + 1) - __ldg(offsets + y);
+    const int64_t n = lx < ly ? lx : ly, mm = lx < ly ? ly : lx;
+    atomicAdd(&h[length_class((uint64_t)n)], 1u);
+    if (cells) acc += band_cells_of(mm, n, K);
   }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
-}
-
-__device__ __forceinline__ uint32_t len_bucket(uint64_t n) { return n <= 1 ? 0u : 63u - (uint32_t)__clzll(n); }
-
-__global__ void bucket_hist_kernel(const uint64_t* __restrict__ keys, uint64_t m, uint64_t N,
-                                   uint32_t* __restrict__ counts) {
-  __shared__ uint32_t h[kLenBuckets];
-  if (threadIdx.x < kLenBuckets) h[threadIdx.x] = 0;
-  __syncthreads();
-  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t b = len_bucket(N - keys[q]);
-    atomicAdd(&h[b < kLenBuckets ? b : kLenBuckets - 1], 1u);
+  if (cells) {
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(cells, acc);
   }
   __syncthreads();
-  if (threadIdx.x < kLenBuckets && h[threadIdx.x]) atomicAdd(&counts[threadIdx.x], h[threadIdx.x]);
+  for (int c = threadIdx.x; c < kOrderClasses; c += blockDim.x)
+    if (h[c]) atomicAdd(hist + c, h[c]);
 }
 
-// longest first: bucket b starts after all pairs of the buckets above it
-__global__ void bucket_scan_kernel(const uint32_t* __restrict__ counts, uint32_t* __restrict__ ranges) {
-  uint32_t run = 0;
-  for (int b = kLenBuckets - 1; b >= 0; --b) {
-    ranges[2 * b] = run;
-    run += counts[b];
-    ranges[2 * b + 1] = run;
+// cursor[c] = start of class c in the longest-first order; counts[b] and
+// ranges[2b], ranges[2b+1] = the pairs and [start, end) of floor(log2)
+// bucket b (n <= 1 in bucket 0).  One block of kOrderClasses threads.
+__global__ void order_scan_kernel(const uint32_t* __restrict__ hist, uint32_t* __restrict__ cursor,
+                                  uint32_t* __restrict__ counts, uint32_t* __restrict__ ranges) {
+  __shared__ uint32_t v[kOrderClasses];
+  const int c = threadIdx.x;
+  // exclusive scan over classes in descending order
+  v[c] = hist[kOrderClasses - 1 - c];
+  __syncthreads();
+  for (int o = 1; o < kOrderClasses; o <<= 1) {
+    const uint32_t y = c >= o ? v[c - o] : 0u;
+    __syncthreads();
+    v[c] += y;
+    __syncthreads();
+  }
+  const int cls = kOrderClasses - 1 - c;
+  const uint32_t end = v[c], start = end - hist[cls];
+  cursor[cls] = start;
+  __syncthreads();
+  if (c < kLenBuckets) {
+    // classes of bucket b: n in [2^b, 2^(b+1)) (b = 0: n <= 1)
+    const int b = c;
+    int lo, hi;   // classes [lo, hi]
+    if (b == 0) { lo = 0; hi = 1; }
+    else if (b == 1) { lo = 2; hi = 3; }
+    else if (b == 2) { lo = 4; hi = 7; }
+    else { lo = (b - 2) * 8; hi = lo + 7; }
+    // longest first: class hi comes first; the bucket spans [cursor[hi], cursor[lo] + hist[lo])
+    uint32_t cnt = 0;
+    for (int k = lo; k <= hi; ++k) cnt += hist[k];
+    counts[b] = cnt;
+    ranges[2 * b] = cursor[hi];
+    ranges[2 * b + 1] = cursor[hi] + cnt;
+  }
+}
+
+// Scatter into the order, a chunk of kOrderThreads * kOrderItems pairs per
+// block step: ranks within the chunk from shared-memory counters, then one
+// global reservation per class and chunk.
+constexpr int kOrderThreads = 256;
+constexpr int kOrderItems = 16;
+
+__global__ void __launch_bounds__(kOrderThreads) order_scatter_kernel(const uint32_t* __restrict__ ci,
+                                                                     const uint32_t* __restrict__ cj,
+                                                                     const int64_t* __restrict__ offsets, uint64_t m,
+                                                                     uint32_t* __restrict__ cursor,
+                                                                     uint32_t* __restrict__ order) {
+  __shared__ uint32_t h[kOrderClasses];
+  __shared__ uint32_t base[kOrderClasses];
+  constexpr uint64_t kChunk = (uint64_t)kOrderThreads * kOrderItems;
+  const uint64_t chunks = (m + kChunk - 1) / kChunk;
+  for (uint64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
+    for (int c = threadIdx.x; c < kOrderClasses; c += kOrderThreads) h[c] = 0;
+    __syncthreads();
+    uint32_t cls[kOrderItems], rank[kOrderItems];
+#pragma unroll
+    for (int k = 0; k < kOrderItems; ++k) {
+      const uint64_t t = ch * kChunk + (uint64_t)k * kOrderThreads + threadIdx.x;
+      cls[k] = 0xffffffffu;
+      if (t < m) {
+        cls[k] = length_class(pair_min_length(ci, cj, offsets, t));
+        rank[k] = atomicAdd(&h[cls[k]], 1u);
+      }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < kOrderClasses; c += kOrderThreads)
+      if (h[c]) base[c] = atomicAdd(cursor + c, h[c]);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kOrderItems; ++k) {
+      const uint64_t t = ch * kChunk + (uint64_t)k * kOrderThreads + threadIdx.x;
+      if (cls[k] != 0xffffffffu) order[base[cls[k]] + rank[k]] = (uint32_t)t;
+    }
+    __syncthreads();
   }
 }
 
@@ -609,23 +682,26 @@ int launch_compact_pairs(const uint64_t* sorted, const uint32_t* flags, const ui
   return MJ_OK;
 }
 
-int launch_bucket_ranges(const uint64_t* sorted_keys, uint64_t m, uint64_t N, uint32_t* counts, uint32_t* ranges,
-                         cudaStream_t s) {
-  MJ_CUDA_TRY(cudaMemsetAsync(counts, 0, kLenBuckets * sizeof(uint32_t), s));
+int launch_length_order(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m, uint32_t K,
+                        uint32_t* scratch, uint32_t* order, uint32_t* counts, uint32_t* ranges,
+                        unsigned long long* cells, cudaStream_t s) {
+  uint32_t* hist = scratch;
+  uint32_t* cursor = scratch + kOrderClasses;
+  MJ_CUDA_TRY(cudaMemsetAsync(hist, 0, kOrderClasses * sizeof(uint32_t), s));
+  if (cells) MJ_CUDA_TRY(cudaMemsetAsync(cells, 0, sizeof(unsigned long long), s));
   if (m) {
-    bucket_hist_kernel<<<grid_for(m), 256, 0, s>>>(sorted_keys, m, N, counts);
+    order_hist_kernel<<<grid_for(m), 256, 0, s>>>(ci, cj, offsets, m, K, hist, cells);
     MJ_KERNEL_DONE();
   }
-  bucket_scan_kernel<<<1, 1, 0, s>>>(counts, ranges);
+  order_scan_kernel<<<1, kOrderClasses, 0, s>>>(hist, cursor, counts, ranges);
   MJ_KERNEL_DONE();
-  return MJ_OK;
-}
-
-int launch_work_keys(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m, uint64_t N,
-                     uint64_t* keys, uint32_t* vals, cudaStream_t s) {
-  if (!m) return MJ_OK;
-  work_keys_kernel<<<grid_for(m), 256, 0, s>>>(ci, cj, offsets, m, N, keys, vals);
-  MJ_KERNEL_DONE();
+  if (m) {
+    const uint64_t chunks = (m + (uint64_t)kOrderThreads * kOrderItems - 1) / ((uint64_t)kOrderThreads * kOrderItems);
+    const uint64_t cap = (uint64_t)kNumSMsHint * 8;
+    order_scatter_kernel<<<(unsigned)(chunks < cap ? chunks : cap), kOrderThreads, 0, s>>>(ci, cj, offsets, m, cursor,
+                                                                                            order);
+    MJ_KERNEL_DONE();
+  }
   return MJ_OK;
 }
 
@@ -663,27 +739,18 @@ int launch_band_buckets(const uint32_t* kband, uint64_t m, uint32_t K, uint32_t 
   return MJ_OK;
 }
 
-int launch_band_cells(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m, uint32_t K,
-                      unsigned long long* out, cudaStream_t s) {
-  MJ_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(unsigned long long), s));
-  if (!m) return MJ_OK;
-  band_cells_kernel<<<grid_for(m), 256, 0, s>>>(ci, cj, offsets, m, K, out);
-  MJ_KERNEL_DONE();
-  return MJ_OK;
-}
 
-int launch_ed_flags(const uint32_t* ed, uint64_t m, uint32_t K, uint32_t* flags, cudaStream_t s) {
-  if (!m) return MJ_OK;
-  ed_flags_kernel<<<grid_for(m), 256, 0, s>>>(ed, m, K, flags);
+int launch_gather_output(const uint32_t* out_t, uint64_t n, uint64_t m, const uint32_t* ci, const uint32_t* cj,
+                         const uint32_t* ed, uint64_t* keys, uint64_t* keys_alt, void* temp, uint32_t* oi,
+                         uint32_t* oj, uint32_t* oed, cudaStream_t s) {
+  if (!n) return MJ_OK;
+  out_keys_kernel<<<grid_for(n), 256, 0, s>>>(out_t, n, keys);
   MJ_KERNEL_DONE();
-  return MJ_OK;
-}
-
-int launch_compact_output(const uint32_t* ci, const uint32_t* cj, const uint32_t* ed, const uint32_t* flags,
-                          const uint32_t* offs, uint64_t m, uint32_t* oi, uint32_t* oj, uint32_t* oed,
-                          cudaStream_t s) {
-  if (!m) return MJ_OK;
-  compact_out_kernel<<<grid_for(m), 256, 0, s>>>(ci, cj, ed, flags, offs, m, oi, oj, oed);
+  int bits = 1;
+  while (bits < 64 && ((m - 1) >> bits)) ++bits;
+  bool alt = false;
+  MJ_TRY(radix_sort_u64(keys, keys_alt, nullptr, nullptr, n, 0, bits, temp, &alt, s));
+  gather_out_kernel<<<grid_for(n), 256, 0, s>>>(alt ? keys_alt : keys, n, ci, cj, ed, oi, oj, oed);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }

@@ -204,26 +204,28 @@ struct RankTable {
   uint8_t r[256];
 };
 struct VerifyArgs {
-  const uint32_t* planes;    // bit-planes of rank codes: plane p at planes + p * plane_words
+  const uint32_t* planes = nullptr;    // bit-planes of rank codes: plane p at planes + p * plane_words
   uint32_t bits;
-  const uint8_t* bytes;
-  const int64_t* offsets;
+  const uint8_t* bytes = nullptr;
+  const int64_t* offsets = nullptr;
   uint32_t n_strings;        // pair ids >= n_strings are rejected (flagged, ed = k + 1)
-  const uint32_t* pi;
-  const uint32_t* pj;
-  const uint32_t* pk;        // nullable per-pair band
-  const uint32_t* order;     // nullable: pair indices in the order to verify them
-  const uint32_t* skip_kband; // nullable: skip pair t when fed[t] <= skip_kband[t] < K (already settled)
-  const uint32_t* first_ed;  // nullable: first-pass results fed (else ed itself); a skipped pair copies fed[t] to ed[t]
-  const uint32_t* range_lo;  // nullable: with range_hi, process order positions [*range_lo, *range_hi) only
-  const uint32_t* range_hi;
-  unsigned long long* skipped; // nullable: number of pairs skipped that way
+  const uint32_t* pi = nullptr;
+  const uint32_t* pj = nullptr;
+  const uint32_t* pk = nullptr;        // nullable per-pair band
+  const uint32_t* order = nullptr;     // nullable: pair indices in the order to verify them
+  const uint32_t* skip_kband = nullptr; // nullable: skip pair t when fed[t] <= skip_kband[t] < K (already settled)
+  const uint32_t* first_ed = nullptr;  // nullable: first-pass results fed (else ed itself); a skipped pair copies fed[t] to ed[t]
+  const uint32_t* range_lo = nullptr;  // nullable: with range_hi, process order positions [*range_lo, *range_hi) only
+  const uint32_t* range_hi = nullptr;
+  unsigned long long* skipped = nullptr; // nullable: number of pairs skipped that way
   uint32_t K;
   uint64_t m;
-  uint32_t* ed;
-  unsigned long long* cells; // nullable: K-band cells accumulated
-  unsigned long long* work;  // nullable: word-columns processed (columns x W) accumulated
-  uint32_t* dev_flags;
+  uint32_t* ed = nullptr;
+  unsigned long long* cells = nullptr; // nullable: K-band cells accumulated
+  unsigned long long* work = nullptr;  // nullable: word-columns processed (columns x W) accumulated
+  uint32_t* dev_flags = nullptr;
+  uint32_t* out_t = nullptr;           // nullable: indices of the pairs with result <= K, appended (order arbitrary)
+  unsigned long long* out_count = nullptr;
 };
 int verify_words_for(uint32_t kmax);
 inline uint32_t plane_guard_words(uint32_t kmax) { return kmax / 64 + (uint32_t)verify_words_for(kmax) + 4; }
@@ -240,16 +242,18 @@ constexpr int kMaxCtaLanes = 1024;
 int cta_lanes_for(uint32_t kmax);
 int fewest_lanes_for(uint32_t kmax);
 
-// length buckets of the verification order (bucket of a pair: floor(log2 of
-// its shorter length), 0..31); keys are the sorted work keys N - n, so the
-// buckets are contiguous, longest first.  ranges[2b], ranges[2b+1] = [start,
-// end) of bucket b.
+// Verification order: pair indices longest first (by the shorter length), a
+// counting sort over 256 length classes; within a class the order is
+// arbitrary.  counts[b] and ranges[2b], ranges[2b+1] = [start, end) of the
+// pairs whose shorter length has floor(log2) = b (lengths 0 and 1: b = 0),
+// the autotuner's length buckets, contiguous and longest first.  scratch:
+// kOrderScratchWords words.
 constexpr int kLenBuckets = 32;
-int launch_bucket_ranges(const uint64_t* sorted_keys, uint64_t m, uint64_t N, uint32_t* counts, uint32_t* ranges,
-                         cudaStream_t s);
-// verification order: candidate indices sorted by key = N - min length
-int launch_work_keys(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m, uint64_t N,
-                     uint64_t* keys, uint32_t* vals, cudaStream_t s);
+constexpr int kOrderScratchWords = 512;
+// cells (nullable): set to the pairs' K-band cells (mj_stats.band_cells).
+int launch_length_order(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m, uint32_t K,
+                        uint32_t* scratch, uint32_t* order, uint32_t* counts, uint32_t* ranges,
+                        unsigned long long* cells, cudaStream_t s);
 
 // ---- learned first-pass band (MLP 8 -> 64 -> 64 -> 1)
 // features of a candidate (i, j), n = min length, d0 = length difference,
@@ -289,14 +293,12 @@ int launch_partition_counts(const PRec* recs, uint64_t n_rec, uint32_t n, uint32
 constexpr uint32_t kMaxBandBuckets = 16;
 int launch_band_buckets(const uint32_t* kband, uint64_t m, uint32_t K, uint32_t nb, uint32_t* cnt, uint32_t* ranges,
                         uint32_t* list, unsigned long long* first_total, cudaStream_t s);
-// K-band cells of every candidate, summed into *out
-int launch_band_cells(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m, uint32_t K,
-                      unsigned long long* out, cudaStream_t s);
 
-// output compaction (ED <= K)
-int launch_ed_flags(const uint32_t* ed, uint64_t m, uint32_t K, uint32_t* flags, cudaStream_t s);
-int launch_compact_output(const uint32_t* ci, const uint32_t* cj, const uint32_t* ed, const uint32_t* flags,
-                          const uint32_t* offs, uint64_t m, uint32_t* oi, uint32_t* oj, uint32_t* oed,
-                          cudaStream_t s);
+// output of the join: the listed pair indices (sorted ascending, which is
+// (i, j) order since the candidates are sorted) gathered into (i, j, ED);
+// keys/keys_alt: 8 * n bytes each, temp: radix_temp_bytes(n)
+int launch_gather_output(const uint32_t* out_t, uint64_t n, uint64_t m, const uint32_t* ci, const uint32_t* cj,
+                         const uint32_t* ed, uint64_t* keys, uint64_t* keys_alt, void* temp, uint32_t* oi,
+                         uint32_t* oj, uint32_t* oed, cudaStream_t s);
 
 }  // namespace mj

@@ -83,6 +83,14 @@ __global__ void build_planes_kernel(const uint8_t* __restrict__ bytes, uint64_t 
   }
 }
 
+// Result of pair t: ed[t] = v; a pair within the join's threshold (v <= K)
+// is also listed in out_t (when given), so the join's output needs no pass
+// over all candidates.
+__device__ __forceinline__ void put_result(const VerifyArgs& a, uint64_t t, uint32_t v) {
+  a.ed[t] = v;
+  if (a.out_t && v <= a.K) a.out_t[atomicAdd(a.out_count, 1ull)] = (uint32_t)t;
+}
+
 // Number of cells (i, j), 1 <= i <= m, 1 <= j <= n, with |i - j| <= K (m >= n).
 __device__ __forceinline__ uint64_t band_cells(int64_t m, int64_t n, int64_t K) {
   if (n <= 0 || m <= 0) return 0;
@@ -391,7 +399,7 @@ __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t
           // stays idle and fetches again at the next iteration
           const uint32_t* fed = a.first_ed ? a.first_ed : a.ed;
           const bool settled = a.skip_kband && a.skip_kband[t] < a.K && fed[t] <= a.skip_kband[t];
-          if (settled && a.first_ed) a.ed[t] = fed[t];
+          if (settled && a.first_ed) put_result(a, t, fed[t]);
           nskip += settled ? 1 : 0;
           if (!settled) {
             if (a.cells) {
@@ -406,7 +414,7 @@ __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t
             if (pair_init<W, P>(st, a, GW, t, &res)) {
               active = true;
             } else {
-              a.ed[t] = res;
+              put_result(a, t, res);
             }
           }
         }
@@ -419,7 +427,7 @@ __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t
       const bool done = pair_chunk<W, P>(st, a, PW, &res);
       work += (uint64_t)(st.j - j_before) * W;
       if (done) {
-        a.ed[st.t] = res;
+        put_result(a, st.t, res);
         active = false;
       }
     }
@@ -587,7 +595,7 @@ __global__ void __launch_bounds__(128, P <= 2 ? 8 : 1) verify_wave_kernel(Verify
           const uint32_t* fed = a.first_ed ? a.first_ed : a.ed;
           const bool skip = a.skip_kband && a.skip_kband[t] < a.K && fed[t] <= a.skip_kband[t];
           if (skip) {
-            if (a.first_ed && gl == 0) a.ed[t] = fed[t];
+            if (a.first_ed && gl == 0) put_result(a, t, fed[t]);
             res = 0xfffffffeu;   // settled by the first pass: nothing to do
           } else if (x >= a.n_strings || y >= a.n_strings) {
             if (gl == 0) atomicOr(a.dev_flags, FLAG_BOUNDS);
@@ -624,7 +632,7 @@ __global__ void __launch_bounds__(128, P <= 2 ? 8 : 1) verify_wave_kernel(Verify
           if (res == 0xfffffffeu) {
             if (gl == 0) ++nskip;
           } else if (res != 0xffffffffu) {
-            if (gl == 0) a.ed[t] = res;
+            if (gl == 0) put_result(a, t, res);
           } else {
             has = true;
           }
@@ -693,12 +701,12 @@ __global__ void __launch_bounds__(128, P <= 2 ? 8 : 1) verify_wave_kernel(Verify
       const int32_t fin = __shfl_sync(0xffffffffu, result, src);
       bool end = false;
       if (has && (dmask || rmask)) {
-        if (gl == 0) a.ed[t] = rmask ? k + 1 : (fin > (int32_t)k ? k + 1 : (uint32_t)fin);
+        if (gl == 0) put_result(a, t, rmask ? k + 1 : (fin > (int32_t)k ? k + 1 : (uint32_t)fin));
         end = true;
       } else if (overrun) {
         if (gl == 0) {
           atomicOr(a.dev_flags, FLAG_BOUNDS);
-          a.ed[t] = k + 1;
+          put_result(a, t, k + 1);
         }
         end = true;
       }
@@ -810,13 +818,13 @@ __global__ void __launch_bounds__(32 * V) verify_cta_kernel(VerifyArgs a, uint64
         const uint32_t kt = a.pk ? a.pk[t] : a.K;
         const uint32_t* fed = a.first_ed ? a.first_ed : a.ed;
         if (a.skip_kband && a.skip_kband[t] < a.K && fed[t] <= a.skip_kband[t]) {
-          if (a.first_ed) a.ed[t] = fed[t];
+          if (a.first_ed) put_result(a, t, fed[t]);
           ++nskip;
           continue;
         }
         if (x >= a.n_strings || y >= a.n_strings) {
           atomicOr(a.dev_flags, FLAG_BOUNDS);
-          a.ed[t] = kt + 1;
+          put_result(a, t, kt + 1);
           continue;
         }
         const int64_t lx = __ldg(a.offsets + x + 1) - __ldg(a.offsets + x);
@@ -825,15 +833,15 @@ __global__ void __launch_bounds__(32 * V) verify_cta_kernel(VerifyArgs a, uint64
         if (a.cells) cells += band_cells(mm, nn, a.K);
         if (mm >= (int64_t)kMaxLen) {
           atomicOr(a.dev_flags, FLAG_LENGTH);
-          a.ed[t] = kt + 1;
+          put_result(a, t, kt + 1);
           continue;
         }
         if (mm - nn > (int64_t)kt) {
-          a.ed[t] = kt + 1;
+          put_result(a, t, kt + 1);
           continue;
         }
         if (nn == 0) {
-          a.ed[t] = (uint32_t)mm;
+          put_result(a, t, (uint32_t)mm);
           continue;
         }
         got = t;
@@ -927,12 +935,12 @@ __global__ void __launch_bounds__(32 * V) verify_cta_kernel(VerifyArgs a, uint64
       if (f || overrun) {
         if (tid == 0) {
           if (f & 1) {
-            a.ed[t] = fin > (int32_t)k ? k + 1 : (uint32_t)fin;
+            put_result(a, t, fin > (int32_t)k ? k + 1 : (uint32_t)fin);
           } else if (f & 2) {
-            a.ed[t] = k + 1;
+            put_result(a, t, k + 1);
           } else {
             atomicOr(a.dev_flags, FLAG_BOUNDS);
-            a.ed[t] = k + 1;
+            put_result(a, t, k + 1);
           }
         }
         if (u >= 0 && u <= span) work += (uint64_t)(u + 1);   // block cut short by the exit

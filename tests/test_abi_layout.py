@@ -20,6 +20,7 @@ PAIRS = {   # C struct -> binding class
     "mj_verify_config": "VerifyConfig",
     "mj_autotune_report": "AutotuneReport",
     "mj_stats": "Stats",
+    "mj_band_calibration": "BandCalibration",
 }
 
 

@@ -157,3 +157,34 @@ def test_learned_join_equals_plain_and_gains(ctx, cfg, roots):
     if cfg != 2:   # K = 100: pairs within K are rare in this workload
         assert learned["first_pass_settled"] > 0
         assert learned["verify_word_columns"] < plain["verify_word_columns"], (learned, plain)
+
+
+def test_calibration_gates_learned_mode(ctx):
+    """mj_band_calibrate times both modes on a held-out instance and keeps the
+    network only if learned mode was faster; either way the learned join
+    returns the plain output, and forcing the first passes still runs them."""
+    import paper_1810_08833_gb300 as mj
+    train_band(ctx, 4, 300, seed=104, steps=500)
+    cal_set = synth.make_config(4, seed=204, n_roots=300)
+    cd, co = to_device(cal_set)
+    rep = ctx.band_calibrate(cd, co, mj.params(cal_set.K, T=cal_set.T))
+    assert rep["enabled"] == (1 if rep["learned_ms"] < rep["plain_ms"] else 0)
+    assert rep["plain_ms"] > 0 and rep["learned_ms"] > 0
+    assert rep["learned_word_columns"] <= rep["plain_word_columns"] + rep["plain_word_columns"] // 2
+    s = synth.make_config(4, n_roots=300)
+    data, off = to_device(s)
+    want = [t.cpu().numpy() for t in ctx.join(data, off, mj.params(s.K, T=s.T))]
+    got = [t.cpu().numpy() for t in ctx.join(data, off, mj.params(s.K, T=s.T, verify_mode=mj.MJ_VERIFY_LEARNED))]
+    for a, b in zip(want, got):
+        assert np.array_equal(a, b)
+    if not rep["enabled"]:
+        assert ctx.stats()["first_pass_settled"] == 0   # the plain path ran
+    forced = [t.cpu().numpy() for t in ctx.join(data, off, mj.params(s.K, T=s.T, verify_mode=mj.MJ_VERIFY_LEARNED,
+                                                                      flags=mj.MJ_FLAG_FIRST_PASS))]
+    assert ctx.stats()["first_pass_settled"] > 0
+    for a, b in zip(want, forced):
+        assert np.array_equal(a, b)
+    # a new model clears the calibration: the network runs again
+    ctx.band_set_weights(ctx.band_weights())
+    ctx.join(data, off, mj.params(s.K, T=s.T, verify_mode=mj.MJ_VERIFY_LEARNED, flags=mj.MJ_FLAG_FIRST_PASS))
+    assert ctx.stats()["first_pass_settled"] > 0
