@@ -148,6 +148,8 @@ struct mj_ctx {
   Buf out_i, out_j, out_ed;
   Buf out_t;          // indices of the candidates within K, listed by the band-K pass
   bool out_collect = false;
+  Buf geo;            // pair geometry at the verification order's positions (uint4)
+  bool geo_valid = false;
   Buf in_bytes, in_offsets;  // staging for mj_join_host
   uint64_t n_part = 0, n_cand = 0, n_out = 0;
   // bit-planes written by the partition kernel for the verifier
@@ -159,8 +161,8 @@ struct mj_ctx {
   Buf branges;   // bucket counts [32] then ranges [64]
   // CUDA graph of the plain verification stage
   cudaGraphExec_t graph_exec = nullptr;
-  uint64_t graph_sig[16] = {};
-  uint64_t last_sig[16] = {};
+  uint64_t graph_sig[17] = {};
+  uint64_t last_sig[17] = {};
   uint64_t graph_launches = 0;
   // learned first-pass band: parameters P, Adam moments M and V, gradient G, loss
   Buf band;
@@ -228,6 +230,7 @@ void tstop(mj_ctx* c, int i, cudaStream_t s) {
 
 void begin_call(mj_ctx* c, bool timing) {
   c->stats = mj_stats{};
+  c->geo_valid = false;
   c->planes_ready = false;
   c->work_started = false;
   c->timing = timing;
@@ -416,6 +419,7 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   g.hash_bits = std::min(32, 8 * sort_passes - low_bits);
   MJ_TRY(c->keys.reserve((size_t)nr * 8, s));
   MJ_TRY(c->keys_alt.reserve((size_t)nr * 8, s));
+  c->geo_valid = false;   // c->idx is reused by the record sort
   MJ_TRY(c->idx.reserve((size_t)nr * 4, s));
   MJ_TRY(c->idx_alt.reserve((size_t)nr * 4, s));
   MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(nr), s));
@@ -578,6 +582,7 @@ int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const ui
   a.cells = count_cells ? c->small.as<unsigned long long>() : nullptr;
   a.work = c->small.as<unsigned long long>() + 2;
   a.dev_flags = c->dev_flags.as<uint32_t>();
+  if (order && order == c->idx.as<uint32_t>() && c->geo_valid) a.pair_geo = c->geo.as<uint4>();
   if (c->out_collect) {   // the join's band-K pass lists the pairs within K
     a.out_t = c->out_t.as<uint32_t>();
     a.out_count = c->small.as<unsigned long long>() + 8;
@@ -602,17 +607,20 @@ constexpr size_t kOrderScratchAt = 128;   // words of branges before the orderin
 // The pairs' K-band cells are summed into small word 9 on the way.
 int pair_order(mj_ctx* c, const uint32_t* ci, const uint32_t* cj, const int64_t* d_offsets, uint64_t m,
                const uint32_t** order, cudaStream_t s) {
-  if (!c->small.p || !c->branges.p || !c->idx.p) return MJ_ERR_STATE;   // order_buffers comes first
+  if (!c->small.p || !c->branges.p || !c->idx.p || !c->geo.p) return MJ_ERR_STATE;   // order_buffers comes first
   uint32_t* counts = c->branges.as<uint32_t>();
-  MJ_TRY(launch_length_order(ci, cj, d_offsets, m, c->d.K, counts + kOrderScratchAt, c->idx.as<uint32_t>(), counts,
-                             counts + kLenBuckets, c->small.as<unsigned long long>() + 9, s));
+  MJ_TRY(launch_length_order(ci, cj, d_offsets, (uint32_t)c->stats.n_strings, m, c->d.K, counts + kOrderScratchAt,
+                             c->idx.as<uint32_t>(), c->geo.as<uint4>(), counts, counts + kLenBuckets,
+                             c->small.as<unsigned long long>() + 9, s));
   *order = c->idx.as<uint32_t>();
+  c->geo_valid = true;   // c->geo matches the order in c->idx
   return MJ_OK;
 }
 
 int order_buffers(mj_ctx* c, uint64_t m, cudaStream_t s) {
   MJ_TRY(c->small.reserve(128, s));   // word 9: the band cells summed by the ordering
   MJ_TRY(c->idx.reserve(m * 4, s));
+  MJ_TRY(c->geo.reserve(m * 16, s));
   MJ_TRY(c->branges.reserve(4 * (kOrderScratchAt + kOrderScratchWords) + 64, s));
   return MJ_OK;
 }
@@ -660,10 +668,10 @@ int verify_ordered_graph(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_off
   if (c->tuned) {
     for (int b = 0; b < kLenBuckets; ++b) plan = plan * 1000003u + c->tuned_kernel[b] * 64u + c->tuned_lanes[b];
   }
-  const uint64_t sig[16] = {(uint64_t)d_bytes, (uint64_t)d_offsets, (uint64_t)ci, (uint64_t)cj, m, K,
+  const uint64_t sig[17] = {(uint64_t)d_bytes, (uint64_t)d_offsets, (uint64_t)ci, (uint64_t)cj, m, K,
                             (uint64_t)ed, (uint64_t)c->planes.p, c->planes_pw, c->d.bits, plan,
                             (uint64_t)c->small.p, (uint64_t)c->idx.p, (uint64_t)c->branges.p,
-                            (uint64_t)c->dev_flags.p, c->out_collect ? (uint64_t)c->out_t.p : 0};
+                            (uint64_t)c->dev_flags.p, c->out_collect ? (uint64_t)c->out_t.p : 0, (uint64_t)c->geo.p};
   if (c->graph_exec && memcmp(sig, c->graph_sig, sizeof(sig)) == 0) {
     tstart(c, 6, s);   // the verify section spans the replay
     MJ_CUDA_TRY(cudaGraphLaunch(c->graph_exec, s));
@@ -921,7 +929,7 @@ void mj_destroy(mj_ctx* c) {
   Buf* bufs[] = {&c->hist, &c->dev_flags, &c->small, &c->bitmap, &c->tile_count, &c->tile_off, &c->scan_tmp,
                  &c->tile_first,
                  &c->recs, &c->keys, &c->keys_alt, &c->idx, &c->idx_alt, &c->sort_tmp, &c->srec, &c->pair_count, &c->pair_off, &c->pairs, &c->pairs_alt,
-                 &c->uflags, &c->uoffs, &c->cand_i, &c->cand_j, &c->pairbm, &c->planes, &c->ed, &c->out_t,
+                 &c->uflags, &c->uoffs, &c->cand_i, &c->cand_j, &c->pairbm, &c->planes, &c->ed, &c->out_t, &c->geo,
                  &c->out_i, &c->out_j, &c->out_ed, &c->in_bytes, &c->in_offsets, &c->branges,
                  &c->band, &c->feat_x, &c->mult, &c->run_start, &c->parts, &c->yhat, &c->kband, &c->lvals,
                  &c->franges, &c->fnext, &c->fcnt, &c->ed_first};

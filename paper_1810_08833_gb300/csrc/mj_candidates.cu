@@ -429,11 +429,23 @@ __device__ __forceinline__ uint32_t length_class(uint64_t n) {
   return (e - 2u) * 8u + (uint32_t)((n >> (e - 3u)) & 7u);
 }
 
-__device__ __forceinline__ uint64_t pair_min_length(const uint32_t* __restrict__ ci, const uint32_t* __restrict__ cj,
-                                                    const int64_t* __restrict__ offsets, uint64_t t) {
+// Offsets and lengths of pair t's strings; ids >= n_str read nothing and
+// count as empty strings.
+struct PairLens {
+  int64_t ox, lx, oy, ly;
+  bool bad;
+};
+__device__ __forceinline__ PairLens pair_lens(const uint32_t* __restrict__ ci, const uint32_t* __restrict__ cj,
+                                              const int64_t* __restrict__ offsets, uint32_t n_str, uint64_t t) {
   const uint32_t x = ci[t], y = cj[t];
-  const int64_t lx = __ldg(offsets + x + 1) - __ldg(offsets + x), ly = __ldg(offsets + y + 1) - __ldg(offsets + y);
-  return (uint64_t)(lx < ly ? lx : ly);
+  PairLens r{0, 0, 0, 0, x >= n_str || y >= n_str};
+  if (!r.bad) {
+    r.ox = __ldg(offsets + x);
+    r.lx = __ldg(offsets + x + 1) - r.ox;
+    r.oy = __ldg(offsets + y);
+    r.ly = __ldg(offsets + y + 1) - r.oy;
+  }
+  return r;
 }
 
 __device__ __forceinline__ uint64_t band_cells_of(int64_t m, int64_t n, int64_t K) {   // m >= n
@@ -449,16 +461,15 @@ __device__ __forceinline__ uint64_t band_cells_of(int64_t m, int64_t n, int64_t 
 // Class histogram of the pairs; with cells non-null also their K-band cells
 // (mj_stats.band_cells), summed.
 __global__ void order_hist_kernel(const uint32_t* __restrict__ ci, const uint32_t* __restrict__ cj,
-                                  const int64_t* __restrict__ offsets, uint64_t m, uint32_t K,
+                                  const int64_t* __restrict__ offsets, uint32_t n_str, uint64_t m, uint32_t K,
                                   uint32_t* __restrict__ hist, unsigned long long* __restrict__ cells) {
   __shared__ uint32_t h[kOrderClasses];
   for (int c = threadIdx.x; c < kOrderClasses; c += blockDim.x) h[c] = 0;
   __syncthreads();
   unsigned long long acc = 0;
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t x = ci[t], y = cj[t];
-    const int64_t lx = __ldg(offsets + x + 1) - __ldg(offsets + x), ly = __ldg(offsets + y + 1) - __ldg(offsets + y);
-    const int64_t n = lx < ly ? lx : ly, mm = lx < ly ? ly : lx;
+    const PairLens L = pair_lens(ci, cj, offsets, n_str, t);
+    const int64_t n = L.lx < L.ly ? L.lx : L.ly, mm = L.lx < L.ly ? L.ly : L.lx;
     atomicAdd(&h[length_class((uint64_t)n)], 1u);
     if (cells) acc += band_cells_of(mm, n, K);
   }
@@ -516,9 +527,11 @@ constexpr int kOrderItems = 16;
 
 __global__ void __launch_bounds__(kOrderThreads) order_scatter_kernel(const uint32_t* __restrict__ ci,
                                                                      const uint32_t* __restrict__ cj,
-                                                                     const int64_t* __restrict__ offsets, uint64_t m,
+                                                                     const int64_t* __restrict__ offsets,
+                                                                     uint32_t n_str, uint64_t m,
                                                                      uint32_t* __restrict__ cursor,
-                                                                     uint32_t* __restrict__ order) {
+                                                                     uint32_t* __restrict__ order,
+                                                                     uint4* __restrict__ geo) {
   __shared__ uint32_t h[kOrderClasses];
   __shared__ uint32_t base[kOrderClasses];
   constexpr uint64_t kChunk = (uint64_t)kOrderThreads * kOrderItems;
@@ -527,12 +540,18 @@ __global__ void __launch_bounds__(kOrderThreads) order_scatter_kernel(const uint
     for (int c = threadIdx.x; c < kOrderClasses; c += kOrderThreads) h[c] = 0;
     __syncthreads();
     uint32_t cls[kOrderItems], rank[kOrderItems];
+    uint4 g[kOrderItems];
 #pragma unroll
     for (int k = 0; k < kOrderItems; ++k) {
       const uint64_t t = ch * kChunk + (uint64_t)k * kOrderThreads + threadIdx.x;
       cls[k] = 0xffffffffu;
       if (t < m) {
-        cls[k] = length_class(pair_min_length(ci, cj, offsets, t));
+        const PairLens L = pair_lens(ci, cj, offsets, n_str, t);
+        const bool xa = L.lx >= L.ly;
+        g[k] = L.bad ? make_uint4(0u, 0u, 0u, kGeoBadIds)
+                     : make_uint4((uint32_t)(xa ? L.ox : L.oy), (uint32_t)(xa ? L.oy : L.ox),
+                                  (uint32_t)(xa ? L.lx : L.ly), (uint32_t)(xa ? L.ly : L.lx));
+        cls[k] = length_class((uint64_t)(L.lx < L.ly ? L.lx : L.ly));
         rank[k] = atomicAdd(&h[cls[k]], 1u);
       }
     }
@@ -543,7 +562,11 @@ __global__ void __launch_bounds__(kOrderThreads) order_scatter_kernel(const uint
 #pragma unroll
     for (int k = 0; k < kOrderItems; ++k) {
       const uint64_t t = ch * kChunk + (uint64_t)k * kOrderThreads + threadIdx.x;
-      if (cls[k] != 0xffffffffu) order[base[cls[k]] + rank[k]] = (uint32_t)t;
+      if (cls[k] != 0xffffffffu) {
+        const uint32_t pos = base[cls[k]] + rank[k];
+        order[pos] = (uint32_t)t;
+        if (geo) geo[pos] = g[k];
+      }
     }
     __syncthreads();
   }
@@ -682,15 +705,15 @@ int launch_compact_pairs(const uint64_t* sorted, const uint32_t* flags, const ui
   return MJ_OK;
 }
 
-int launch_length_order(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m, uint32_t K,
-                        uint32_t* scratch, uint32_t* order, uint32_t* counts, uint32_t* ranges,
-                        unsigned long long* cells, cudaStream_t s) {
+int launch_length_order(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint32_t n_str, uint64_t m,
+                        uint32_t K, uint32_t* scratch, uint32_t* order, uint4* geo, uint32_t* counts,
+                        uint32_t* ranges, unsigned long long* cells, cudaStream_t s) {
   uint32_t* hist = scratch;
   uint32_t* cursor = scratch + kOrderClasses;
   MJ_CUDA_TRY(cudaMemsetAsync(hist, 0, kOrderClasses * sizeof(uint32_t), s));
   if (cells) MJ_CUDA_TRY(cudaMemsetAsync(cells, 0, sizeof(unsigned long long), s));
   if (m) {
-    order_hist_kernel<<<grid_for(m), 256, 0, s>>>(ci, cj, offsets, m, K, hist, cells);
+    order_hist_kernel<<<grid_for(m), 256, 0, s>>>(ci, cj, offsets, n_str, m, K, hist, cells);
     MJ_KERNEL_DONE();
   }
   order_scan_kernel<<<1, kOrderClasses, 0, s>>>(hist, cursor, counts, ranges);
@@ -698,8 +721,8 @@ int launch_length_order(const uint32_t* ci, const uint32_t* cj, const int64_t* o
   if (m) {
     const uint64_t chunks = (m + (uint64_t)kOrderThreads * kOrderItems - 1) / ((uint64_t)kOrderThreads * kOrderItems);
     const uint64_t cap = (uint64_t)kNumSMsHint * 8;
-    order_scatter_kernel<<<(unsigned)(chunks < cap ? chunks : cap), kOrderThreads, 0, s>>>(ci, cj, offsets, m, cursor,
-                                                                                            order);
+    order_scatter_kernel<<<(unsigned)(chunks < cap ? chunks : cap), kOrderThreads, 0, s>>>(ci, cj, offsets, n_str, m,
+                                                                                            cursor, order, geo);
     MJ_KERNEL_DONE();
   }
   return MJ_OK;

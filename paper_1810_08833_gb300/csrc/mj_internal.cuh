@@ -224,6 +224,8 @@ struct VerifyArgs {
   unsigned long long* cells = nullptr; // nullable: K-band cells accumulated
   unsigned long long* work = nullptr;  // nullable: word-columns processed (columns x W) accumulated
   uint32_t* dev_flags = nullptr;
+  const uint4* pair_geo = nullptr;     // nullable: at order position q, (oA, oB, m, n) of pair order[q], A the
+                                       // longer string (n = kGeoBadIds: an id out of range); loaded with order[q]
   uint32_t* out_t = nullptr;           // nullable: indices of the pairs with result <= K, appended (order arbitrary)
   unsigned long long* out_count = nullptr;
 };
@@ -251,9 +253,13 @@ int fewest_lanes_for(uint32_t kmax);
 constexpr int kLenBuckets = 32;
 constexpr int kOrderScratchWords = 512;
 // cells (nullable): set to the pairs' K-band cells (mj_stats.band_cells).
-int launch_length_order(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint64_t m, uint32_t K,
-                        uint32_t* scratch, uint32_t* order, uint32_t* counts, uint32_t* ranges,
-                        unsigned long long* cells, cudaStream_t s);
+// geo (nullable): the pairs' geometry at their order positions (VerifyArgs::
+// pair_geo).  Pair ids >= n_str count as empty strings here (the verifier
+// flags them).
+constexpr uint32_t kGeoBadIds = 0xffffffffu;
+int launch_length_order(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint32_t n_str, uint64_t m,
+                        uint32_t K, uint32_t* scratch, uint32_t* order, uint4* geo, uint32_t* counts,
+                        uint32_t* ranges, unsigned long long* cells, cudaStream_t s);
 
 // ---- learned first-pass band (MLP 8 -> 64 -> 64 -> 1)
 // features of a candidate (i, j), n = min length, d0 = length difference,

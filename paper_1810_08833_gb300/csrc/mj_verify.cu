@@ -116,23 +116,43 @@ struct PairState {
 
 // Sets up pair t; returns false if the pair is decided without the DP
 // (result written to *res).
-template <int W, int P>
-__device__ __forceinline__ bool pair_init(PairState<W, P>& st, const VerifyArgs& a, uint32_t GW, uint64_t t,
-                                          uint32_t* res) {
+// Geometry of the pair at order position q (index t): offsets of A (the
+// longer string) and B, their lengths; false for an id out of range.
+__device__ __forceinline__ bool pair_geometry(const VerifyArgs& a, uint64_t q, uint64_t t, int64_t& oA, int64_t& oB,
+                                              int64_t& m, int64_t& n) {
+  if (a.pair_geo) {   // written with the order: one load, no chain through the ids
+    const uint4 g = a.pair_geo[q];
+    if (g.w == kGeoBadIds) return false;
+    oA = g.x;
+    oB = g.y;
+    m = g.z;
+    n = g.w;
+    return true;
+  }
   const uint32_t x = a.pi[t], y = a.pj[t];
+  if (x >= a.n_strings || y >= a.n_strings) return false;
+  const int64_t ox = __ldg(a.offsets + x), lx = __ldg(a.offsets + x + 1) - ox;
+  const int64_t oy = __ldg(a.offsets + y), ly = __ldg(a.offsets + y + 1) - oy;
+  const bool xa = lx >= ly;
+  oA = xa ? ox : oy;
+  m = xa ? lx : ly;
+  oB = xa ? oy : ox;
+  n = xa ? ly : lx;
+  return true;
+}
+
+template <int W, int P>
+__device__ __forceinline__ bool pair_init(PairState<W, P>& st, const VerifyArgs& a, uint32_t GW, uint64_t q, uint64_t t,
+                                          uint32_t* res) {
   const uint32_t k = a.pk ? a.pk[t] : a.K;
   st.t = t;
   st.k = k;
-  if (x >= a.n_strings || y >= a.n_strings) {
+  int64_t oA, oB, m, n;
+  if (!pair_geometry(a, q, t, oA, oB, m, n)) {
     atomicOr(a.dev_flags, FLAG_BOUNDS);
     *res = k + 1;
     return false;
   }
-  const int64_t ox = __ldg(a.offsets + x), lx = __ldg(a.offsets + x + 1) - ox;
-  const int64_t oy = __ldg(a.offsets + y), ly = __ldg(a.offsets + y + 1) - oy;
-  const bool xa = lx >= ly;
-  const int64_t oA = xa ? ox : oy, m = xa ? lx : ly;
-  const int64_t oB = xa ? oy : ox, n = xa ? ly : lx;
   const int64_t d0 = m - n;
   if (d0 > (int64_t)k) {
     *res = k + 1;
@@ -411,7 +431,7 @@ __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t
               }
             }
             uint32_t res;
-            if (pair_init<W, P>(st, a, GW, t, &res)) {
+            if (pair_init<W, P>(st, a, GW, q, t, &res)) {
               active = true;
             } else {
               put_result(a, t, res);
@@ -589,7 +609,7 @@ __global__ void __launch_bounds__(128, P <= 2 ? 8 : 1) verify_wave_kernel(Verify
           more = false;
         } else {
           t = a.order ? a.order[q] : q;
-          const uint32_t x = a.pi[t], y = a.pj[t];
+          int64_t gm = 0, gn = 0;
           k = a.pk ? a.pk[t] : a.K;
           uint32_t res = 0xffffffffu;
           const uint32_t* fed = a.first_ed ? a.first_ed : a.ed;
@@ -597,17 +617,12 @@ __global__ void __launch_bounds__(128, P <= 2 ? 8 : 1) verify_wave_kernel(Verify
           if (skip) {
             if (a.first_ed && gl == 0) put_result(a, t, fed[t]);
             res = 0xfffffffeu;   // settled by the first pass: nothing to do
-          } else if (x >= a.n_strings || y >= a.n_strings) {
+          } else if (!pair_geometry(a, q, t, oA, oB, gm, gn)) {
             if (gl == 0) atomicOr(a.dev_flags, FLAG_BOUNDS);
             res = k + 1;
           } else {
-            const int64_t ox = __ldg(a.offsets + x), lx = __ldg(a.offsets + x + 1) - ox;
-            const int64_t oy = __ldg(a.offsets + y), ly = __ldg(a.offsets + y + 1) - oy;
-            const bool xa = lx >= ly;
-            if (a.cells && gl == 0) cells += band_cells(xa ? lx : ly, xa ? ly : lx, a.K);
-            const int64_t mm = xa ? lx : ly, nn = xa ? ly : lx;
-            oA = xa ? ox : oy;
-            oB = xa ? oy : ox;
+            if (a.cells && gl == 0) cells += band_cells(gm, gn, a.K);
+            const int64_t mm = gm, nn = gn;
             if (mm >= (int64_t)kMaxLen) {
               if (gl == 0) atomicOr(a.dev_flags, FLAG_LENGTH);
               res = k + 1;
@@ -764,6 +779,8 @@ __global__ void __launch_bounds__(32 * V) verify_cta_kernel(VerifyArgs a, uint64
   static_assert(S == 32 && kRing >= 2 * S + 2 && (kRing & (kRing - 1)) == 0, "window and ring sizes");
   __shared__ uint32_t ring[V][kRing];
   __shared__ unsigned long long s_t;   // pair of the CTA (~0: none left)
+  __shared__ longlong2 s_geo;          // its offsets of A and B
+  __shared__ int2 s_len;               // and lengths m >= n
   __shared__ int s_flag[3];            // per window (mod 3): 1 = finished, 2 = rejected
   __shared__ int32_t s_result[3];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -814,7 +831,6 @@ __global__ void __launch_bounds__(32 * V) verify_cta_kernel(VerifyArgs a, uint64
         const uint64_t q = q_lo + atomicAdd(next, 1ull);
         if (q >= q_hi) break;
         const uint64_t t = a.order ? a.order[q] : q;
-        const uint32_t x = a.pi[t], y = a.pj[t];
         const uint32_t kt = a.pk ? a.pk[t] : a.K;
         const uint32_t* fed = a.first_ed ? a.first_ed : a.ed;
         if (a.skip_kband && a.skip_kband[t] < a.K && fed[t] <= a.skip_kband[t]) {
@@ -822,14 +838,12 @@ __global__ void __launch_bounds__(32 * V) verify_cta_kernel(VerifyArgs a, uint64
           ++nskip;
           continue;
         }
-        if (x >= a.n_strings || y >= a.n_strings) {
+        int64_t gA, gB, mm, nn;
+        if (!pair_geometry(a, q, t, gA, gB, mm, nn)) {
           atomicOr(a.dev_flags, FLAG_BOUNDS);
           put_result(a, t, kt + 1);
           continue;
         }
-        const int64_t lx = __ldg(a.offsets + x + 1) - __ldg(a.offsets + x);
-        const int64_t ly = __ldg(a.offsets + y + 1) - __ldg(a.offsets + y);
-        const int64_t mm = lx >= ly ? lx : ly, nn = lx >= ly ? ly : lx;
         if (a.cells) cells += band_cells(mm, nn, a.K);
         if (mm >= (int64_t)kMaxLen) {
           atomicOr(a.dev_flags, FLAG_LENGTH);
@@ -845,6 +859,8 @@ __global__ void __launch_bounds__(32 * V) verify_cta_kernel(VerifyArgs a, uint64
           continue;
         }
         got = t;
+        s_geo = make_longlong2(gA, gB);
+        s_len = make_int2((int32_t)mm, (int32_t)nn);
         break;
       }
       s_t = got;
@@ -853,15 +869,13 @@ __global__ void __launch_bounds__(32 * V) verify_cta_kernel(VerifyArgs a, uint64
     const unsigned long long t = s_t;
     if (t == ~0ull) break;
     {
-      const uint32_t x = a.pi[t], y = a.pj[t];
       k = a.pk ? a.pk[t] : a.K;
-      const int64_t ox = __ldg(a.offsets + x), lx = __ldg(a.offsets + x + 1) - ox;
-      const int64_t oy = __ldg(a.offsets + y), ly = __ldg(a.offsets + y + 1) - oy;
-      const bool xa = lx >= ly;
-      oA = xa ? ox : oy;
-      oB = xa ? oy : ox;
-      m = (int32_t)(xa ? lx : ly);
-      n = (int32_t)(xa ? ly : lx);
+      const longlong2 geo = s_geo;
+      const int2 len = s_len;
+      oA = geo.x;
+      oB = geo.y;
+      m = len.x;
+      n = len.y;
       d0 = m - n;
       dlo = -(int32_t)((k - (uint32_t)d0) >> 1);
       dhi = d0 + (int32_t)((k - (uint32_t)d0) >> 1);
