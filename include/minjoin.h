@@ -152,8 +152,10 @@ typedef struct {
   uint32_t bits;         /* bits per rank code, max(1, ceil(log2 sigma)) */
   uint32_t q, T, K;
   int32_t r_max;         /* radius of the longest string */
-  uint64_t N;            /* longest string length */
+  uint64_t N;            /* longest string length (the fixed one after mj_set_alphabet) */
   uint8_t rank[256];     /* rank code of every byte value (ascending byte order) */
+  uint64_t input_max_len; /* longest string length of this input */
+  uint8_t present[256];  /* 1 for every byte value present in this input */
 } mj_derived;
 
 /* Counters and timings of the last call (see each field). */
@@ -224,6 +226,40 @@ int mj_partition_copy(mj_ctx* ctx, uint32_t* d_sid, uint32_t* d_pos, uint32_t* d
 int mj_candidates(mj_ctx* ctx, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t n,
                   const mj_params* p, const uint64_t* d_qgram_table, void* stream, uint64_t* count);
 int mj_candidates_copy(mj_ctx* ctx, uint32_t* d_i, uint32_t* d_j, void* stream);
+
+/* ---- Sharded join over several GPUs (one process per GPU; the exchange
+ * itself, by collective communication, is the caller's: see the package's
+ * sharded module).  The strings are split by id range; every shard is
+ * partitioned locally under the global alphabet and longest length; the
+ * partition records go to the rank owning their (length, key) class, so that
+ * Alg. 3's hash join (grouping by partition substring) runs with every group
+ * whole on one rank; the candidate pairs go to the rank owning the pair for
+ * the dedup of C; verification needs every string on every rank.
+ *
+ * mj_set_alphabet: later mj_derive / mj_partition / mj_join calls on this
+ * context take Sigma = the byte values with h_present[b] != 0 (256 flags) and
+ * N as the longest length instead of the input's own, so that all shards
+ * derive the same rank codes, q and Pi; an input with a byte value outside
+ * Sigma or a string longer than N is MJ_ERR_ARG.  h_present = NULL reverts to
+ * the input's own values. */
+int mj_set_alphabet(mj_ctx* ctx, const uint8_t* h_present, uint64_t N);
+/* Steps a5-a7 on given partition records (Alg. 3's join and filters, dedup):
+ * record r is partition (d_pos[r], d_len[r]) of string d_sid[r] (global id
+ * < n_strings) of length d_slen[r], with partition key d_key[r] (as written
+ * by mj_partition_copy).  Records of one (length, key) class must all be
+ * here.  *count receives the candidates; mj_candidates_copy writes them (i <
+ * j, sorted).  Key equality stands for byte equality (no bytes are given, so
+ * MJ_FLAG_KEY_CHECK is MJ_ERR_ARG); ids >= n_strings are MJ_ERR_ARG.
+ * Synchronises. */
+int mj_candidates_records(mj_ctx* ctx, const uint32_t* d_sid, const uint32_t* d_pos, const uint32_t* d_len,
+                          const uint64_t* d_key, const uint32_t* d_slen, uint64_t n_rec, uint32_t n_strings,
+                          const mj_params* p, void* stream, uint64_t* count);
+/* The distinct pairs among (d_i[t], d_j[t]), t < m, each as (min, max):
+ * *count receives their number and mj_candidates_copy writes them sorted
+ * (the dedup of C over candidates gathered from several shards).  Ids >=
+ * n_strings are MJ_ERR_ARG.  Synchronises. */
+int mj_pairs_unique(mj_ctx* ctx, const uint32_t* d_i, const uint32_t* d_j, uint64_t m, uint32_t n_strings,
+                    void* stream, uint64_t* count);
 
 /* Step a8 (Sec. 3, verification with Ukkonen's band): for every pair
  * (d_i[t], d_j[t]), t < m, writes d_ed[t] = ED if ED <= k_t, else k_t + 1,

@@ -42,7 +42,8 @@ class Params(ctypes.Structure):
 class Derived(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_uint32), ("bits", ctypes.c_uint32), ("q", ctypes.c_uint32),
                 ("T", ctypes.c_uint32), ("K", ctypes.c_uint32), ("r_max", ctypes.c_int32),
-                ("N", ctypes.c_uint64), ("rank", ctypes.c_uint8 * 256)]
+                ("N", ctypes.c_uint64), ("rank", ctypes.c_uint8 * 256), ("input_max_len", ctypes.c_uint64),
+                ("present", ctypes.c_uint8 * 256)]
 
 
 class BandTrainParams(ctypes.Structure):
@@ -119,6 +120,10 @@ _SIGS = {
     "mj_device_flags": (ctypes.c_int, [VP, VP, ctypes.POINTER(U32)]),
     "mj_verify_static_flags": (ctypes.c_int, [VP, ctypes.POINTER(U32)]),
     "mj_inject_alloc_failure": (ctypes.c_int, [ctypes.c_int64]),
+    "mj_set_alphabet": (ctypes.c_int, [VP, VP, U64]),
+    "mj_candidates_records": (ctypes.c_int, [VP, VP, VP, VP, VP, VP, U64, U32, ctypes.POINTER(Params), VP,
+                                             ctypes.POINTER(U64)]),
+    "mj_pairs_unique": (ctypes.c_int, [VP, VP, VP, U64, U32, VP, ctypes.POINTER(U64)]),
     "mj_band_calibrate": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP,
                                          ctypes.POINTER(BandCalibration)]),
     "mj_join": (ctypes.c_int, [VP, VP, VP, U32, ctypes.POINTER(Params), VP, ctypes.POINTER(U64)]),
@@ -256,7 +261,8 @@ class Context:
         _check(self._lib.mj_derive(self._h, _ptr(data), _ptr(offsets), n, ctypes.byref(p), _stream(stream),
                                    ctypes.byref(d)), "mj_derive")
         return {"sigma": d.sigma, "bits": d.bits, "q": d.q, "T": d.T, "K": d.K, "r_max": d.r_max, "N": d.N,
-                "rank": np.frombuffer(bytes(d.rank), dtype=np.uint8).copy()}
+                "rank": np.frombuffer(bytes(d.rank), dtype=np.uint8).copy(), "input_max_len": d.input_max_len,
+                "present": np.frombuffer(bytes(d.present), dtype=np.uint8).astype(bool)}
 
     def partition(self, data, offsets, p: Params, table=None, stream=None):
         import torch
@@ -285,6 +291,49 @@ class Context:
         cj = torch.empty(m, dtype=torch.int32, device=data.device)
         _check(self._lib.mj_candidates_copy(self._h, _ptr(ci), _ptr(cj), _stream(stream)), "mj_candidates_copy")
         return ci, cj
+
+    def set_alphabet(self, present=None, N: int = 0):
+        """Fix Sigma (256 presence flags) and the longest length N for later
+        calls (a sharded join's global values); None reverts."""
+        if present is None:
+            _check(self._lib.mj_set_alphabet(self._h, None, 0), "mj_set_alphabet")
+            return
+        buf = (ctypes.c_uint8 * 256)(*[1 if x else 0 for x in np.asarray(present).tolist()])
+        _check(self._lib.mj_set_alphabet(self._h, ctypes.cast(buf, VP), int(N)), "mj_set_alphabet")
+
+    def _copy_candidates(self, m: int, device):
+        import torch
+        ci = torch.empty(m, dtype=torch.int32, device=device)
+        cj = torch.empty(m, dtype=torch.int32, device=device)
+        _check(self._lib.mj_candidates_copy(self._h, _ptr(ci), _ptr(cj), None), "mj_candidates_copy")
+        return ci, cj
+
+    def candidates_records(self, sid, pos, ln, key, slen, n_strings: int, p: Params, stream=None):
+        """Candidate pairs (i < j, sorted) from partition records (int32 sid,
+        pos, len, slen; int64 key), all CUDA tensors of one size."""
+        import torch
+        m = sid.numel()
+        for t, dt in ((sid, torch.int32), (pos, torch.int32), (ln, torch.int32), (key, torch.int64),
+                      (slen, torch.int32)):
+            if not t.is_cuda or t.dtype != dt or not t.is_contiguous() or t.numel() != m:
+                raise ValueError("records must be contiguous CUDA tensors (int32; key int64) of one size")
+        cnt = U64()
+        _check(self._lib.mj_candidates_records(self._h, _ptr(sid), _ptr(pos), _ptr(ln), _ptr(key), _ptr(slen), m,
+                                               int(n_strings), ctypes.byref(p), _stream(stream), ctypes.byref(cnt)),
+               "mj_candidates_records")
+        return self._copy_candidates(cnt.value, sid.device)
+
+    def pairs_unique(self, i, j, n_strings: int, stream=None):
+        """The distinct pairs (min, max) among (i[t], j[t]), sorted."""
+        import torch
+        m = i.numel()
+        for t in (i, j):
+            if not t.is_cuda or t.dtype != torch.int32 or not t.is_contiguous() or t.numel() != m:
+                raise ValueError("pair tensors must be contiguous int32 CUDA tensors of one size")
+        cnt = U64()
+        _check(self._lib.mj_pairs_unique(self._h, _ptr(i), _ptr(j), m, int(n_strings), _stream(stream),
+                                         ctypes.byref(cnt)), "mj_pairs_unique")
+        return self._copy_candidates(cnt.value, i.device)
 
     def verify(self, data, offsets, i, j, K: int, k=None, stream=None):
         import torch

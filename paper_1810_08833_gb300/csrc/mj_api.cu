@@ -150,6 +150,11 @@ struct mj_ctx {
   bool out_collect = false;
   Buf geo;            // pair geometry at the verification order's positions (uint4)
   bool geo_valid = false;
+  // alphabet and longest length fixed by mj_set_alphabet (a sharded join's
+  // global values), used by derive instead of the input's own
+  bool fixed_alpha = false;
+  uint8_t fixed_present[256] = {};
+  uint64_t fixed_N = 0;
   Buf in_bytes, in_offsets;  // staging for mj_join_host
   uint64_t n_part = 0, n_cand = 0, n_out = 0;
   // bit-planes written by the partition kernel for the verifier
@@ -273,13 +278,21 @@ int derive(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t
   Derived& d = c->d;
   d = Derived();
   uint32_t sigma = 0;
-  for (int b = 0; b < 256; ++b) {
-    if (c->h_small[b]) d.rank[b] = (uint8_t)sigma++;
+  if (c->fixed_alpha) {   // a global alphabet and length: every local byte and length must lie within them
+    for (int b = 0; b < 256; ++b)
+      if (c->h_small[b] && !c->fixed_present[b]) return MJ_ERR_ARG;
+    if (c->h_small[256] > c->fixed_N) return MJ_ERR_ARG;
+    for (int b = 0; b < 256; ++b)
+      if (c->fixed_present[b]) d.rank[b] = (uint8_t)sigma++;
+  } else {
+    for (int b = 0; b < 256; ++b) {
+      if (c->h_small[b]) d.rank[b] = (uint8_t)sigma++;
+    }
   }
   d.sigma = sigma;
   d.bits = 1;
   while ((1u << d.bits) < sigma) ++d.bits;
-  d.N = c->h_small[256];
+  d.N = c->fixed_alpha ? c->fixed_N : c->h_small[256];
   d.K = p->K;
   d.T = p->T ? p->T : p->K;
   if (d.T == 0) d.T = 1;
@@ -979,6 +992,8 @@ int mj_derive(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
   out->r_max = d.r_max;
   out->N = d.N;
   memcpy(out->rank, d.rank, 256);
+  out->input_max_len = c->h_small[256];   // derive leaves the histogram and longest length here
+  for (int b = 0; b < 256; ++b) out->present[b] = c->h_small[b] ? 1 : 0;
   return MJ_OK;
 }
 
@@ -1038,6 +1053,106 @@ int mj_candidates_copy(mj_ctx* c, uint32_t* d_i, uint32_t* d_j, void* stream) {
   if (!n) return MJ_OK;
   if (d_i) MJ_CUDA_TRY(cudaMemcpyAsync(d_i, c->cand_i.p, n * 4, cudaMemcpyDeviceToDevice, s));
   if (d_j) MJ_CUDA_TRY(cudaMemcpyAsync(d_j, c->cand_j.p, n * 4, cudaMemcpyDeviceToDevice, s));
+  return MJ_OK;
+}
+
+int mj_set_alphabet(mj_ctx* c, const uint8_t* h_present, uint64_t N) {
+  if (!c) return MJ_ERR_ARG;
+  if (!h_present) {
+    c->fixed_alpha = false;
+    return MJ_OK;
+  }
+  for (int b = 0; b < 256; ++b) c->fixed_present[b] = h_present[b] ? 1 : 0;
+  c->fixed_N = N;
+  c->fixed_alpha = true;
+  return MJ_OK;
+}
+
+int mj_candidates_records(mj_ctx* c, const uint32_t* d_sid, const uint32_t* d_pos, const uint32_t* d_len,
+                          const uint64_t* d_key, const uint32_t* d_slen, uint64_t n_rec, uint32_t n_strings,
+                          const mj_params* p, void* stream, uint64_t* count) {
+  if (!c || !p || !count) return MJ_ERR_ARG;
+  if (n_rec && (!d_sid || !d_pos || !d_len || !d_key || !d_slen)) return MJ_ERR_ARG;
+  if (p->flags & MJ_FLAG_KEY_CHECK) return MJ_ERR_ARG;   // no bytes to check against
+  if (p->K > (1u << 20) || n_rec >= (1ull << 32)) return MJ_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = S(stream);
+  begin_call(c, false);
+  c->have_part = c->have_cand = false;
+  Derived& d = c->d;
+  d = Derived();
+  d.K = p->K;
+  d.T = p->T ? p->T : p->K;
+  d.seed = p->seed;
+  c->stats.n_strings = n_strings;
+  c->n_part = n_rec;
+  c->n_cand = 0;
+  if (n_rec) {
+    // ids and lengths bound the grouping key and the pair bitmap: check them
+    MJ_TRY(c->small.reserve(128, s));
+    unsigned int* mx = reinterpret_cast<unsigned int*>(c->small.as<unsigned long long>() + 10);
+    MJ_TRY(launch_max_u32(d_sid, n_rec, mx, s));
+    MJ_TRY(launch_max_u32(d_slen, n_rec, mx + 2, s));
+    MJ_TRY(readback(c, mx, 16, s));
+    const uint32_t max_sid = ((uint32_t*)c->h_small)[0], max_slen = ((uint32_t*)c->h_small)[2];
+    if (max_sid >= n_strings) return MJ_ERR_ARG;
+    d.N = max_slen;
+    MJ_TRY(c->recs.reserve(n_rec * sizeof(PRec), s));
+    MJ_TRY(launch_pack_records(d_sid, d_pos, d_len, d_key, d_slen, n_rec, c->recs.as<PRec>(), s));
+    MJ_TRY(candidates(c, nullptr, nullptr, n_strings, p->flags, s));
+  }
+  MJ_CUDA_TRY(cudaStreamSynchronize(s));
+  c->have_cand = true;
+  c->stats.n_launches = launch_count() - c->launches_at_start;
+  *count = c->n_cand;
+  return MJ_OK;
+}
+
+int mj_pairs_unique(mj_ctx* c, const uint32_t* d_i, const uint32_t* d_j, uint64_t m, uint32_t n_strings,
+                    void* stream, uint64_t* count) {
+  if (!c || !count) return MJ_ERR_ARG;
+  if (m && (!d_i || !d_j)) return MJ_ERR_ARG;
+  if (m >= (1ull << 32)) return MJ_ERR_UNSUPPORTED;
+  DeviceGuard g(c->device);
+  cudaStream_t s = S(stream);
+  begin_call(c, false);
+  c->have_part = c->have_cand = false;
+  c->n_cand = 0;
+  if (m) {
+    MJ_TRY(c->small.reserve(128, s));
+    unsigned int* mx = reinterpret_cast<unsigned int*>(c->small.as<unsigned long long>() + 10);
+    MJ_TRY(launch_max_u32(d_i, m, mx, s));
+    MJ_TRY(launch_max_u32(d_j, m, mx + 2, s));
+    MJ_TRY(readback(c, mx, 16, s));
+    if (((uint32_t*)c->h_small)[0] >= n_strings || ((uint32_t*)c->h_small)[2] >= n_strings) return MJ_ERR_ARG;
+    const int nb = bits_for(n_strings ? n_strings - 1 : 0);
+    MJ_TRY(c->pairs.reserve(m * 8, s));
+    MJ_TRY(c->pairs_alt.reserve(m * 8, s));
+    MJ_TRY(c->sort_tmp.reserve(radix_temp_bytes(m), s));
+    MJ_TRY(c->uflags.reserve(m * 4, s));
+    MJ_TRY(c->uoffs.reserve(m * 4 + 16, s));
+    MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(m), s));
+    MJ_TRY(launch_pack_pairs(d_i, d_j, m, nb, c->pairs.as<uint64_t>(), s));
+    bool alt = false;
+    MJ_TRY(radix_sort_u64(c->pairs.as<uint64_t>(), c->pairs_alt.as<uint64_t>(), nullptr, nullptr, m, 0, 2 * nb,
+                          c->sort_tmp.p, &alt, s));
+    const uint64_t* sp = alt ? c->pairs_alt.as<uint64_t>() : c->pairs.as<uint64_t>();
+    MJ_TRY(launch_unique_flags(sp, m, c->uflags.as<uint32_t>(), s));
+    uint32_t* utotal = c->uoffs.as<uint32_t>() + m;
+    MJ_TRY(launch_exclusive_scan_u32(c->uflags.as<uint32_t>(), c->uoffs.as<uint32_t>(), m, c->scan_tmp.p, utotal, s));
+    MJ_TRY(readback(c, utotal, 4, s));
+    const uint32_t nc = *(uint32_t*)c->h_small;
+    MJ_TRY(c->cand_i.reserve((size_t)nc * 4 + 16, s));
+    MJ_TRY(c->cand_j.reserve((size_t)nc * 4 + 16, s));
+    MJ_TRY(launch_compact_pairs(sp, c->uflags.as<uint32_t>(), c->uoffs.as<uint32_t>(), m, nb,
+                                c->cand_i.as<uint32_t>(), c->cand_j.as<uint32_t>(), nullptr, s));
+    c->n_cand = nc;
+  }
+  MJ_CUDA_TRY(cudaStreamSynchronize(s));
+  c->stats.n_candidates = c->n_cand;
+  c->have_cand = true;
+  c->stats.n_launches = launch_count() - c->launches_at_start;
+  *count = c->n_cand;
   return MJ_OK;
 }
 

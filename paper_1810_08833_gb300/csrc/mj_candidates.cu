@@ -572,6 +572,32 @@ __global__ void __launch_bounds__(kOrderThreads) order_scatter_kernel(const uint
   }
 }
 
+// Records given as separate arrays (a sharded join's exchanged records).
+__global__ void pack_records_kernel(const uint32_t* __restrict__ sid, const uint32_t* __restrict__ pos,
+                                    const uint32_t* __restrict__ len, const uint64_t* __restrict__ key,
+                                    const uint32_t* __restrict__ slen, uint64_t n, PRec* __restrict__ out) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
+    PRec r;
+    r.h61 = key[t];
+    r.run = 0;
+    r.slen = slen[t];
+    r.len = len[t];
+    r.sid = sid[t];
+    r.pos = pos[t];
+    r.pad = 0;
+    store_rec(out, t, r);
+  }
+}
+
+// Pairs as packed keys (min << nb | max) for the dedup sort.
+__global__ void pack_pairs_kernel(const uint32_t* __restrict__ pi, const uint32_t* __restrict__ pj, uint64_t m, int nb,
+                                  uint64_t* __restrict__ out) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t a = pi[t], b = pj[t];
+    out[t] = ((uint64_t)(a < b ? a : b) << nb) | (a < b ? b : a);
+  }
+}
+
 unsigned grid_for(uint64_t n, int threads = 256) {
   uint64_t g = (n + threads - 1) / threads;
   uint64_t cap = (uint64_t)kNumSMsHint * 32;
@@ -774,6 +800,21 @@ int launch_gather_output(const uint32_t* out_t, uint64_t n, uint64_t m, const ui
   bool alt = false;
   MJ_TRY(radix_sort_u64(keys, keys_alt, nullptr, nullptr, n, 0, bits, temp, &alt, s));
   gather_out_kernel<<<grid_for(n), 256, 0, s>>>(alt ? keys_alt : keys, n, ci, cj, ed, oi, oj, oed);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
+int launch_pack_records(const uint32_t* sid, const uint32_t* pos, const uint32_t* len, const uint64_t* key,
+                        const uint32_t* slen, uint64_t n, PRec* out, cudaStream_t s) {
+  if (!n) return MJ_OK;
+  pack_records_kernel<<<grid_for(n), 256, 0, s>>>(sid, pos, len, key, slen, n, out);
+  MJ_KERNEL_DONE();
+  return MJ_OK;
+}
+
+int launch_pack_pairs(const uint32_t* pi, const uint32_t* pj, uint64_t m, int nb, uint64_t* out, cudaStream_t s) {
+  if (!m) return MJ_OK;
+  pack_pairs_kernel<<<grid_for(m), 256, 0, s>>>(pi, pj, m, nb, out);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }

@@ -193,6 +193,10 @@ int launch_bitmap_write(const uint32_t* bm, uint32_t n_str, const uint32_t* off,
                         cudaStream_t s);
 int launch_key_check(const PRec* r, const uint8_t* bytes, const int64_t* offsets, uint32_t n_rec,
                      unsigned long long* mismatches, cudaStream_t s);
+// Sharded join: records from separate arrays, pairs packed for a dedup sort.
+int launch_pack_records(const uint32_t* sid, const uint32_t* pos, const uint32_t* len, const uint64_t* key,
+                        const uint32_t* slen, uint64_t n, PRec* out, cudaStream_t s);
+int launch_pack_pairs(const uint32_t* pi, const uint32_t* pj, uint64_t m, int nb, uint64_t* out, cudaStream_t s);
 // a7: unique of sorted u64 pairs -> flags; then compaction.
 int launch_unique_flags(const uint64_t* sorted, uint64_t n, uint32_t* flags, cudaStream_t s);
 // run_start (nullable): run_start[u] = index of candidate u's first raw pair
