@@ -227,20 +227,28 @@ __global__ void walk_kernel(const PRec* __restrict__ r, uint32_t n, uint32_t K, 
   }
 }
 
-// cnt[a] = candidates in row a of the pair bitmap (one warp per row).
+// cnt[a] = candidates in row a of the pair bitmap (one warp per row, four
+// independent word loads per lane in flight).
 __global__ void bitmap_rows_kernel(const uint32_t* __restrict__ bm, uint32_t n, uint32_t* __restrict__ cnt) {
   const int lane = threadIdx.x & 31;
   const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t a = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < n; a += warps) {
     const uint64_t w0 = bitmap_row(a, n), w1 = a + 1 < n ? bitmap_row(a + 1, n) : w0;
     uint32_t c = 0;
-    for (uint64_t w = w0 + lane; w < w1; w += 32) c += __popc(__ldcs(bm + w));
+    for (uint64_t w = w0 + 4 * (uint64_t)lane; w < w1; w += 128) {
+      uint32_t v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = w + k < w1 ? __ldcs(bm + w + k) : 0u;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) c += __popc(v[k]);
+    }
     c = __reduce_add_sync(0xffffffffu, c);
     if (lane == 0) cnt[a] = c;
   }
 }
 
-// The candidates (a, b) of every row, in (a, b) order, from the row offsets.
+// The candidates (a, b) of every row, in (a, b) order, from the row offsets:
+// per warp step 128 words of the row, four per lane.
 __global__ void bitmap_write_kernel(const uint32_t* __restrict__ bm, uint32_t n, const uint32_t* __restrict__ off,
                                     uint32_t* __restrict__ oi, uint32_t* __restrict__ oj) {
   const int lane = threadIdx.x & 31;
@@ -248,23 +256,32 @@ __global__ void bitmap_write_kernel(const uint32_t* __restrict__ bm, uint32_t n,
   for (uint64_t a = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < n; a += warps) {
     const uint64_t w0 = bitmap_row(a, n), w1 = a + 1 < n ? bitmap_row(a + 1, n) : w0;
     uint32_t base = off[a];
-    for (uint64_t w = w0; w < w1; w += 32) {
-      const uint64_t lw = w + lane;
-      uint32_t v = lw < w1 ? __ldcs(bm + lw) : 0u;
-      const uint32_t p = __popc(v);
+    for (uint64_t w = w0; w < w1; w += 128) {
+      const uint64_t lw = w + 4 * (uint64_t)lane;
+      uint32_t v[4];
+      uint32_t p = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        v[k] = lw + k < w1 ? __ldcs(bm + lw + k) : 0u;
+        p += __popc(v[k]);
+      }
       uint32_t incl = p;
       for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
       }
       uint32_t at = base + incl - p;
-      const uint32_t b0 = (uint32_t)a + 1u + 32u * (uint32_t)(lw - w0);
-      while (v) {
-        const uint32_t bit = __ffs(v) - 1;
-        v &= v - 1;
-        oi[at] = (uint32_t)a;
-        oj[at] = b0 + bit;
-        ++at;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t b0 = (uint32_t)a + 1u + 32u * (uint32_t)(lw + k - w0);
+        uint32_t x = v[k];
+        while (x) {
+          const uint32_t bit = __ffs(x) - 1;
+          x &= x - 1;
+          oi[at] = (uint32_t)a;
+          oj[at] = b0 + bit;
+          ++at;
+        }
       }
       base += __shfl_sync(0xffffffffu, incl, 31);
     }
@@ -523,7 +540,7 @@ __global__ void order_scan_kernel(const uint32_t* __restrict__ hist, uint32_t* _
 // block step: ranks within the chunk from shared-memory counters, then one
 // global reservation per class and chunk.
 constexpr int kOrderThreads = 256;
-constexpr int kOrderItems = 16;
+constexpr int kOrderItems = 4;
 
 __global__ void __launch_bounds__(kOrderThreads) order_scatter_kernel(const uint32_t* __restrict__ ci,
                                                                      const uint32_t* __restrict__ cj,
