@@ -148,6 +148,7 @@ struct mj_ctx {
   Buf out_i, out_j, out_ed;
   Buf out_t;          // indices of the candidates within K, listed by the band-K pass
   bool out_collect = false;
+  Buf rank_dev;       // the derived rank codes on the device (256 bytes)
   Buf geo;            // pair geometry at the verification order's positions (uint4)
   bool geo_valid = false;
   // alphabet and longest length fixed by mj_set_alphabet (a sharded join's
@@ -304,6 +305,13 @@ int derive(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint32_t
   d.repeats = p->repeats;
   c->stats.n_strings = n;
   c->stats.n_bytes = nbytes;
+  // the rank codes on the device (the text verifier reads B's bytes through
+  // them), staged through pinned memory
+  MJ_TRY(c->rank_dev.reserve(256, s));
+  uint8_t* stage = reinterpret_cast<uint8_t*>(c->h_small) + 3072;
+  MJ_CUDA_TRY(cudaStreamSynchronize(s));   // an earlier copy may still read the staging area
+  memcpy(stage, d.rank, 256);
+  MJ_CUDA_TRY(cudaMemcpyAsync(c->rank_dev.p, stage, 256, cudaMemcpyHostToDevice, s));
   return MJ_OK;
 }
 
@@ -596,6 +604,8 @@ int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const ui
   a.work = c->small.as<unsigned long long>() + 2;
   a.dev_flags = c->dev_flags.as<uint32_t>();
   if (order && order == c->idx.as<uint32_t>() && c->geo_valid) a.pair_geo = c->geo.as<uint4>();
+  a.rank_table = c->rank_dev.as<uint8_t>();
+  a.nbytes = nbytes;
   if (c->out_collect) {   // the join's band-K pass lists the pairs within K
     a.out_t = c->out_t.as<uint32_t>();
     a.out_count = c->small.as<unsigned long long>() + 8;
@@ -942,7 +952,7 @@ void mj_destroy(mj_ctx* c) {
   Buf* bufs[] = {&c->hist, &c->dev_flags, &c->small, &c->bitmap, &c->tile_count, &c->tile_off, &c->scan_tmp,
                  &c->tile_first,
                  &c->recs, &c->keys, &c->keys_alt, &c->idx, &c->idx_alt, &c->sort_tmp, &c->srec, &c->pair_count, &c->pair_off, &c->pairs, &c->pairs_alt,
-                 &c->uflags, &c->uoffs, &c->cand_i, &c->cand_j, &c->pairbm, &c->planes, &c->ed, &c->out_t, &c->geo,
+                 &c->uflags, &c->uoffs, &c->cand_i, &c->cand_j, &c->pairbm, &c->planes, &c->ed, &c->out_t, &c->geo, &c->rank_dev,
                  &c->out_i, &c->out_j, &c->out_ed, &c->in_bytes, &c->in_offsets, &c->branges,
                  &c->band, &c->feat_x, &c->mult, &c->run_start, &c->parts, &c->yhat, &c->kband, &c->lvals,
                  &c->franges, &c->fnext, &c->fcnt, &c->ed_first};

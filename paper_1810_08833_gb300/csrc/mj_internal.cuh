@@ -231,6 +231,8 @@ struct VerifyArgs {
   const uint4* pair_geo = nullptr;     // nullable: at order position q, (oA, oB, m, n) of pair order[q], A the
                                        // longer string (n = kGeoBadIds: an id out of range); loaded with order[q]
   uint32_t* out_t = nullptr;           // nullable: indices of the pairs with result <= K, appended (order arbitrary)
+  const uint8_t* rank_table = nullptr; // device copy of the 256 rank codes (text kernels read B's bytes through it)
+  uint64_t nbytes = 0;                 // bytes of the input
   unsigned long long* out_count = nullptr;
 };
 int verify_words_for(uint32_t kmax);

@@ -288,11 +288,25 @@ constexpr int kChunkFor = W <= 2 ? 16 : 32;
 // plane words of the rows the band covers in these columns (pre-shifted so
 // that column j0 + c needs a shift by c < 32), and B's plane bits of the
 // columns, bit-reversed so that the next column's bit is the sign bit.
+// Text (7 bit-planes): equality bits by digit tables.  Per chunk, every
+// thread writes to shared memory, for each of A's band words, the 16 masks
+// "rows whose rank code has low digit d" (code bits 0-3) and the 8 masks "high
+// digit e" (bits 4-6); a column then takes its symbol's rank code from B's
+// bytes and ANDs one mask of each table: two loads per word instead of 7
+// XNOR-ANDs.  Tables: word (d * (W + 1) + w) * 128 + thread.
+constexpr int kDigitLo = 16, kDigitHi = 8;
+template <int W>
+constexpr size_t digit_smem_bytes() { return 256 + (size_t)(kDigitLo + kDigitHi) * (W + 1) * 128 * 4; }
+
 template <int W, int P>
-__device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs& a, uint64_t PW, uint32_t* res) {
+__device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs& a, uint64_t PW, uint32_t* res,
+                                           uint32_t* __restrict__ dlo, uint32_t* __restrict__ dhi,
+                                           const uint8_t* __restrict__ s_rank, uint32_t GW) {
+  constexpr bool kDigits = P == 7;
   const int32_t j0 = st.j;
   uint32_t pa[P][W + 1];
   uint32_t bw[P];
+  uint32_t bsym[kDigits ? 8 : 1];   // B's bytes of the chunk's columns, four per word
   {
     const uint64_t ab = st.abit + (uint64_t)(j0 - 1);
     const uint64_t aw = ab >> 5;
@@ -310,12 +324,53 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
           pa[p][w] = __funnelshift_r(w0, w1, ash);
           w0 = w1;
         }
-        bw[p] = __brev(__funnelshift_r(__ldg(plane + wb), __ldg(plane + wb + 1), sb));
+        if (!kDigits) bw[p] = __brev(__funnelshift_r(__ldg(plane + wb), __ldg(plane + wb + 1), sb));
       } else {
 #pragma unroll
         for (int w = 0; w <= W; ++w) pa[p][w] = 0u;
         bw[p] = 0u;
       }
+    }
+    if (kDigits) {
+      const int tid = threadIdx.x;
+#pragma unroll
+      for (int w = 0; w <= W; ++w) {
+        const uint32_t a0 = pa[0][w], a1 = pa[1][w], a2 = pa[2][w], a3 = pa[3][w];
+        const uint32_t t2[4] = {~a0 & ~a1, a0 & ~a1, ~a0 & a1, a0 & a1};
+        uint32_t t3[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) t3[d] = t2[d & 3] & ((d & 4) ? a2 : ~a2);
+#pragma unroll
+        for (int d = 0; d < kDigitLo; ++d) dlo[(d * (W + 1) + w) * 128 + tid] = t3[d & 7] & ((d & 8) ? a3 : ~a3);
+        const uint32_t a4 = pa[4][w], a5 = pa[5][w], a6 = pa[6][w];
+        const uint32_t h2[4] = {~a4 & ~a5, a4 & ~a5, ~a4 & a5, a4 & a5};
+#pragma unroll
+        for (int e = 0; e < kDigitHi; ++e) dhi[(e * (W + 1) + w) * 128 + tid] = h2[e & 3] & ((e & 4) ? a6 : ~a6);
+      }
+      // B's bytes of columns j0 .. j0 + 31, aligned so that column j0 + c is
+      // byte c (words beyond the input read as zero)
+      const uint64_t bi = st.bpos - 32 * (uint64_t)GW;   // byte index of column j0's symbol
+      const uintptr_t at0 = (uintptr_t)(a.bytes + bi);
+      const uint32_t sh = 8u * (uint32_t)(at0 & 3);
+      const uintptr_t wa = at0 & ~(uintptr_t)3;
+      const uintptr_t lo_end = (uintptr_t)a.bytes, hi_end = (uintptr_t)(a.bytes + a.nbytes);
+      uint32_t raw[9];
+      if (wa >= lo_end && wa + 36 <= hi_end) {   // the common case: nine aligned words inside the input
+#pragma unroll
+        for (int k = 0; k < 9; ++k) raw[k] = __ldg(reinterpret_cast<const uint32_t*>(wa) + k);
+      } else {   // near an end of the input: byte by byte, zero outside it
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          uint32_t x = 0;
+          for (int b = 0; b < 4; ++b) {
+            const uintptr_t q = wa + 4 * k + b;
+            if (q >= lo_end && q < hi_end) x |= (uint32_t)__ldg(reinterpret_cast<const uint8_t*>(q)) << (8 * b);
+          }
+          raw[k] = x;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) bsym[k] = __funnelshift_r(raw[k], raw[k + 1], sh);
     }
   }
   constexpr int kChunk = kChunkFor<W>;
@@ -325,15 +380,23 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
     if (c >= cnt) break;
     // equality bits of column j0 + c: A's plane bits XNOR B's, over the planes
     uint32_t EqF[W + 1];
+    if (kDigits) {
+      const uint32_t code = s_rank[(bsym[c >> 2] >> (8 * (c & 3))) & 255u];
+      const uint32_t* lo = dlo + (code & 15u) * (W + 1) * 128 + threadIdx.x;
+      const uint32_t* hi = dhi + (code >> 4) * (W + 1) * 128 + threadIdx.x;
 #pragma unroll
-    for (int w = 0; w <= W; ++w) EqF[w] = 0xffffffffu;
+      for (int w = 0; w <= W; ++w) EqF[w] = lo[w * 128] & hi[w * 128];
+    } else {
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
-      if (p < (int)a.bits) {
-        const uint32_t xb = (uint32_t)__mulhi((int32_t)bw[p], 1);   // B's bit broadcast (sign)
-        bw[p] *= 2u;
+      for (int w = 0; w <= W; ++w) EqF[w] = 0xffffffffu;
 #pragma unroll
-        for (int w = 0; w <= W; ++w) EqF[w] &= ~(pa[p][w] ^ xb);
+      for (int p = 0; p < P; ++p) {
+        if (p < (int)a.bits) {
+          const uint32_t xb = (uint32_t)__mulhi((int32_t)bw[p], 1);   // B's bit broadcast (sign)
+          bw[p] *= 2u;
+#pragma unroll
+          for (int w = 0; w <= W; ++w) EqF[w] &= ~(pa[p][w] ^ xb);
+        }
       }
     }
     uint32_t Eq[W];
@@ -393,6 +456,14 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
 template <int W, int P>
 __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t PW, uint32_t GW,
                                                           unsigned long long* __restrict__ next) {
+  extern __shared__ __align__(16) uint32_t vsm[];   // text: rank table, then the digit tables
+  uint8_t* s_rank = reinterpret_cast<uint8_t*>(vsm);
+  uint32_t* dlo = vsm + 64;
+  uint32_t* dhi = dlo + kDigitLo * (W + 1) * 128;
+  if (P == 7) {
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) s_rank[b] = a.rank_table[b];
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31;
   const uint64_t q_lo = a.range_lo ? *a.range_lo : 0;
   const uint64_t q_hi = a.range_hi ? *a.range_hi : a.m;
@@ -444,7 +515,7 @@ __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t
     if (active) {
       uint32_t res;
       const int32_t j_before = st.j;
-      const bool done = pair_chunk<W, P>(st, a, PW, &res);
+      const bool done = pair_chunk<W, P>(st, a, PW, &res, dlo, dhi, s_rank, GW);
       work += (uint64_t)(st.j - j_before) * W;
       if (done) {
         put_result(a, st.t, res);
@@ -1018,7 +1089,13 @@ int launch_wp(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long*
   int dev = 0, sms = kNumSMsHint, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, verify_diag_kernel<W, P>, 128, 0);
+  const size_t smem = P == 7 ? digit_smem_bytes<W>() : 0;
+  if (P == 7) {
+    if (!a.rank_table) return MJ_ERR_ARG;
+    MJ_CUDA_TRY(cudaFuncSetAttribute(verify_diag_kernel<W, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, verify_diag_kernel<W, P>, 128, smem);
   // at least ~3 pairs per lane, so that the shared queue evens out the early
   // exits (a warp lasts as long as its slowest lane), but at least 3 blocks
   // per SM to hide the recurrence's latency
@@ -1028,7 +1105,7 @@ int launch_wp(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long*
   uint64_t need = (a.m + 127) / 128;
   uint64_t grid = (uint64_t)sms * per_sm;
   if (need < grid) grid = need;
-  verify_diag_kernel<W, P><<<(unsigned)(grid ? grid : 1), 128, 0, s>>>(a, PW, GW, next);
+  verify_diag_kernel<W, P><<<(unsigned)(grid ? grid : 1), 128, smem, s>>>(a, PW, GW, next);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }
@@ -1037,7 +1114,7 @@ template <int W>
 int launch_w(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long* next, cudaStream_t s) {
   if (a.bits <= 2) return launch_wp<W, 2>(a, PW, GW, next, s);
   if (a.bits <= 5) return launch_wp<W, 5>(a, PW, GW, next, s);
-  if (a.bits == 7) return launch_wp<W, 7>(a, PW, GW, next, s);   // printable text (33-128 symbols)
+  if (a.bits == 7 && a.rank_table) return launch_wp<W, 7>(a, PW, GW, next, s);   // text (33-128 symbols): digit tables
   return launch_wp<W, 8>(a, PW, GW, next, s);
 }
 
