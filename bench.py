@@ -44,14 +44,15 @@ INT_LANES_PER_SM = {10: 64, 12: 64, 9: 64}
 ALU_OPS_PER_WORD_COLUMN = 16 # ops of one band word in one column of the bit-vector recurrence
 RECORD_BYTES = 24            # one partition record written: sid, pos, len, string length (u32), key (u64)
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current
-# kernel, keyed by (section, workload number); absent (reported as null)
-# where no capture of the current kernel exists
-# Read-length DNA: verify_diag_kernel<4, 2> (32-column chunks, loop unrolled
-# by 8) captured on 3,000 of the 5,000 families (32.1 MB per launch), scaled
-# by the candidates (x 1.666) to the full workload: the bit-planes and pair
-# arrays it reads grow with them.
-TRAFFIC_BYTES = {("verify_kernel", 2): 53.5e6}
+# capture (dram__bytes_read.sum + dram__bytes_write.sum, a one-pass capture
+# of the full-size launch) of the current kernel, keyed by (section, workload
+# number); absent (reported as null) where no capture of the current kernel
+# exists.  Text-like workload: verify_diag_kernel<3, 7> with digit tables,
+# 51.19 GB read + 3.81 GB written in one launch over 645 M candidates.
+TRAFFIC_BYTES = {("verify_kernel", 5): 51.187e9 + 3.813e9}
+# integer issue ceiling per SM and clock: the ALU pipe's 64 lanes plus the
+# FMA pipe's 64 (integer multiply-adds run there)
+ISSUE_LANES_PER_SM = 128
 
 
 def replica_seed(cfg: int, rank: int) -> int:
@@ -448,9 +449,11 @@ def roofline(section: str, ms: float, st: dict, nbytes: int, hbm: float, hbm_src
     peak = alu["sms"] * alu["lanes"] * alu["mhz"] * 1e6 / 1e9   # Gop/s
     ops = st["verify_word_columns"] * ALU_OPS_PER_WORD_COLUMN
     ach = ops / sec / 1e9
+    issue_peak = alu["sms"] * ISSUE_LANES_PER_SM * alu["mhz"] * 1e6 / 1e9
     return {"kernel": section, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gop/s", "frac": ach / peak,
             "traffic": traffic,
-            "peak_source": f"{alu['sms']} SMs x {alu['lanes']} int32 lanes x {alu['mhz']:.0f} MHz (sampled)"}
+            "peak_source": f"{alu['sms']} SMs x {alu['lanes']} int32 lanes x {alu['mhz']:.0f} MHz (sampled)",
+            "frac_of_issue_ceiling": ach / issue_peak}
 
 
 def partition_roofline(sec_ms: dict, st: dict, nbytes: int, hbm: float, hbm_src: str) -> dict:
