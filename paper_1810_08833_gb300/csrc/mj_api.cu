@@ -462,34 +462,48 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
     MJ_TRY(readback(c, c->small.p, 8, s));
     c->stats.key_collisions = c->h_small[0];
   }
-  MJ_TRY(c->pair_count.reserve((size_t)nr * 4, s));
-  MJ_TRY(c->pair_off.reserve((size_t)nr * 8 + 16, s));
-  MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(nr), s));
-  tstart(c, 3, s);
-  MJ_TRY(launch_count_pairs(r, nr, d.K, g, c->pair_count.as<uint32_t>(), s));
-  uint64_t* total = c->pair_off.as<uint64_t>() + nr;
-  MJ_TRY(launch_exclusive_scan_u32_to_u64(c->pair_count.as<uint32_t>(), c->pair_off.as<uint64_t>(), nr,
-                                          c->scan_tmp.p, total, s));
-  MJ_TRY(readback(c, total, 8, s));
-  tstop(c, 3, s);
-  const uint64_t raw = c->h_small[0];
-  c->stats.n_raw_pairs = raw;
-  if (raw == 0) return MJ_OK;
-  if (raw >= (1ull << 32)) return MJ_ERR_UNSUPPORTED;
   // Dedup by the pair bitmap when its sweep (clear, count, write: three
   // passes over n^2/16 bytes) costs less than sorting the raw pairs (about
   // 80 bytes of traffic per pair over the radix passes), unless the
   // candidates' multiplicities are wanted (only the sort gives them) or a
-  // flag forces one way.
+  // flag forces one way.  When the bitmap is at most 256 bytes per partition
+  // record (its sweep then costs about what the record sort did), the
+  // bitmap is taken without counting the raw pairs first: the marking walk
+  // counts them itself.  Otherwise a counting walk decides.
   const uint64_t bm_bytes = pair_bitmap_words(n) * 4;
-  bool use_bitmap = !want_run_start && bm_bytes > 0 && !(flags & MJ_FLAG_DEDUP_SORT) &&
-                    ((flags & MJ_FLAG_DEDUP_BITMAP) || (bm_bytes <= raw * 80 && bm_bytes <= (48ull << 30)));
-  if (use_bitmap) {
+  const bool bitmap_ok = !want_run_start && bm_bytes > 0 && !(flags & MJ_FLAG_DEDUP_SORT) &&
+                         bm_bytes <= (48ull << 30);
+  bool counted = false, use_bitmap = false;
+  uint64_t raw = 0;
+  if (bitmap_ok && ((flags & MJ_FLAG_DEDUP_BITMAP) || bm_bytes <= (uint64_t)nr * 256)) {
     const int st = c->pairbm.reserve(bm_bytes, s);
-    if (st == MJ_ERR_OOM && !(flags & MJ_FLAG_DEDUP_BITMAP)) {
-      use_bitmap = false;   // not enough device memory: sort instead
-    } else if (st != MJ_OK) {
-      return st;
+    if (st == MJ_OK) use_bitmap = true;
+    else if (st != MJ_ERR_OOM || (flags & MJ_FLAG_DEDUP_BITMAP)) return st;   // OOM without the flag: count and decide
+  }
+  if (!use_bitmap) {
+    MJ_TRY(c->pair_count.reserve((size_t)nr * 4, s));
+    MJ_TRY(c->pair_off.reserve((size_t)nr * 8 + 16, s));
+    MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(nr), s));
+    tstart(c, 3, s);
+    MJ_TRY(launch_count_pairs(r, nr, d.K, g, c->pair_count.as<uint32_t>(), s));
+    uint64_t* total = c->pair_off.as<uint64_t>() + nr;
+    MJ_TRY(launch_exclusive_scan_u32_to_u64(c->pair_count.as<uint32_t>(), c->pair_off.as<uint64_t>(), nr,
+                                            c->scan_tmp.p, total, s));
+    MJ_TRY(readback(c, total, 8, s));
+    tstop(c, 3, s);
+    raw = c->h_small[0];
+    counted = true;
+    c->stats.n_raw_pairs = raw;
+    if (raw == 0) return MJ_OK;
+    if (raw >= (1ull << 32)) return MJ_ERR_UNSUPPORTED;
+    use_bitmap = bitmap_ok && ((flags & MJ_FLAG_DEDUP_BITMAP) || bm_bytes <= raw * 80);
+    if (use_bitmap) {
+      const int st = c->pairbm.reserve(bm_bytes, s);
+      if (st == MJ_ERR_OOM && !(flags & MJ_FLAG_DEDUP_BITMAP)) {
+        use_bitmap = false;   // not enough device memory: sort instead
+      } else if (st != MJ_OK) {
+        return st;
+      }
     }
   }
   if (use_bitmap) {
@@ -505,11 +519,17 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
     MJ_CUDA_TRY(cudaMemcpyAsync(c->h_small + 1, c->small.as<unsigned long long>() + 7, 8, cudaMemcpyDeviceToHost, s));
     MJ_TRY(readback(c, ctotal, 4, s));
     const uint32_t nc = *(uint32_t*)c->h_small;
-    if (c->h_small[1] != raw) return MJ_ERR_DEVICE;   // both walks must see the same pairs
-    MJ_TRY(c->cand_i.reserve((size_t)nc * 4 + 16, s));
-    MJ_TRY(c->cand_j.reserve((size_t)nc * 4 + 16, s));
-    MJ_TRY(launch_bitmap_write(c->pairbm.as<uint32_t>(), n, c->uoffs.as<uint32_t>(), c->cand_i.as<uint32_t>(),
-                               c->cand_j.as<uint32_t>(), s));
+    if (counted && c->h_small[1] != raw) return MJ_ERR_DEVICE;   // both walks must see the same pairs
+    raw = c->h_small[1];
+    c->stats.n_raw_pairs = raw;
+    // the row counts' scan is 32-bit: the raw pairs bound the candidates
+    if (raw >= (1ull << 32)) return MJ_ERR_UNSUPPORTED;
+    if (nc) {
+      MJ_TRY(c->cand_i.reserve((size_t)nc * 4 + 16, s));
+      MJ_TRY(c->cand_j.reserve((size_t)nc * 4 + 16, s));
+      MJ_TRY(launch_bitmap_write(c->pairbm.as<uint32_t>(), n, c->uoffs.as<uint32_t>(), c->cand_i.as<uint32_t>(),
+                                 c->cand_j.as<uint32_t>(), s));
+    }
     tstop(c, 4, s);
     c->n_cand = nc;
     c->stats.n_candidates = nc;
