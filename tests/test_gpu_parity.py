@@ -326,6 +326,40 @@ def test_verify_other_alphabets(ctx):
             assert np.array_equal(got, want), (symbols.shape, K)
 
 
+def test_diag_text_digit_tables(ctx):
+    """The per-thread kernel on 7-bit text (rank codes by digit tables), forced,
+    at band widths of 1 to 5 words (both table layouts), with the last string
+    of the input in many pairs (B's bytes read near the end of the buffer)."""
+    import torch
+    import paper_1810_08833_gb300 as mj
+    rng = np.random.Generator(np.random.PCG64(41))
+    symbols = synth.PRINTABLE
+    strs = []
+    for t in range(120):
+        L = int(rng.integers(0, 700))
+        a = symbols[rng.integers(0, symbols.shape[0], size=L)]
+        strs += [a.tobytes(), synth.mutate(rng, a, float(rng.uniform(0, 0.2)), symbols).tobytes()]
+    strs.append(symbols[rng.integers(0, symbols.shape[0], size=333)].tobytes())
+    s = synth.from_strings(strs, K=40, T=40)
+    last = s.n - 1
+    pairs = [(2 * t, 2 * t + 1) for t in range(120)] + [(t, last) for t in range(0, 2 * 120, 3)]
+    pairs = np.array(pairs, np.int64)
+    data, off = to_device(s)
+    i = torch.from_numpy(pairs[:, 0].astype(np.int32)).cuda()
+    j = torch.from_numpy(pairs[:, 1].astype(np.int32)).cuda()
+    assert ctx.derive(data, off, mj.params(40, T=40))["bits"] == 7
+    ctx.set_verify_config(1, 0)
+    try:
+        for K in (7, 31, 40, 75, 100, 127, 150):
+            want = oracle.ed_band_pairs(s.bytes, s.offsets, pairs, K)
+            got = ctx.verify(data, off, i, j, K).cpu().numpy().astype(np.int64)
+            assert np.array_equal(got, want), (K, np.nonzero(got != want)[0][:10])
+            got = ctx.verify(data, off, j, i, K).cpu().numpy().astype(np.int64)
+            assert np.array_equal(got, want), K
+    finally:
+        ctx.set_verify_config(0, 0)
+
+
 def test_verify_rejects_bad_ids(ctx):
     import torch
     import paper_1810_08833_gb300 as mj
