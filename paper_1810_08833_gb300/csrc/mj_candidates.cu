@@ -467,6 +467,14 @@ __device__ __forceinline__ PairLens pair_lens(const uint32_t* __restrict__ ci, c
 
 __device__ __forceinline__ uint64_t band_cells_of(int64_t m, int64_t n, int64_t K) {   // m >= n
   if (n <= 0) return 0;
+  if (m < ((int64_t)1 << 31) && K < ((int64_t)1 << 31)) {   // the same sums with 32-bit factors
+    const uint32_t M = (uint32_t)m, N = (uint32_t)n, KK = (uint32_t)K;
+    const uint32_t a = M > KK ? min(M - KK, N) : 0u;
+    const uint64_t smin = (((uint64_t)a * (a + 1u)) >> 1) + (uint64_t)a * KK + (uint64_t)(N - a) * M;
+    const uint32_t b = min(KK, N);
+    const uint64_t smax = b + (N > KK ? (((uint64_t)(N - KK) * (N - KK + 1u)) >> 1) : 0ull);
+    return smin - smax + N;
+  }
   int64_t a = m - K;
   a = a < 0 ? 0 : (a > n ? n : a);
   const int64_t smin = a * (a + 1) / 2 + a * K + (n - a) * m;
@@ -475,16 +483,30 @@ __device__ __forceinline__ uint64_t band_cells_of(int64_t m, int64_t n, int64_t 
   return (uint64_t)(smin - smax + n);
 }
 
-// Class histogram of the pairs; with cells non-null also their K-band cells
-// (mj_stats.band_cells), summed.
-__global__ void order_hist_kernel(const uint32_t* __restrict__ ci, const uint32_t* __restrict__ cj,
-                                  const int64_t* __restrict__ offsets, uint32_t n_str, uint64_t m, uint32_t K,
-                                  uint32_t* __restrict__ hist, unsigned long long* __restrict__ cells) {
+// The histogram and the scatter give block b of G the pairs [b R, (b + 1) R)
+// (R a multiple of the scatter's chunk): the histogram writes each block's
+// class counts, block-major (bh[b * 256 + c]); the scan turns them into each
+// block's first position per class, so the scatter needs no global atomics.
+constexpr int kOrderThreads = 256;
+constexpr int kOrderItems = 4;
+constexpr uint64_t kOrderChunk = (uint64_t)kOrderThreads * kOrderItems;
+constexpr int kOrderBlocksMax = kNumSMsHint * 8;
+
+// Class histogram of each block's pairs; with cells non-null also their
+// K-band cells (mj_stats.band_cells), summed.
+__global__ void __launch_bounds__(kOrderThreads) order_hist_kernel(const uint32_t* __restrict__ ci,
+                                                                   const uint32_t* __restrict__ cj,
+                                                                   const int64_t* __restrict__ offsets, uint32_t n_str,
+                                                                   uint64_t m, uint64_t R, uint32_t K,
+                                                                   uint32_t* __restrict__ bh,
+                                                                   unsigned long long* __restrict__ cells) {
   __shared__ uint32_t h[kOrderClasses];
   for (int c = threadIdx.x; c < kOrderClasses; c += blockDim.x) h[c] = 0;
   __syncthreads();
   unsigned long long acc = 0;
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (uint64_t)gridDim.x * blockDim.x) {
+  const uint64_t t0 = (uint64_t)blockIdx.x * R;
+  const uint64_t t1 = t0 + R < m ? t0 + R : m;
+  for (uint64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
     const PairLens L = pair_lens(ci, cj, offsets, n_str, t);
     const int64_t n = L.lx < L.ly ? L.lx : L.ly, mm = L.lx < L.ly ? L.ly : L.lx;
     atomicAdd(&h[length_class((uint64_t)n)], 1u);
@@ -495,19 +517,25 @@ __global__ void order_hist_kernel(const uint32_t* __restrict__ ci, const uint32_
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(cells, acc);
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < kOrderClasses; c += blockDim.x)
-    if (h[c]) atomicAdd(hist + c, h[c]);
+  for (int c = threadIdx.x; c < kOrderClasses; c += blockDim.x) bh[(uint64_t)blockIdx.x * kOrderClasses + c] = h[c];
 }
 
-// cursor[c] = start of class c in the longest-first order; counts[b] and
-// ranges[2b], ranges[2b+1] = the pairs and [start, end) of floor(log2)
-// bucket b (n <= 1 in bucket 0).  One block of kOrderClasses threads.
-__global__ void order_scan_kernel(const uint32_t* __restrict__ hist, uint32_t* __restrict__ cursor,
-                                  uint32_t* __restrict__ counts, uint32_t* __restrict__ ranges) {
-  __shared__ uint32_t v[kOrderClasses];
+// One block of kOrderClasses threads.  Class c's pairs start at cursor c
+// (classes in descending order: longest first) and block b's pairs of
+// class c at cursor c + the counts of the blocks before b, written over bh;
+// counts[b] and ranges[2b], ranges[2b+1] = the pairs and [start, end) of
+// floor(log2) bucket b (n <= 1 in bucket 0).
+__global__ void order_scan_kernel(uint32_t* __restrict__ bh, uint32_t G, uint32_t* __restrict__ counts,
+                                  uint32_t* __restrict__ ranges) {
+  __shared__ uint32_t v[kOrderClasses], tot[kOrderClasses], cursor[kOrderClasses];
   const int c = threadIdx.x;
+  uint32_t sum = 0;
+#pragma unroll 8
+  for (uint32_t b = 0; b < G; ++b) sum += bh[(uint64_t)b * kOrderClasses + c];
+  tot[c] = sum;
+  __syncthreads();
   // exclusive scan over classes in descending order
-  v[c] = hist[kOrderClasses - 1 - c];
+  v[c] = tot[kOrderClasses - 1 - c];
   __syncthreads();
   for (int o = 1; o < kOrderClasses; o <<= 1) {
     const uint32_t y = c >= o ? v[c - o] : 0u;
@@ -516,9 +544,15 @@ __global__ void order_scan_kernel(const uint32_t* __restrict__ hist, uint32_t* _
     __syncthreads();
   }
   const int cls = kOrderClasses - 1 - c;
-  const uint32_t end = v[c], start = end - hist[cls];
-  cursor[cls] = start;
+  cursor[cls] = v[c] - tot[cls];
   __syncthreads();
+  uint32_t run = cursor[c];
+  for (uint32_t b = 0; b < G; ++b) {
+    const uint64_t at = (uint64_t)b * kOrderClasses + c;
+    const uint32_t x = bh[at];
+    bh[at] = run;
+    run += x;
+  }
   if (c < kLenBuckets) {
     // classes of bucket b: n in [2^b, 2^(b+1)) (b = 0: n <= 1)
     const int b = c;
@@ -527,42 +561,42 @@ __global__ void order_scan_kernel(const uint32_t* __restrict__ hist, uint32_t* _
     else if (b == 1) { lo = 2; hi = 3; }
     else if (b == 2) { lo = 4; hi = 7; }
     else { lo = (b - 2) * 8; hi = lo + 7; }
-    // longest first: class hi comes first; the bucket spans [cursor[hi], cursor[lo] + hist[lo])
+    // longest first: class hi comes first; the bucket spans [cursor[hi], cursor[lo] + tot[lo])
     uint32_t cnt = 0;
-    for (int k = lo; k <= hi; ++k) cnt += hist[k];
+    for (int k = lo; k <= hi; ++k) cnt += tot[k];
     counts[b] = cnt;
     ranges[2 * b] = cursor[hi];
     ranges[2 * b + 1] = cursor[hi] + cnt;
   }
 }
 
-// Scatter into the order, a chunk of kOrderThreads * kOrderItems pairs per
-// block step: ranks within the chunk from shared-memory counters, then one
-// global reservation per class and chunk.
-constexpr int kOrderThreads = 256;
-constexpr int kOrderItems = 4;
-
+// Scatter of each block's pairs into the order, a chunk of kOrderChunk pairs
+// at a time: ranks within the chunk from shared-memory counters, positions
+// from the block's running base per class.
 __global__ void __launch_bounds__(kOrderThreads) order_scatter_kernel(const uint32_t* __restrict__ ci,
                                                                      const uint32_t* __restrict__ cj,
                                                                      const int64_t* __restrict__ offsets,
-                                                                     uint32_t n_str, uint64_t m,
-                                                                     uint32_t* __restrict__ cursor,
+                                                                     uint32_t n_str, uint64_t m, uint64_t R,
+                                                                     const uint32_t* __restrict__ bbase,
                                                                      uint32_t* __restrict__ order,
                                                                      uint4* __restrict__ geo) {
   __shared__ uint32_t h[kOrderClasses];
-  __shared__ uint32_t base[kOrderClasses];
-  constexpr uint64_t kChunk = (uint64_t)kOrderThreads * kOrderItems;
-  const uint64_t chunks = (m + kChunk - 1) / kChunk;
-  for (uint64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
-    for (int c = threadIdx.x; c < kOrderClasses; c += kOrderThreads) h[c] = 0;
-    __syncthreads();
+  __shared__ uint32_t run[kOrderClasses];
+  for (int c = threadIdx.x; c < kOrderClasses; c += kOrderThreads) {
+    h[c] = 0;
+    run[c] = bbase[(uint64_t)blockIdx.x * kOrderClasses + c];
+  }
+  __syncthreads();
+  const uint64_t t0 = (uint64_t)blockIdx.x * R;
+  const uint64_t t1 = t0 + R < m ? t0 + R : m;
+  for (uint64_t base = t0; base < t1; base += kOrderChunk) {
     uint32_t cls[kOrderItems], rank[kOrderItems];
     uint4 g[kOrderItems];
 #pragma unroll
     for (int k = 0; k < kOrderItems; ++k) {
-      const uint64_t t = ch * kChunk + (uint64_t)k * kOrderThreads + threadIdx.x;
+      const uint64_t t = base + (uint64_t)k * kOrderThreads + threadIdx.x;
       cls[k] = 0xffffffffu;
-      if (t < m) {
+      if (t < t1) {
         const PairLens L = pair_lens(ci, cj, offsets, n_str, t);
         const bool xa = L.lx >= L.ly;
         g[k] = L.bad ? make_uint4(0u, 0u, 0u, kGeoBadIds)
@@ -573,17 +607,19 @@ __global__ void __launch_bounds__(kOrderThreads) order_scatter_kernel(const uint
       }
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < kOrderClasses; c += kOrderThreads)
-      if (h[c]) base[c] = atomicAdd(cursor + c, h[c]);
-    __syncthreads();
 #pragma unroll
     for (int k = 0; k < kOrderItems; ++k) {
-      const uint64_t t = ch * kChunk + (uint64_t)k * kOrderThreads + threadIdx.x;
+      const uint64_t t = base + (uint64_t)k * kOrderThreads + threadIdx.x;
       if (cls[k] != 0xffffffffu) {
-        const uint32_t pos = base[cls[k]] + rank[k];
+        const uint32_t pos = run[cls[k]] + rank[k];
         order[pos] = (uint32_t)t;
         if (geo) geo[pos] = g[k];
       }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < kOrderClasses; c += kOrderThreads) {
+      run[c] += h[c];
+      h[c] = 0;
     }
     __syncthreads();
   }
@@ -751,21 +787,17 @@ int launch_compact_pairs(const uint64_t* sorted, const uint32_t* flags, const ui
 int launch_length_order(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint32_t n_str, uint64_t m,
                         uint32_t K, uint32_t* scratch, uint32_t* order, uint4* geo, uint32_t* counts,
                         uint32_t* ranges, unsigned long long* cells, cudaStream_t s) {
-  uint32_t* hist = scratch;
-  uint32_t* cursor = scratch + kOrderClasses;
-  MJ_CUDA_TRY(cudaMemsetAsync(hist, 0, kOrderClasses * sizeof(uint32_t), s));
+  // G blocks of R pairs (R a whole number of chunks), at least one block
+  const uint64_t chunks = (m + kOrderChunk - 1) / kOrderChunk;
+  const uint32_t G = (uint32_t)(chunks < 1 ? 1 : (chunks < (uint64_t)kOrderBlocksMax ? chunks : kOrderBlocksMax));
+  const uint64_t R = (chunks + G - 1) / G * kOrderChunk;
   if (cells) MJ_CUDA_TRY(cudaMemsetAsync(cells, 0, sizeof(unsigned long long), s));
-  if (m) {
-    order_hist_kernel<<<grid_for(m), 256, 0, s>>>(ci, cj, offsets, n_str, m, K, hist, cells);
-    MJ_KERNEL_DONE();
-  }
-  order_scan_kernel<<<1, kOrderClasses, 0, s>>>(hist, cursor, counts, ranges);
+  order_hist_kernel<<<G, kOrderThreads, 0, s>>>(ci, cj, offsets, n_str, m, R, K, scratch, cells);
+  MJ_KERNEL_DONE();
+  order_scan_kernel<<<1, kOrderClasses, 0, s>>>(scratch, G, counts, ranges);
   MJ_KERNEL_DONE();
   if (m) {
-    const uint64_t chunks = (m + (uint64_t)kOrderThreads * kOrderItems - 1) / ((uint64_t)kOrderThreads * kOrderItems);
-    const uint64_t cap = (uint64_t)kNumSMsHint * 8;
-    order_scatter_kernel<<<(unsigned)(chunks < cap ? chunks : cap), kOrderThreads, 0, s>>>(ci, cj, offsets, n_str, m,
-                                                                                            cursor, order, geo);
+    order_scatter_kernel<<<G, kOrderThreads, 0, s>>>(ci, cj, offsets, n_str, m, R, scratch, order, geo);
     MJ_KERNEL_DONE();
   }
   return MJ_OK;

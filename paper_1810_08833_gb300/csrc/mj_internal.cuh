@@ -255,9 +255,10 @@ int fewest_lanes_for(uint32_t kmax);
 // arbitrary.  counts[b] and ranges[2b], ranges[2b+1] = [start, end) of the
 // pairs whose shorter length has floor(log2) = b (lengths 0 and 1: b = 0),
 // the autotuner's length buckets, contiguous and longest first.  scratch:
-// kOrderScratchWords words.
+// kOrderScratchWords words (256 class counts for each of up to 8 blocks per
+// SM of the counting sort).
 constexpr int kLenBuckets = 32;
-constexpr int kOrderScratchWords = 512;
+constexpr int kOrderScratchWords = 256 * kNumSMsHint * 8;
 // cells (nullable): set to the pairs' K-band cells (mj_stats.band_cells).
 // geo (nullable): the pairs' geometry at their order positions (VerifyArgs::
 // pair_geo).  Pair ids >= n_str count as empty strings here (the verifier
