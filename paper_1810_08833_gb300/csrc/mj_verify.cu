@@ -375,6 +375,13 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
   }
   constexpr int kChunk = kChunkFor<W>;
   const int32_t cnt = min(kChunk, st.n - j0 + 1);
+  // The top row's D moves along a diagonal, so it rises by 0 or 1 per
+  // column: by 1 exactly when the vertical delta entering the row and the
+  // horizontal delta leaving it are +1 and 0 or 0 and +1 (the pairs summing
+  // to 2 or -2 cannot occur).  Bit 0 of (Pv | Ph) & ~(Mv | Mh) per column,
+  // shifted into `rises` (one bit per column, at most 32), and counted at the
+  // end of the chunk.
+  uint32_t rises = 0;
 #pragma unroll 8   // part of the chunk: a smaller body is fetched better (measured)
   for (int c = 0; c < kChunk; ++c) {
     if (c >= cnt) break;
@@ -403,8 +410,6 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
 #pragma unroll
     for (int w = 0; w < W; ++w) Eq[w] = __funnelshift_r(EqF[w], EqF[w + 1], (uint32_t)c);
 
-    // the band has slid down one row already (the vectors are kept shifted)
-    const int32_t sv = (int32_t)(st.Pv[0] & 1u) - (int32_t)(st.Mv[0] & 1u);
 
     uint32_t Xv[W], Ph[W], Mh[W], EP[W], SUM[W];
 #pragma unroll
@@ -417,7 +422,9 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
       Ph[w] = st.Mv[w] | ~(Xh | st.Pv[w]);
       Mh[w] = st.Pv[w] & Xh;
     }
-    st.score += sv + (int32_t)(Ph[0] & 1u) - (int32_t)(Mh[0] & 1u);
+    // the band has slid down one row already (the vectors are kept shifted):
+    // bit 0 of Pv / Mv is the vertical delta entering the top row
+    rises = __funnelshift_r(rises, (st.Pv[0] | Ph[0]) & ~(st.Mv[0] | Mh[0]), 1);
     // Myers' update Pv' = (Mh << 1) | ~(Xv | (Ph << 1) | 1), Mv' = ((Ph << 1) | 1)
     // & Xv, followed by the next column's slide (>> 1, Pv's new bottom row +1),
     // is Pv = Mh | ~((Xv >> 1) | Ph) | top, Mv = Ph & (Xv >> 1): one shift
@@ -433,6 +440,7 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
   const int32_t jend = j0 + cnt - 1;
   st.j = jend + 1;
   st.bpos += (uint64_t)cnt;
+  st.score += __popc(rises);
   // D on diagonal d0 at column jend: a lower bound of D[m][n] (exact at n);
   // M1 (kept shifted like the vectors) selects the rows below the top row
   // down to diagonal d0
