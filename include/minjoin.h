@@ -177,8 +177,9 @@ typedef struct {
    * last mj_join, in this order: 0 anchor test (Alg. 2), 1 partition
    * records from the anchors (Alg. 1), 2 record grouping sort, 3 pair emission
    * (filters of Alg. 3), 4 pair dedup, 5 equality bit-planes, 6 verification
-   * kernel(s), 7 output compaction */
-  float ms_section[8];
+   * kernel(s), 7 output compaction, 8 the candidates' longest-first order for
+   * verification (a counting sort) */
+  float ms_section[9];
   uint64_t verify_word_columns; /* 32-bit band words x columns the verifier advanced */
 } mj_stats;
 

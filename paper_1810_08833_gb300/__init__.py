@@ -91,11 +91,11 @@ class Stats(ctypes.Structure):
                 ("fallback_pairs", ctypes.c_uint64), ("device_flags", ctypes.c_uint32),
                 ("ms_derive", ctypes.c_float), ("ms_partition", ctypes.c_float),
                 ("ms_join_filter", ctypes.c_float), ("ms_verify", ctypes.c_float), ("ms_total", ctypes.c_float),
-                ("n_launches", ctypes.c_uint64), ("ms_section", ctypes.c_float * 8),
+                ("n_launches", ctypes.c_uint64), ("ms_section", ctypes.c_float * 9),
                 ("verify_word_columns", ctypes.c_uint64)]
 
 SECTIONS = ("anchor_test", "partition_records", "record_sort", "pair_emission", "pair_dedup", "eq_planes",
-            "verify_kernel", "output_compaction")
+            "verify_kernel", "output_compaction", "verify_order")
 
 
 VP = ctypes.c_void_p

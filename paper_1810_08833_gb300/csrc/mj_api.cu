@@ -195,10 +195,15 @@ struct mj_ctx {
   bool have_part = false, have_cand = false, have_out = false;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   // section timers of mj_join (mj_stats.ms_section)
-  static constexpr int kSections = 8;
+  static constexpr int kSections = 9;
   cudaEvent_t sec_ev[2 * kSections] = {};
   bool sec_used[kSections] = {};
   bool timing = false;
+  // while the verification stage is captured, section events become event
+  // nodes of the graph (recorded at every replay); graph_sections: the
+  // sections the captured graph records
+  bool capturing = false;
+  uint32_t graph_sections = 0;
   uint64_t launches_at_start = 0;
 };
 
@@ -224,14 +229,25 @@ int readback(mj_ctx* c, const void* d_src, size_t bytes, cudaStream_t s) {
 }
 
 // A section's interval runs from its first start to its last stop in a call.
+void record_event(mj_ctx* c, cudaEvent_t e, cudaStream_t s) {
+  if (c->capturing) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else cudaEventRecord(e, s);
+}
 void tstart(mj_ctx* c, int i, cudaStream_t s) {
   if (c->timing && !c->sec_used[i]) {
-    cudaEventRecord(c->sec_ev[2 * i], s);
+    record_event(c, c->sec_ev[2 * i], s);
     c->sec_used[i] = true;
+    if (c->capturing) c->graph_sections |= 1u << i;
   }
 }
 void tstop(mj_ctx* c, int i, cudaStream_t s) {
-  if (c->timing) cudaEventRecord(c->sec_ev[2 * i + 1], s);
+  if (c->timing) record_event(c, c->sec_ev[2 * i + 1], s);
+}
+// after a replay of the verification graph: its event nodes timed these
+void mark_graph_sections(mj_ctx* c) {
+  if (!c->timing) return;
+  for (int i = 0; i < mj_ctx::kSections; ++i)
+    if (c->graph_sections & (1u << i)) c->sec_used[i] = true;
 }
 
 void begin_call(mj_ctx* c, bool timing) {
@@ -652,9 +668,11 @@ int pair_order(mj_ctx* c, const uint32_t* ci, const uint32_t* cj, const int64_t*
                const uint32_t** order, cudaStream_t s) {
   if (!c->small.p || !c->branges.p || !c->idx.p || !c->geo.p) return MJ_ERR_STATE;   // order_buffers comes first
   uint32_t* counts = c->branges.as<uint32_t>();
+  tstart(c, 8, s);
   MJ_TRY(launch_length_order(ci, cj, d_offsets, (uint32_t)c->stats.n_strings, m, c->d.K, counts + kOrderScratchAt,
                              c->idx.as<uint32_t>(), c->geo.as<uint4>(), counts, counts + kLenBuckets,
                              c->small.as<unsigned long long>() + 9, s));
+  tstop(c, 8, s);
   *order = c->idx.as<uint32_t>();
   c->geo_valid = true;   // c->geo matches the order in c->idx
   return MJ_OK;
@@ -707,7 +725,7 @@ int verify_ordered_graph(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_off
   // streams run the stage uncaptured
   const bool capturable = s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
   if (!c->vcfg.graph || !capturable) return verify_ordered(c, d_bytes, d_offsets, ci, cj, m, K, ed, s);
-  uint64_t plan = c->vcfg.kernel * 131u + c->vcfg.lanes * 7u + c->vcfg.batching;
+  uint64_t plan = (c->vcfg.kernel * 131u + c->vcfg.lanes * 7u + c->vcfg.batching) * 2u + (c->timing ? 1u : 0u);
   if (c->tuned) {
     for (int b = 0; b < kLenBuckets; ++b) plan = plan * 1000003u + c->tuned_kernel[b] * 64u + c->tuned_lanes[b];
   }
@@ -716,9 +734,8 @@ int verify_ordered_graph(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_off
                             (uint64_t)c->small.p, (uint64_t)c->idx.p, (uint64_t)c->branges.p,
                             (uint64_t)c->dev_flags.p, c->out_collect ? (uint64_t)c->out_t.p : 0, (uint64_t)c->geo.p};
   if (c->graph_exec && memcmp(sig, c->graph_sig, sizeof(sig)) == 0) {
-    tstart(c, 6, s);   // the verify section spans the replay
     MJ_CUDA_TRY(cudaGraphLaunch(c->graph_exec, s));
-    tstop(c, 6, s);
+    mark_graph_sections(c);
     c->launches_at_start -= c->graph_launches;   // kernels replayed by the graph
     return MJ_OK;
   }
@@ -730,14 +747,19 @@ int verify_ordered_graph(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_off
     cudaGraphExecDestroy(c->graph_exec);
     c->graph_exec = nullptr;
   }
-  const bool timing = c->timing;
-  c->timing = false;   // no section events inside the graph
+  // the sections inside the stage are timed by event nodes of the graph
+  bool used[mj_ctx::kSections];
+  memcpy(used, c->sec_used, sizeof(used));
+  for (bool& u : c->sec_used) u = false;
+  c->graph_sections = 0;
   const uint64_t before = launch_count();
   MJ_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+  c->capturing = true;
   const int st = verify_ordered(c, d_bytes, d_offsets, ci, cj, m, K, ed, s);
+  c->capturing = false;
   cudaGraph_t graph = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(s, &graph);
-  c->timing = timing;
+  memcpy(c->sec_used, used, sizeof(used));
   if (st != MJ_OK) {
     if (graph) cudaGraphDestroy(graph);
     return st;
@@ -748,9 +770,8 @@ int verify_ordered_graph(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_off
   MJ_CUDA_TRY(ie);
   c->graph_launches = launch_count() - before;
   memcpy(c->graph_sig, sig, sizeof(sig));
-  tstart(c, 6, s);
   MJ_CUDA_TRY(cudaGraphLaunch(c->graph_exec, s));
-  tstop(c, 6, s);
+  mark_graph_sections(c);
   return MJ_OK;
 }
 
