@@ -739,8 +739,32 @@ __global__ void __launch_bounds__(128, P <= 2 ? 8 : 1) verify_wave_kernel(Verify
     // outside its block's steps computes on stale state (rebuilt at the
     // block's first column) that no other lane reads.  First and last
     // columns and the diagonal test take one rarely divergent branch.
-#pragma unroll 8   // a quarter of the steps: a smaller loop body is fetched better (measured)
-    for (int it = 0; it < kWaveSteps; ++it) {
+    // Steps in which no lane of the warp meets such an event (a block's first
+    // or last column, its input word switching from the predecessor's to the
+    // band edge's, the window's last step) run in a loop without the tests:
+    // their number is the warp's minimum of the steps to each lane's next
+    // event.
+    int it = 0;
+    while (it < kWaveSteps) {
+      {
+        const int64_t un = (int64_t)u + 1;   // u at the next step
+        int64_t fr = kWaveSteps - 1 - it;
+        if (un <= 0) fr = min(fr, -un);
+        if (un <= span) fr = min(fr, (int64_t)span - un);
+        if (un <= u_valid) fr = min(fr, (int64_t)u_valid - un + 1);
+        const int free = __reduce_min_sync(0xffffffffu, (int)fr);
+        const bool from_prev = un <= u_valid;
+#pragma unroll 4
+        for (int f = 0; f < free; ++f) {
+          const uint32_t w_in = __shfl_sync(0xffffffffu, pub, prev_lane);
+          const uint32_t wv = from_prev ? w_in : kIdle;
+          uint32_t Ph, hn;
+          wave_column<P>(pa, bw, wv, Pv, Mv, T, Ph, hn);
+          pub = ((Ph & 0x80000000u) | T) + hn;
+        }
+        u += free;
+        it += free;
+      }
       const uint32_t w_in = __shfl_sync(0xffffffffu, pub, prev_lane);
       ++u;
       const uint32_t wv = u <= u_valid ? w_in : kIdle;
@@ -780,6 +804,7 @@ __global__ void __launch_bounds__(128, P <= 2 ? 8 : 1) verify_wave_kernel(Verify
           take_block(b + G, sbase + it + 1);
         }
       }
+      ++it;
     }
     sbase += kWaveSteps;
     if ((sbase & 31) == 0 && u >= 0 && u <= span) {   // B's symbols of the next 32 columns, all lanes at once
