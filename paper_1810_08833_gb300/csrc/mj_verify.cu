@@ -289,14 +289,16 @@ constexpr int kChunkFor = W <= 2 ? 16 : 32;
 // that column j0 + c needs a shift by c < 32), and B's plane bits of the
 // columns, bit-reversed so that the next column's bit is the sign bit.
 // Text (7 bit-planes): equality bits by digit tables.  Per chunk, every
-// thread writes to shared memory, for each of A's band words, the 16 masks
-// "rows whose rank code has low digit d" (code bits 0-3) and the 8 masks "high
-// digit e" (bits 4-6); a column then takes its symbol's rank code from B's
-// bytes and ANDs one mask of each table: two loads per word instead of 7
-// XNOR-ANDs.  Tables: word (d * (W + 1) + w) * 128 + thread.
-constexpr int kDigitLo = 16, kDigitHi = 8;
+// thread writes to shared memory, for each of A's band words, the masks "rows
+// whose rank code has digit value d" for three digits of the code: 8 masks
+// for bits 0-2, 4 for bits 3-4 and 4 for bits 5-6; a column then takes its
+// symbol's rank code from B's bytes and ANDs one mask of each table (one
+// three-input logic op per word).  Tables: word (d * (W + 1) + w) * 128 +
+// thread, the three back to back.  (Two digits of 4 and 3 bits, 24 masks a
+// word, take 50% more shared memory: 4 blocks per SM instead of 6.)
+constexpr int kDigitA = 8, kDigitB = 4, kDigitC = 4;
 template <int W>
-constexpr size_t digit_smem_bytes() { return 256 + (size_t)(kDigitLo + kDigitHi) * (W + 1) * 128 * 4; }
+constexpr size_t digit_smem_bytes() { return 256 + (size_t)(kDigitA + kDigitB + kDigitC) * (W + 1) * 128 * 4; }
 
 template <int W, int P>
 __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs& a, uint64_t PW, uint32_t* res,
@@ -333,19 +335,23 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
     }
     if (kDigits) {
       const int tid = threadIdx.x;
+      uint32_t* dB = dlo + kDigitA * (W + 1) * 128;
 #pragma unroll
       for (int w = 0; w <= W; ++w) {
-        const uint32_t a0 = pa[0][w], a1 = pa[1][w], a2 = pa[2][w], a3 = pa[3][w];
+        const uint32_t a0 = pa[0][w], a1 = pa[1][w], a2 = pa[2][w];
         const uint32_t t2[4] = {~a0 & ~a1, a0 & ~a1, ~a0 & a1, a0 & a1};
-        uint32_t t3[8];
 #pragma unroll
-        for (int d = 0; d < 8; ++d) t3[d] = t2[d & 3] & ((d & 4) ? a2 : ~a2);
-#pragma unroll
-        for (int d = 0; d < kDigitLo; ++d) dlo[(d * (W + 1) + w) * 128 + tid] = t3[d & 7] & ((d & 8) ? a3 : ~a3);
-        const uint32_t a4 = pa[4][w], a5 = pa[5][w], a6 = pa[6][w];
-        const uint32_t h2[4] = {~a4 & ~a5, a4 & ~a5, ~a4 & a5, a4 & a5};
-#pragma unroll
-        for (int e = 0; e < kDigitHi; ++e) dhi[(e * (W + 1) + w) * 128 + tid] = h2[e & 3] & ((e & 4) ? a6 : ~a6);
+        for (int d = 0; d < kDigitA; ++d) dlo[(d * (W + 1) + w) * 128 + tid] = t2[d & 3] & ((d & 4) ? a2 : ~a2);
+        const uint32_t a3 = pa[3][w], a4 = pa[4][w];
+        dB[(0 * (W + 1) + w) * 128 + tid] = ~a3 & ~a4;
+        dB[(1 * (W + 1) + w) * 128 + tid] = a3 & ~a4;
+        dB[(2 * (W + 1) + w) * 128 + tid] = ~a3 & a4;
+        dB[(3 * (W + 1) + w) * 128 + tid] = a3 & a4;
+        const uint32_t a5 = pa[5][w], a6 = pa[6][w];
+        dhi[(0 * (W + 1) + w) * 128 + tid] = ~a5 & ~a6;
+        dhi[(1 * (W + 1) + w) * 128 + tid] = a5 & ~a6;
+        dhi[(2 * (W + 1) + w) * 128 + tid] = ~a5 & a6;
+        dhi[(3 * (W + 1) + w) * 128 + tid] = a5 & a6;
       }
       // B's bytes of columns j0 .. j0 + 31, aligned so that column j0 + c is
       // byte c (words beyond the input read as zero)
@@ -389,10 +395,11 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
     uint32_t EqF[W + 1];
     if (kDigits) {
       const uint32_t code = s_rank[(bsym[c >> 2] >> (8 * (c & 3))) & 255u];
-      const uint32_t* lo = dlo + (code & 15u) * (W + 1) * 128 + threadIdx.x;
-      const uint32_t* hi = dhi + (code >> 4) * (W + 1) * 128 + threadIdx.x;
+      const uint32_t* ta = dlo + (code & 7u) * (W + 1) * 128 + threadIdx.x;
+      const uint32_t* tb = dlo + (kDigitA + ((code >> 3) & 3u)) * (W + 1) * 128 + threadIdx.x;
+      const uint32_t* tc = dhi + (code >> 5) * (W + 1) * 128 + threadIdx.x;
 #pragma unroll
-      for (int w = 0; w <= W; ++w) EqF[w] = lo[w * 128] & hi[w * 128];
+      for (int w = 0; w <= W; ++w) EqF[w] = ta[w * 128] & tb[w * 128] & tc[w * 128];
     } else {
 #pragma unroll
       for (int w = 0; w <= W; ++w) EqF[w] = 0xffffffffu;
@@ -466,8 +473,8 @@ __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t
                                                           unsigned long long* __restrict__ next) {
   extern __shared__ __align__(16) uint32_t vsm[];   // text: rank table, then the digit tables
   uint8_t* s_rank = reinterpret_cast<uint8_t*>(vsm);
-  uint32_t* dlo = vsm + 64;
-  uint32_t* dhi = dlo + kDigitLo * (W + 1) * 128;
+  uint32_t* dlo = vsm + 64;   // digit tables A and B, then C
+  uint32_t* dhi = dlo + (kDigitA + kDigitB) * (W + 1) * 128;
   if (P == 7) {
     for (int b = threadIdx.x; b < 256; b += blockDim.x) s_rank[b] = a.rank_table[b];
     __syncthreads();
