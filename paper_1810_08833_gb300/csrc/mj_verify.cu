@@ -288,23 +288,77 @@ constexpr int kChunkFor = W <= 2 ? 16 : 32;
 // plane words of the rows the band covers in these columns (pre-shifted so
 // that column j0 + c needs a shift by c < 32), and B's plane bits of the
 // columns, bit-reversed so that the next column's bit is the sign bit.
-// Text (7 bit-planes): equality bits by digit tables.  Per chunk, every
+// Equality bits by digit tables (2, 5 and 7 bit-planes).  Per chunk, every
 // thread writes to shared memory, for each of A's band words, the masks "rows
-// whose rank code has digit value d" for three digits of the code: 8 masks
-// for bits 0-2, 4 for bits 3-4 and 4 for bits 5-6; a column then takes its
-// symbol's rank code from B's bytes and ANDs one mask of each table (one
-// three-input logic op per word).  Tables: word (d * (W + 1) + w) * 128 +
-// thread, the three back to back.  (Two digits of 4 and 3 bits, 24 masks a
-// word, take 50% more shared memory: 4 blocks per SM instead of 6.)
-constexpr int kDigitA = 8, kDigitB = 4, kDigitC = 4;
-template <int W>
-constexpr size_t digit_smem_bytes() { return 256 + (size_t)(kDigitA + kDigitB + kDigitC) * (W + 1) * 128 * 4; }
+// whose rank code has digit value d" for each digit of the code: one digit of
+// 2 bits for 2 planes (4 masks), 3 + 2 bits for 5 planes (8 + 4), 3 + 2 + 2
+// bits for 7 planes (8 + 4 + 4); a column then takes its symbol's rank code
+// from B's bytes and ANDs one mask of each digit's table (one load per word
+// for 2 planes, one three-input logic op per word for 7), instead of an XNOR
+// per plane and word.  Tables: word (d * (W + 1) + w) * 128 + thread, the
+// digits' tables back to back.  (For 7 planes, two digits of 4 and 3 bits,
+// 24 masks a word, take 50% more shared memory: 4 blocks per SM instead of
+// 6.)  8 planes (byte alphabets) keep the XNORs.
+template <int P>
+constexpr bool kDigitTables = P == 2 || P == 5 || P == 7;
+template <int P>
+constexpr int digit_masks() { return P == 2 ? 4 : (P == 5 ? 12 : 16); }
+template <int W, int P>
+constexpr size_t digit_smem_bytes() { return 256 + (size_t)digit_masks<P>() * (W + 1) * 128 * 4; }
+
+// The masks of band word w (A's pre-shifted plane words pa) into the tables.
+template <int W, int P>
+__device__ __forceinline__ void build_digit_tables(const uint32_t (&pa)[P][W + 1], int w, uint32_t* __restrict__ tab,
+                                                   int tid) {
+  auto put = [&](int d, uint32_t v) { tab[(d * (W + 1) + w) * 128 + tid] = v; };
+  auto two = [&](int p, int base) {   // a 2-bit digit from planes p, p + 1
+    const uint32_t x = pa[p][w], y = pa[p + 1][w];
+    put(base + 0, ~x & ~y);
+    put(base + 1, x & ~y);
+    put(base + 2, ~x & y);
+    put(base + 3, x & y);
+  };
+  if constexpr (P == 2) {
+    two(0, 0);
+  } else {
+    // a 3-bit digit from planes 0-2
+    const uint32_t a0 = pa[0][w], a1 = pa[1][w], a2 = pa[2][w];
+    const uint32_t t2[4] = {~a0 & ~a1, a0 & ~a1, ~a0 & a1, a0 & a1};
+#pragma unroll
+    for (int d = 0; d < 8; ++d) put(d, t2[d & 3] & ((d & 4) ? a2 : ~a2));
+    two(3, 8);
+    if constexpr (P == 7) two(5, 12);
+  }
+}
+
+// The equality bits of a symbol with rank code `code` over the band's words.
+template <int W, int P>
+__device__ __forceinline__ void digit_lookup(const uint32_t* __restrict__ tab, uint32_t code, int tid,
+                                             uint32_t (&EqF)[W + 1]) {
+  constexpr int S = (W + 1) * 128;
+  if constexpr (P == 2) {
+    const uint32_t* t = tab + code * S + tid;
+#pragma unroll
+    for (int w = 0; w <= W; ++w) EqF[w] = t[w * 128];
+  } else if constexpr (P == 5) {
+    const uint32_t* ta = tab + (code & 7u) * S + tid;
+    const uint32_t* tb = tab + (8u + (code >> 3)) * S + tid;
+#pragma unroll
+    for (int w = 0; w <= W; ++w) EqF[w] = ta[w * 128] & tb[w * 128];
+  } else {
+    const uint32_t* ta = tab + (code & 7u) * S + tid;
+    const uint32_t* tb = tab + (8u + ((code >> 3) & 3u)) * S + tid;
+    const uint32_t* tc = tab + (12u + (code >> 5)) * S + tid;
+#pragma unroll
+    for (int w = 0; w <= W; ++w) EqF[w] = ta[w * 128] & tb[w * 128] & tc[w * 128];
+  }
+}
 
 template <int W, int P>
 __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs& a, uint64_t PW, uint32_t* res,
-                                           uint32_t* __restrict__ dlo, uint32_t* __restrict__ dhi,
-                                           const uint8_t* __restrict__ s_rank, uint32_t GW) {
-  constexpr bool kDigits = P == 7;
+                                           uint32_t* __restrict__ tab, const uint8_t* __restrict__ s_rank,
+                                           uint32_t GW) {
+  constexpr bool kDigits = kDigitTables<P>;
   const int32_t j0 = st.j;
   uint32_t pa[P][W + 1];
   uint32_t bw[P];
@@ -335,24 +389,8 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
     }
     if (kDigits) {
       const int tid = threadIdx.x;
-      uint32_t* dB = dlo + kDigitA * (W + 1) * 128;
 #pragma unroll
-      for (int w = 0; w <= W; ++w) {
-        const uint32_t a0 = pa[0][w], a1 = pa[1][w], a2 = pa[2][w];
-        const uint32_t t2[4] = {~a0 & ~a1, a0 & ~a1, ~a0 & a1, a0 & a1};
-#pragma unroll
-        for (int d = 0; d < kDigitA; ++d) dlo[(d * (W + 1) + w) * 128 + tid] = t2[d & 3] & ((d & 4) ? a2 : ~a2);
-        const uint32_t a3 = pa[3][w], a4 = pa[4][w];
-        dB[(0 * (W + 1) + w) * 128 + tid] = ~a3 & ~a4;
-        dB[(1 * (W + 1) + w) * 128 + tid] = a3 & ~a4;
-        dB[(2 * (W + 1) + w) * 128 + tid] = ~a3 & a4;
-        dB[(3 * (W + 1) + w) * 128 + tid] = a3 & a4;
-        const uint32_t a5 = pa[5][w], a6 = pa[6][w];
-        dhi[(0 * (W + 1) + w) * 128 + tid] = ~a5 & ~a6;
-        dhi[(1 * (W + 1) + w) * 128 + tid] = a5 & ~a6;
-        dhi[(2 * (W + 1) + w) * 128 + tid] = ~a5 & a6;
-        dhi[(3 * (W + 1) + w) * 128 + tid] = a5 & a6;
-      }
+      for (int w = 0; w <= W; ++w) build_digit_tables<W, P>(pa, w, tab, tid);
       // B's bytes of columns j0 .. j0 + 31, aligned so that column j0 + c is
       // byte c (words beyond the input read as zero)
       const uint64_t bi = st.bpos - 32 * (uint64_t)GW;   // byte index of column j0's symbol
@@ -393,13 +431,9 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
     if (c >= cnt) break;
     // equality bits of column j0 + c: A's plane bits XNOR B's, over the planes
     uint32_t EqF[W + 1];
-    if (kDigits) {
+    if constexpr (kDigits) {
       const uint32_t code = s_rank[(bsym[c >> 2] >> (8 * (c & 3))) & 255u];
-      const uint32_t* ta = dlo + (code & 7u) * (W + 1) * 128 + threadIdx.x;
-      const uint32_t* tb = dlo + (kDigitA + ((code >> 3) & 3u)) * (W + 1) * 128 + threadIdx.x;
-      const uint32_t* tc = dhi + (code >> 5) * (W + 1) * 128 + threadIdx.x;
-#pragma unroll
-      for (int w = 0; w <= W; ++w) EqF[w] = ta[w * 128] & tb[w * 128] & tc[w * 128];
+      digit_lookup<W, P>(tab, code, threadIdx.x, EqF);
     } else {
 #pragma unroll
       for (int w = 0; w <= W; ++w) EqF[w] = 0xffffffffu;
@@ -471,11 +505,10 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
 template <int W, int P>
 __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t PW, uint32_t GW,
                                                           unsigned long long* __restrict__ next) {
-  extern __shared__ __align__(16) uint32_t vsm[];   // text: rank table, then the digit tables
+  extern __shared__ __align__(16) uint32_t vsm[];   // digit tables: the rank table, then the tables
   uint8_t* s_rank = reinterpret_cast<uint8_t*>(vsm);
-  uint32_t* dlo = vsm + 64;   // digit tables A and B, then C
-  uint32_t* dhi = dlo + (kDigitA + kDigitB) * (W + 1) * 128;
-  if (P == 7) {
+  uint32_t* tab = vsm + 64;   // the digit tables
+  if (kDigitTables<P>) {
     for (int b = threadIdx.x; b < 256; b += blockDim.x) s_rank[b] = a.rank_table[b];
     __syncthreads();
   }
@@ -530,7 +563,7 @@ __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t
     if (active) {
       uint32_t res;
       const int32_t j_before = st.j;
-      const bool done = pair_chunk<W, P>(st, a, PW, &res, dlo, dhi, s_rank, GW);
+      const bool done = pair_chunk<W, P>(st, a, PW, &res, tab, s_rank, GW);
       work += (uint64_t)(st.j - j_before) * W;
       if (done) {
         put_result(a, st.t, res);
@@ -1129,8 +1162,8 @@ int launch_wp(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long*
   int dev = 0, sms = kNumSMsHint, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = P == 7 ? digit_smem_bytes<W>() : 0;
-  if (P == 7) {
+  const size_t smem = kDigitTables<P> ? digit_smem_bytes<W, P>() : 0;
+  if (kDigitTables<P>) {
     if (!a.rank_table) return MJ_ERR_ARG;
     MJ_CUDA_TRY(cudaFuncSetAttribute(verify_diag_kernel<W, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
@@ -1152,9 +1185,12 @@ int launch_wp(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long*
 
 template <int W>
 int launch_w(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long* next, cudaStream_t s) {
+  // digit tables read B's symbols through the rank codes; without them (raw
+  // byte planes) every plane is XNORed
+  if (!a.rank_table) return launch_wp<W, 8>(a, PW, GW, next, s);
   if (a.bits <= 2) return launch_wp<W, 2>(a, PW, GW, next, s);
   if (a.bits <= 5) return launch_wp<W, 5>(a, PW, GW, next, s);
-  if (a.bits == 7 && a.rank_table) return launch_wp<W, 7>(a, PW, GW, next, s);   // text (33-128 symbols): digit tables
+  if (a.bits == 7) return launch_wp<W, 7>(a, PW, GW, next, s);   // text (65-128 symbols)
   return launch_wp<W, 8>(a, PW, GW, next, s);
 }
 

@@ -326,14 +326,20 @@ def test_verify_other_alphabets(ctx):
             assert np.array_equal(got, want), (symbols.shape, K)
 
 
-def test_diag_text_digit_tables(ctx):
-    """The per-thread kernel on 7-bit text (rank codes by digit tables), forced,
-    at band widths of 1 to 5 words (both table layouts), with the last string
-    of the input in many pairs (B's bytes read near the end of the buffer)."""
+DIGIT_ALPHABETS = {"dna": (lambda: synth.DNA, 2), "protein": (lambda: synth.PROTEIN, 5),
+                   "text": (lambda: synth.PRINTABLE, 7)}
+
+
+@pytest.mark.parametrize("alphabet", sorted(DIGIT_ALPHABETS))
+def test_diag_digit_tables(ctx, alphabet):
+    """The per-thread kernel with digit tables (2, 5 and 7 bit-planes), forced,
+    at band widths of 1 to 5 words, with the last string of the input in many
+    pairs (B's bytes read near the end of the buffer)."""
     import torch
     import paper_1810_08833_gb300 as mj
-    rng = np.random.Generator(np.random.PCG64(41))
-    symbols = synth.PRINTABLE
+    symbols_of, bits = DIGIT_ALPHABETS[alphabet]
+    symbols = symbols_of()
+    rng = np.random.Generator(np.random.PCG64(41 + bits))
     strs = []
     for t in range(120):
         L = int(rng.integers(0, 700))
@@ -347,7 +353,7 @@ def test_diag_text_digit_tables(ctx):
     data, off = to_device(s)
     i = torch.from_numpy(pairs[:, 0].astype(np.int32)).cuda()
     j = torch.from_numpy(pairs[:, 1].astype(np.int32)).cuda()
-    assert ctx.derive(data, off, mj.params(40, T=40))["bits"] == 7
+    assert ctx.derive(data, off, mj.params(40, T=40))["bits"] == bits
     ctx.set_verify_config(1, 0)
     try:
         for K in (7, 31, 40, 75, 100, 127, 150):
