@@ -276,14 +276,18 @@ template <> struct add_chain<8> {
   }
 };
 
-// Columns between two early-exit checks.  Wider bands run longer per pair
-// and take 32 (the most one load of B's bits covers); bands of one or two
-// words take 16, since their pairs are often short and exit early (measured:
-// 32 was 5% faster at 3-4 words and 8% slower at 2).
-template <int W>
-constexpr int kChunkFor = W <= 2 ? 16 : 32;
+// Columns between two early-exit checks: 32 (the most one load of B's bits
+// covers).  With the XNOR path (8 planes), bands of one or two words take 16,
+// since their pairs are often short and exit early (measured before the
+// digit tables: 32 was 5% faster at 3-4 words and 8% slower at 2).  With
+// digit tables every chunk rebuilds them, and 32 columns won at two words
+// too (protein verify 24.9 -> 22.6 ms, with 25% more word-columns advanced).
+template <int P>
+constexpr bool kDigitTables = P == 2 || P == 5 || P == 7;
+template <int W, int P>
+constexpr int kChunkFor = (W <= 2 && !kDigitTables<P>) ? 16 : 32;
 
-// Advances up to kChunkFor<W> columns; returns true when the pair is decided.
+// Advances up to kChunkFor<W, P> columns; returns true when the pair is decided.
 // The chunk's symbols are loaded at its start for every lane at once: A's
 // plane words of the rows the band covers in these columns (pre-shifted so
 // that column j0 + c needs a shift by c < 32), and B's plane bits of the
@@ -299,8 +303,6 @@ constexpr int kChunkFor = W <= 2 ? 16 : 32;
 // digits' tables back to back.  (For 7 planes, two digits of 4 and 3 bits,
 // 24 masks a word, take 50% more shared memory: 4 blocks per SM instead of
 // 6.)  8 planes (byte alphabets) keep the XNORs.
-template <int P>
-constexpr bool kDigitTables = P == 2 || P == 5 || P == 7;
 template <int P>
 constexpr int digit_masks() { return P == 2 ? 4 : (P == 5 ? 12 : 16); }
 template <int W, int P>
@@ -417,7 +419,7 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
       for (int k = 0; k < 8; ++k) bsym[k] = __funnelshift_r(raw[k], raw[k + 1], sh);
     }
   }
-  constexpr int kChunk = kChunkFor<W>;
+  constexpr int kChunk = kChunkFor<W, P>;
   const int32_t cnt = min(kChunk, st.n - j0 + 1);
   // The top row's D moves along a diagonal, so it rises by 0 or 1 per
   // column: by 1 exactly when the vertical delta entering the row and the
