@@ -144,6 +144,10 @@ struct mj_ctx {
   Buf pair_count, pair_off, pairs, pairs_alt;
   Buf uflags, uoffs, cand_i, cand_j;
   Buf pairbm;  // pair bitmap of the candidate dedup (bit per pair i < j)
+  // the bitmap's first pairbm_zero_words words are zero (its writer clears
+  // what it reads), valid while the buffer is still at pairbm_zero_at
+  uint64_t pairbm_zero_words = 0;
+  const void* pairbm_zero_at = nullptr;
   Buf planes, ed;
   Buf out_i, out_j, out_ed;
   Buf out_t;          // indices of the candidates within K, listed by the band-K pass
@@ -528,7 +532,12 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
   if (use_bitmap) {
     tstart(c, 4, s);
     MJ_TRY(c->small.reserve(128, s));
-    MJ_TRY(launch_mark_pairs(r, nr, d.K, g, n, c->pairbm.as<uint32_t>(), c->small.as<unsigned long long>() + 7, s));
+    const uint64_t words = pair_bitmap_words(n);
+    const bool zero = c->pairbm.p == c->pairbm_zero_at && words <= c->pairbm_zero_words;
+    const uint64_t zero_after = zero ? c->pairbm_zero_words : words;
+    c->pairbm_zero_words = 0;   // bits are set from here until the writer clears them
+    MJ_TRY(launch_mark_pairs(r, nr, d.K, g, n, c->pairbm.as<uint32_t>(), c->small.as<unsigned long long>() + 7, !zero,
+                             s));
     MJ_TRY(c->uflags.reserve((size_t)n * 4, s));
     MJ_TRY(c->uoffs.reserve((size_t)n * 4 + 16, s));
     MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(n), s));
@@ -543,11 +552,19 @@ int candidates(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint
     c->stats.n_raw_pairs = raw;
     // the row counts' scan is 32-bit: the raw pairs bound the candidates
     if (raw >= (1ull << 32)) return MJ_ERR_UNSUPPORTED;
+    // the writer clears the words it reads when few of them hold bits (at
+    // most one candidate per eight words): cheaper than clearing all the
+    // words before the next marking; denser bitmaps are cleared then
+    const bool writer_clears = nc <= words / 8;
     if (nc) {
       MJ_TRY(c->cand_i.reserve((size_t)nc * 4 + 16, s));
       MJ_TRY(c->cand_j.reserve((size_t)nc * 4 + 16, s));
       MJ_TRY(launch_bitmap_write(c->pairbm.as<uint32_t>(), n, c->uoffs.as<uint32_t>(), c->cand_i.as<uint32_t>(),
-                                 c->cand_j.as<uint32_t>(), s));
+                                 c->cand_j.as<uint32_t>(), writer_clears, s));
+    }
+    if (writer_clears) {   // every word read is zero again (none was set when nc = 0)
+      c->pairbm_zero_words = zero_after;
+      c->pairbm_zero_at = c->pairbm.p;
     }
     tstop(c, 4, s);
     c->n_cand = nc;

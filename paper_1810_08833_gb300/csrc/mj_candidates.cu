@@ -249,8 +249,10 @@ __global__ void bitmap_rows_kernel(const uint32_t* __restrict__ bm, uint32_t n, 
 
 // The candidates (a, b) of every row, in (a, b) order, from the row offsets:
 // per warp step 128 words of the row, four per lane.
-__global__ void bitmap_write_kernel(const uint32_t* __restrict__ bm, uint32_t n, const uint32_t* __restrict__ off,
-                                    uint32_t* __restrict__ oi, uint32_t* __restrict__ oj) {
+// With `clear`, words with bits are cleared after they are read, so the
+// bitmap is zero again for the next marking.
+__global__ void bitmap_write_kernel(uint32_t* __restrict__ bm, uint32_t n, const uint32_t* __restrict__ off,
+                                    uint32_t* __restrict__ oi, uint32_t* __restrict__ oj, bool clear) {
   const int lane = threadIdx.x & 31;
   const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t a = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < n; a += warps) {
@@ -264,6 +266,11 @@ __global__ void bitmap_write_kernel(const uint32_t* __restrict__ bm, uint32_t n,
       for (int k = 0; k < 4; ++k) {
         v[k] = lw + k < w1 ? __ldcs(bm + lw + k) : 0u;
         p += __popc(v[k]);
+      }
+      if (clear) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (v[k]) __stcs(bm + lw + k, 0u);
       }
       uint32_t incl = p;
       for (int o = 1; o < 32; o <<= 1) {
@@ -735,10 +742,10 @@ uint64_t pair_bitmap_words(uint32_t n_str) {
 }
 
 int launch_mark_pairs(const PRec* r, uint32_t n, uint32_t K, const GroupKeyShape& g, uint32_t n_str, uint32_t* bm,
-                      unsigned long long* raw_total, cudaStream_t s) {
+                      unsigned long long* raw_total, bool clear, cudaStream_t s) {
   MJ_CUDA_TRY(cudaMemsetAsync(raw_total, 0, sizeof(unsigned long long), s));
   const uint64_t words = pair_bitmap_words(n_str);
-  if (words) MJ_CUDA_TRY(cudaMemsetAsync(bm, 0, words * 4, s));
+  if (words && clear) MJ_CUDA_TRY(cudaMemsetAsync(bm, 0, words * 4, s));
   if (!n || !words) return MJ_OK;
   walk_kernel<WALK_MARK><<<grid_for(n), 256, 0, s>>>(r, n, K, g.slen_bits, g.slen_bits + g.pb_bits, 0, nullptr,
                                                      nullptr, nullptr, bm, n_str, raw_total);
@@ -753,10 +760,10 @@ int launch_bitmap_rows(const uint32_t* bm, uint32_t n_str, uint32_t* cnt, cudaSt
   return MJ_OK;
 }
 
-int launch_bitmap_write(const uint32_t* bm, uint32_t n_str, const uint32_t* off, uint32_t* oi, uint32_t* oj,
+int launch_bitmap_write(uint32_t* bm, uint32_t n_str, const uint32_t* off, uint32_t* oi, uint32_t* oj, bool clear,
                         cudaStream_t s) {
   if (!n_str) return MJ_OK;
-  bitmap_write_kernel<<<grid_for((uint64_t)n_str * 32), 256, 0, s>>>(bm, n_str, off, oi, oj);
+  bitmap_write_kernel<<<grid_for((uint64_t)n_str * 32), 256, 0, s>>>(bm, n_str, off, oi, oj, clear);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }

@@ -180,16 +180,17 @@ int launch_fill_pairs(const PRec* r, uint32_t n_rec, uint32_t K, const GroupKeyS
                       const uint64_t* offs, uint64_t* pairs, cudaStream_t s);
 // a7 by the pair bitmap: bit (a, b), a < b < n_str, in row a (ceil((n_str - 1
 // - a) / 32) words, rows back to back); pair_bitmap_words(n_str) words in all.
-// launch_mark_pairs clears the bitmap, sets the bit of every pair the walk
-// finds and counts them (raw pairs, duplicates included) into *raw_total;
-// launch_bitmap_rows writes the candidates per row, launch_bitmap_write the
-// candidates (i, j) sorted, at the row offsets `off` (exclusive scan of the
-// row counts).
+// launch_mark_pairs clears the bitmap (unless `clear` is false: the caller
+// knows it is zero), sets the bit of every pair the walk finds and counts
+// them (raw pairs, duplicates included) into *raw_total; launch_bitmap_rows
+// writes the candidates per row, launch_bitmap_write the candidates (i, j)
+// sorted, at the row offsets `off` (exclusive scan of the row counts), and
+// with `clear` clears the bitmap's words as it reads them.
 uint64_t pair_bitmap_words(uint32_t n_str);
 int launch_mark_pairs(const PRec* r, uint32_t n_rec, uint32_t K, const GroupKeyShape& g, uint32_t n_str, uint32_t* bm,
-                      unsigned long long* raw_total, cudaStream_t s);
+                      unsigned long long* raw_total, bool clear, cudaStream_t s);
 int launch_bitmap_rows(const uint32_t* bm, uint32_t n_str, uint32_t* cnt, cudaStream_t s);
-int launch_bitmap_write(const uint32_t* bm, uint32_t n_str, const uint32_t* off, uint32_t* oi, uint32_t* oj,
+int launch_bitmap_write(uint32_t* bm, uint32_t n_str, const uint32_t* off, uint32_t* oi, uint32_t* oj, bool clear,
                         cudaStream_t s);
 int launch_key_check(const PRec* r, const uint8_t* bytes, const int64_t* offsets, uint32_t n_rec,
                      unsigned long long* mismatches, cudaStream_t s);
