@@ -637,9 +637,18 @@ __device__ __forceinline__ void wave_load_bits(const VerifyArgs& a, uint64_t PW,
 // bit 31 and hn is its -1.  Bit extraction, shifts and disjoint ORs are
 // written as integer multiply-adds, which the FMA pipe can take: the logic
 // ops already fill the ALU pipe.
+__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {   // a * b + c on the FMA pipe
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+// pub: the word published to the next lane, ((Ph & 2^31) | T) + hn with the
+// updated T (bit 31 and bit 0 of T are clear), formed by multiply-adds as
+// T_old + hp (2^31 + 2) - hn.
 template <int P>
 __device__ __forceinline__ void wave_column(const uint32_t (&pa)[P], uint32_t (&bw)[P], uint32_t wv, uint32_t& Pv,
-                                            uint32_t& Mv, uint32_t& T, uint32_t& Ph, uint32_t& hn) {
+                                            uint32_t& Mv, uint32_t& T, uint32_t& Ph, uint32_t& hn, uint32_t& pub) {
   uint32_t Eq = 0xffffffffu;
 #pragma unroll
   for (int p = 0; p < P; ++p) {
@@ -655,7 +664,9 @@ __device__ __forceinline__ void wave_column(const uint32_t (&pa)[P], uint32_t (&
   Ph = Mv | ~(Xh | Pv);
   const uint32_t Mh = Pv & Xh;
   hn = __umulhi(Mh, 2u);
-  T = T + 2u * __umulhi(Ph, 2u) - 2u * hn;
+  const uint32_t hp = __umulhi(Ph, 2u);
+  pub = mad_lo(hn, 0xffffffffu, mad_lo(hp, 0x80000002u, T));
+  T = mad_lo(hn, 0xfffffffeu, mad_lo(hp, 2u, T));
   const uint32_t Ph1 = Ph * 2u + hin_pos;   // (Ph << 1) | hin > 0
   const uint32_t Mh1 = Mh * 2u + hin_neg;   // (Mh << 1) | hin < 0
   Pv = Mh1 | ~(Xv | Ph1);
@@ -796,13 +807,13 @@ __global__ void __launch_bounds__(128, P <= 2 ? 8 : 1) verify_wave_kernel(Verify
         if (un <= u_valid) fr = min(fr, (int64_t)u_valid - un + 1);
         const int free = __reduce_min_sync(0xffffffffu, (int)fr);
         const bool from_prev = un <= u_valid;
+        const uint32_t keep_in = from_prev ? 1u : 0u, idle_in = from_prev ? 0u : kIdle;
 #pragma unroll 4
         for (int f = 0; f < free; ++f) {
           const uint32_t w_in = __shfl_sync(0xffffffffu, pub, prev_lane);
-          const uint32_t wv = from_prev ? w_in : kIdle;
+          const uint32_t wv = mad_lo(w_in, keep_in, idle_in);   // w_in, or kIdle at the band's edge
           uint32_t Ph, hn;
-          wave_column<P>(pa, bw, wv, Pv, Mv, T, Ph, hn);
-          pub = ((Ph & 0x80000000u) | T) + hn;
+          wave_column<P>(pa, bw, wv, Pv, Mv, T, Ph, hn, pub);
         }
         u += free;
         it += free;
@@ -811,8 +822,7 @@ __global__ void __launch_bounds__(128, P <= 2 ? 8 : 1) verify_wave_kernel(Verify
       ++u;
       const uint32_t wv = u <= u_valid ? w_in : kIdle;
       uint32_t Ph, hn;
-      wave_column<P>(pa, bw, wv, Pv, Mv, T, Ph, hn);
-      pub = ((Ph & 0x80000000u) | T) + hn;
+      wave_column<P>(pa, bw, wv, Pv, Mv, T, Ph, hn, pub);
       const bool diag_here = it == kWaveSteps - 1 && (uint32_t)(u + dg) < 32u;
       if (u == 0 || u == span || diag_here) {
         if (u == 0) {   // first column: load the block's symbols, rows start from +1 deltas
@@ -821,7 +831,7 @@ __global__ void __launch_bounds__(128, P <= 2 ? 8 : 1) verify_wave_kernel(Verify
           wave_load_bits<P>(a, PW, (uint64_t)(oB + jf - 1 + 32 * (int64_t)GW), bw, true);
           Pv = 0xffffffffu;
           Mv = 0u;
-          wave_column<P>(pa, bw, wv, Pv, Mv, T, Ph, hn);
+          wave_column<P>(pa, bw, wv, Pv, Mv, T, Ph, hn, pub);
           // D of the row above the block in this column, plus the block's deltas
           const int32_t above = b == 0 ? 1 : (int32_t)((w_in >> 1) & 0x3fffffffu);
           const int32_t score = above + (int32_t)__popc(Pv) - (int32_t)__popc(Mv);
@@ -1042,8 +1052,7 @@ __global__ void __launch_bounds__(32 * V) verify_cta_kernel(VerifyArgs a, uint64
         ++u;
         const uint32_t wv = u <= u_valid ? w_in : kIdle;
         uint32_t Ph, hn;
-        wave_column<P>(pa, bw, wv, Pv, Mv, T, Ph, hn);
-        pub = ((Ph & 0x80000000u) | T) + hn;
+        wave_column<P>(pa, bw, wv, Pv, Mv, T, Ph, hn, pub);
         const bool diag_here = it == S - 1 && (uint32_t)(u + dg) < 32u;
         if (u == 0 || u == span || diag_here) {
           if (u == 0) {   // first column: load the block's symbols, rows start from +1 deltas
@@ -1052,7 +1061,7 @@ __global__ void __launch_bounds__(32 * V) verify_cta_kernel(VerifyArgs a, uint64
             wave_load_bits<P>(a, PW, (uint64_t)(oB + jf - 1 + 32 * (int64_t)GW), bw, true);
             Pv = 0xffffffffu;
             Mv = 0u;
-            wave_column<P>(pa, bw, wv, Pv, Mv, T, Ph, hn);
+            wave_column<P>(pa, bw, wv, Pv, Mv, T, Ph, hn, pub);
             const int32_t above = b == 0 ? 1 : (int32_t)((w_in >> 1) & 0x3fffffffu);
             const int32_t score = above + (int32_t)__popc(Pv) - (int32_t)__popc(Mv);
             T = (uint32_t)score << 1;
