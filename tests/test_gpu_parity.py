@@ -163,6 +163,27 @@ def test_join_parity(ctx, name, factory, dedup):
 REPEAT_SETS = [x for x in SETS if x[0] in ("config1", "config4_400roots", "random_mixed", "edge")]
 
 
+def test_bitmap_reuse_across_joins(ctx):
+    """The pair bitmap is cleared by the candidate writer when it is sparse
+    (and the next join's marking then skips clearing it) and cleared before
+    marking otherwise.  Joins of sparse and dense inputs, growing and
+    shrinking, on one context, each equal to the oracle's join."""
+    import paper_1810_08833_gb300 as mj
+    sets = [synth.random_set(301, n=600, min_len=40, max_len=200, K=6, T=6, families=10, rate=0.03),
+            synth.random_set(302, n=300, min_len=40, max_len=200, K=6, T=6, families=60, rate=0.02),
+            synth.random_set(303, n=900, min_len=40, max_len=200, K=6, T=6, families=5, rate=0.03),
+            synth.random_set(304, n=200, min_len=20, max_len=60, symbols=synth.DNA[:2], K=8, T=8),
+            synth.random_set(305, n=900, min_len=40, max_len=200, K=6, T=6, families=30, rate=0.03)]
+    for s in sets + sets[::-1]:
+        ref = oracle.minjoin(s.bytes, s.offsets, K=s.K, T=s.T)
+        data, off = to_device(s)
+        for flags in (0, mj.MJ_FLAG_DEDUP_BITMAP):
+            oi, oj, oe = ctx.join(data, off, mj.params(s.K, T=s.T, flags=flags))
+            got = np.stack([t.cpu().numpy() for t in (oi, oj, oe)], axis=1).astype(np.int64)
+            want = np.concatenate([ref.pairs, ref.ed[:, None]], axis=1)
+            assert np.array_equal(got, want), (s.n, flags)
+
+
 @pytest.mark.parametrize("name,factory", REPEAT_SETS, ids=[n for n, _ in REPEAT_SETS])
 def test_repetition_parity(ctx, name, factory):
     """Parallel repetition (Sec. 2.2): the partitions under R seeds equal the
