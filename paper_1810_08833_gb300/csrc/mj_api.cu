@@ -154,6 +154,7 @@ struct mj_ctx {
   bool out_collect = false;
   Buf rank_dev;       // the derived rank codes on the device (256 bytes)
   Buf geo;            // pair geometry at the verification order's positions (uint4)
+  Buf strgeo;         // per string {offset, length} for the ordering (uint2)
   bool geo_valid = false;
   // alphabet and longest length fixed by mj_set_alphabet (a sharded join's
   // global values), used by derive instead of the input's own
@@ -686,12 +687,12 @@ constexpr size_t kOrderScratchAt = 128;   // words of branges before the orderin
 // The pairs' K-band cells are summed into small word 9 on the way.
 int pair_order(mj_ctx* c, const uint32_t* ci, const uint32_t* cj, const int64_t* d_offsets, uint64_t m,
                const uint32_t** order, cudaStream_t s) {
-  if (!c->small.p || !c->branges.p || !c->idx.p || !c->geo.p) return MJ_ERR_STATE;   // order_buffers comes first
+  if (!c->small.p || !c->branges.p || !c->idx.p || !c->geo.p || !c->strgeo.p) return MJ_ERR_STATE;   // order_buffers first
   uint32_t* counts = c->branges.as<uint32_t>();
   tstart(c, 8, s);
   MJ_TRY(launch_length_order(ci, cj, d_offsets, (uint32_t)c->stats.n_strings, m, c->d.K, counts + kOrderScratchAt,
-                             c->idx.as<uint32_t>(), c->geo.as<uint4>(), counts, counts + kLenBuckets,
-                             c->small.as<unsigned long long>() + 9, s));
+                             c->strgeo.as<uint2>(), c->idx.as<uint32_t>(), c->geo.as<uint4>(), counts,
+                             counts + kLenBuckets, c->small.as<unsigned long long>() + 9, s));
   tstop(c, 8, s);
   *order = c->idx.as<uint32_t>();
   c->geo_valid = true;   // c->geo matches the order in c->idx
@@ -702,6 +703,7 @@ int order_buffers(mj_ctx* c, uint64_t m, cudaStream_t s) {
   MJ_TRY(c->small.reserve(128, s));   // word 9: the band cells summed by the ordering
   MJ_TRY(c->idx.reserve(m * 4, s));
   MJ_TRY(c->geo.reserve(m * 16, s));
+  MJ_TRY(c->strgeo.reserve((size_t)c->stats.n_strings * 8 + 16, s));
   MJ_TRY(c->branges.reserve(4 * (kOrderScratchAt + kOrderScratchWords) + 64, s));
   return MJ_OK;
 }
@@ -1013,7 +1015,7 @@ void mj_destroy(mj_ctx* c) {
   Buf* bufs[] = {&c->hist, &c->dev_flags, &c->small, &c->bitmap, &c->tile_count, &c->tile_off, &c->scan_tmp,
                  &c->tile_first,
                  &c->recs, &c->keys, &c->keys_alt, &c->idx, &c->idx_alt, &c->sort_tmp, &c->srec, &c->pair_count, &c->pair_off, &c->pairs, &c->pairs_alt,
-                 &c->uflags, &c->uoffs, &c->cand_i, &c->cand_j, &c->pairbm, &c->planes, &c->ed, &c->out_t, &c->geo, &c->rank_dev,
+                 &c->uflags, &c->uoffs, &c->cand_i, &c->cand_j, &c->pairbm, &c->planes, &c->ed, &c->out_t, &c->geo, &c->strgeo, &c->rank_dev,
                  &c->out_i, &c->out_j, &c->out_ed, &c->in_bytes, &c->in_offsets, &c->branges,
                  &c->band, &c->feat_x, &c->mult, &c->run_start, &c->parts, &c->yhat, &c->kband, &c->lvals,
                  &c->franges, &c->fnext, &c->fcnt, &c->ed_first};

@@ -453,23 +453,33 @@ __device__ __forceinline__ uint32_t length_class(uint64_t n) {
   return (e - 2u) * 8u + (uint32_t)((n >> (e - 3u)) & 7u);
 }
 
-// Offsets and lengths of pair t's strings; ids >= n_str read nothing and
-// count as empty strings.
+// Offsets and lengths of pair t's strings from the per-string table sg
+// ({offset, length}, 32-bit: inputs are under 4 GB); ids >= n_str read
+// nothing and count as empty strings.
 struct PairLens {
-  int64_t ox, lx, oy, ly;
+  uint32_t ox, lx, oy, ly;
   bool bad;
 };
 __device__ __forceinline__ PairLens pair_lens(const uint32_t* __restrict__ ci, const uint32_t* __restrict__ cj,
-                                              const int64_t* __restrict__ offsets, uint32_t n_str, uint64_t t) {
+                                              const uint2* __restrict__ sg, uint32_t n_str, uint64_t t) {
   const uint32_t x = ci[t], y = cj[t];
   PairLens r{0, 0, 0, 0, x >= n_str || y >= n_str};
   if (!r.bad) {
-    r.ox = __ldg(offsets + x);
-    r.lx = __ldg(offsets + x + 1) - r.ox;
-    r.oy = __ldg(offsets + y);
-    r.ly = __ldg(offsets + y + 1) - r.oy;
+    const uint2 gx = __ldg(sg + x), gy = __ldg(sg + y);
+    r.ox = gx.x;
+    r.lx = gx.y;
+    r.oy = gy.x;
+    r.ly = gy.y;
   }
   return r;
+}
+
+// sg[i] = {offset, length} of string i.
+__global__ void string_geo_kernel(const int64_t* __restrict__ offsets, uint32_t n, uint2* __restrict__ sg) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const int64_t o = offsets[i];
+    sg[i] = make_uint2((uint32_t)o, (uint32_t)(offsets[i + 1] - o));
+  }
 }
 
 __device__ __forceinline__ uint64_t band_cells_of(int64_t m, int64_t n, int64_t K) {   // m >= n
@@ -503,7 +513,7 @@ constexpr int kOrderBlocksMax = kNumSMsHint * 8;
 // K-band cells (mj_stats.band_cells), summed.
 __global__ void __launch_bounds__(kOrderThreads) order_hist_kernel(const uint32_t* __restrict__ ci,
                                                                    const uint32_t* __restrict__ cj,
-                                                                   const int64_t* __restrict__ offsets, uint32_t n_str,
+                                                                   const uint2* __restrict__ sg, uint32_t n_str,
                                                                    uint64_t m, uint64_t R, uint32_t K,
                                                                    uint32_t* __restrict__ bh,
                                                                    unsigned long long* __restrict__ cells) {
@@ -514,8 +524,8 @@ __global__ void __launch_bounds__(kOrderThreads) order_hist_kernel(const uint32_
   const uint64_t t0 = (uint64_t)blockIdx.x * R;
   const uint64_t t1 = t0 + R < m ? t0 + R : m;
   for (uint64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
-    const PairLens L = pair_lens(ci, cj, offsets, n_str, t);
-    const int64_t n = L.lx < L.ly ? L.lx : L.ly, mm = L.lx < L.ly ? L.ly : L.lx;
+    const PairLens L = pair_lens(ci, cj, sg, n_str, t);
+    const uint32_t n = L.lx < L.ly ? L.lx : L.ly, mm = L.lx < L.ly ? L.ly : L.lx;
     atomicAdd(&h[length_class((uint64_t)n)], 1u);
     if (cells) acc += band_cells_of(mm, n, K);
   }
@@ -582,7 +592,7 @@ __global__ void order_scan_kernel(uint32_t* __restrict__ bh, uint32_t G, uint32_
 // from the block's running base per class.
 __global__ void __launch_bounds__(kOrderThreads) order_scatter_kernel(const uint32_t* __restrict__ ci,
                                                                      const uint32_t* __restrict__ cj,
-                                                                     const int64_t* __restrict__ offsets,
+                                                                     const uint2* __restrict__ sg,
                                                                      uint32_t n_str, uint64_t m, uint64_t R,
                                                                      const uint32_t* __restrict__ bbase,
                                                                      uint32_t* __restrict__ order,
@@ -604,11 +614,10 @@ __global__ void __launch_bounds__(kOrderThreads) order_scatter_kernel(const uint
       const uint64_t t = base + (uint64_t)k * kOrderThreads + threadIdx.x;
       cls[k] = 0xffffffffu;
       if (t < t1) {
-        const PairLens L = pair_lens(ci, cj, offsets, n_str, t);
+        const PairLens L = pair_lens(ci, cj, sg, n_str, t);
         const bool xa = L.lx >= L.ly;
         g[k] = L.bad ? make_uint4(0u, 0u, 0u, kGeoBadIds)
-                     : make_uint4((uint32_t)(xa ? L.ox : L.oy), (uint32_t)(xa ? L.oy : L.ox),
-                                  (uint32_t)(xa ? L.lx : L.ly), (uint32_t)(xa ? L.ly : L.lx));
+                     : make_uint4(xa ? L.ox : L.oy, xa ? L.oy : L.ox, xa ? L.lx : L.ly, xa ? L.ly : L.lx);
         cls[k] = length_class((uint64_t)(L.lx < L.ly ? L.lx : L.ly));
         rank[k] = atomicAdd(&h[cls[k]], 1u);
       }
@@ -792,19 +801,23 @@ int launch_compact_pairs(const uint64_t* sorted, const uint32_t* flags, const ui
 }
 
 int launch_length_order(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint32_t n_str, uint64_t m,
-                        uint32_t K, uint32_t* scratch, uint32_t* order, uint4* geo, uint32_t* counts,
+                        uint32_t K, uint32_t* scratch, uint2* sg, uint32_t* order, uint4* geo, uint32_t* counts,
                         uint32_t* ranges, unsigned long long* cells, cudaStream_t s) {
+  if (n_str) {
+    string_geo_kernel<<<grid_for(n_str), 256, 0, s>>>(offsets, n_str, sg);
+    MJ_KERNEL_DONE();
+  }
   // G blocks of R pairs (R a whole number of chunks), at least one block
   const uint64_t chunks = (m + kOrderChunk - 1) / kOrderChunk;
   const uint32_t G = (uint32_t)(chunks < 1 ? 1 : (chunks < (uint64_t)kOrderBlocksMax ? chunks : kOrderBlocksMax));
   const uint64_t R = (chunks + G - 1) / G * kOrderChunk;
   if (cells) MJ_CUDA_TRY(cudaMemsetAsync(cells, 0, sizeof(unsigned long long), s));
-  order_hist_kernel<<<G, kOrderThreads, 0, s>>>(ci, cj, offsets, n_str, m, R, K, scratch, cells);
+  order_hist_kernel<<<G, kOrderThreads, 0, s>>>(ci, cj, sg, n_str, m, R, K, scratch, cells);
   MJ_KERNEL_DONE();
   order_scan_kernel<<<1, kOrderClasses, 0, s>>>(scratch, G, counts, ranges);
   MJ_KERNEL_DONE();
   if (m) {
-    order_scatter_kernel<<<G, kOrderThreads, 0, s>>>(ci, cj, offsets, n_str, m, R, scratch, order, geo);
+    order_scatter_kernel<<<G, kOrderThreads, 0, s>>>(ci, cj, sg, n_str, m, R, scratch, order, geo);
     MJ_KERNEL_DONE();
   }
   return MJ_OK;

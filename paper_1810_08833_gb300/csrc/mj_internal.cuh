@@ -265,8 +265,10 @@ constexpr int kOrderScratchWords = 256 * kNumSMsHint * 8;
 // pair_geo).  Pair ids >= n_str count as empty strings here (the verifier
 // flags them).
 constexpr uint32_t kGeoBadIds = 0xffffffffu;
+// sg: n_str entries of scratch for the strings' {offset, length} (inputs
+// are under 4 GB).
 int launch_length_order(const uint32_t* ci, const uint32_t* cj, const int64_t* offsets, uint32_t n_str, uint64_t m,
-                        uint32_t K, uint32_t* scratch, uint32_t* order, uint4* geo, uint32_t* counts,
+                        uint32_t K, uint32_t* scratch, uint2* sg, uint32_t* order, uint4* geo, uint32_t* counts,
                         uint32_t* ranges, unsigned long long* cells, cudaStream_t s);
 
 // ---- learned first-pass band (MLP 8 -> 64 -> 64 -> 1)
