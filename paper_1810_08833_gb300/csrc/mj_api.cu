@@ -195,6 +195,8 @@ struct mj_ctx {
   bool have_features = false;
   bool work_started = false;   // verification counters cleared in this call
   bool planes_ready = false;
+  Buf codes;                  // the input's rank codes, one byte per input byte (digit-table verifiers)
+  bool codes_ready = false;   // written in this call (with the planes)
   uint64_t planes_pw = 0;
   uint32_t planes_gw = 0;
   bool have_part = false, have_cand = false, have_out = false;
@@ -259,6 +261,7 @@ void begin_call(mj_ctx* c, bool timing) {
   c->stats = mj_stats{};
   c->geo_valid = false;
   c->planes_ready = false;
+  c->codes_ready = false;
   c->work_started = false;
   c->timing = timing;
   for (bool& u : c->sec_used) u = false;
@@ -374,6 +377,7 @@ int partition(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
   MJ_TRY(c->tile_off.reserve(tiles * sizeof(uint32_t) + 16, s));
   MJ_TRY(c->scan_tmp.reserve(scan_temp_bytes(tiles), s));
   c->planes_ready = false;
+  c->codes_ready = false;
   uint32_t* planes = nullptr;
   uint64_t PW = 0;
   uint32_t GW = 0;
@@ -382,6 +386,7 @@ int partition(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
     PW = tiles * (kPartTile / 32) + 2 * (uint64_t)GW;
     MJ_TRY(c->planes.reserve(PW * d.bits * 4, s));
     planes = c->planes.as<uint32_t>();
+    MJ_TRY(c->codes.reserve(tiles * kPartTile + 64, s));   // written by the first repetition's tiles
     // guard words before and after every plane's data are zero
     MJ_CUDA_TRY(cudaMemsetAsync(planes, 0, (size_t)GW * 4, s));
     for (uint32_t p = 0; p < d.bits; ++p) {
@@ -400,12 +405,14 @@ int partition(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, uint3
     a.seed32 = (uint32_t)seed_k ^ (uint32_t)(seed_k >> 32);
     a.seed64 = seed_k;
     tstart(c, 0, s);
+    a.codes = (planes && k == 0) ? c->codes.as<uint8_t>() : nullptr;
     MJ_TRY(launch_anchor_flags(a, c->bitmap.as<uint32_t>(), c->tile_count.as<uint32_t>(),
                                c->dev_flags.as<uint32_t>(), k == 0 ? planes : nullptr, PW, GW,
                                c->tile_first.as<uint32_t>(), s));
     tstop(c, 0, s);
     if (planes && k == 0) {
       c->planes_ready = true;
+      c->codes_ready = true;
       c->planes_pw = PW;
       c->planes_gw = GW;
     }
@@ -634,9 +641,12 @@ int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const ui
     MJ_TRY(c->planes.reserve(PW * d.bits * 4, s));
     RankTable rt;
     memcpy(rt.r, d.rank, 256);
+    MJ_TRY(c->codes.reserve(nbytes + 64, s));
     tstart(c, 5, s);
-    MJ_TRY(launch_build_planes(d_bytes, nbytes, rt, d.bits, c->planes.as<uint32_t>(), PW, GW, s));
+    MJ_TRY(launch_build_planes(d_bytes, nbytes, rt, d.bits, c->planes.as<uint32_t>(), PW, GW,
+                               c->codes.as<uint8_t>(), s));
     tstop(c, 5, s);
+    c->codes_ready = true;
   }
   if (prep) MJ_TRY(verify_prep(c, s));
   VerifyArgs a;
@@ -662,6 +672,7 @@ int verify(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_offsets, const ui
   a.dev_flags = c->dev_flags.as<uint32_t>();
   if (order && order == c->idx.as<uint32_t>() && c->geo_valid) a.pair_geo = c->geo.as<uint4>();
   a.rank_table = c->rank_dev.as<uint8_t>();
+  a.codes = c->codes_ready ? c->codes.as<uint8_t>() : nullptr;
   a.nbytes = nbytes;
   if (c->out_collect) {   // the join's band-K pass lists the pairs within K
     a.out_t = c->out_t.as<uint32_t>();
@@ -1015,7 +1026,7 @@ void mj_destroy(mj_ctx* c) {
   Buf* bufs[] = {&c->hist, &c->dev_flags, &c->small, &c->bitmap, &c->tile_count, &c->tile_off, &c->scan_tmp,
                  &c->tile_first,
                  &c->recs, &c->keys, &c->keys_alt, &c->idx, &c->idx_alt, &c->sort_tmp, &c->srec, &c->pair_count, &c->pair_off, &c->pairs, &c->pairs_alt,
-                 &c->uflags, &c->uoffs, &c->cand_i, &c->cand_j, &c->pairbm, &c->planes, &c->ed, &c->out_t, &c->geo, &c->strgeo, &c->rank_dev,
+                 &c->uflags, &c->uoffs, &c->cand_i, &c->cand_j, &c->pairbm, &c->planes, &c->ed, &c->out_t, &c->geo, &c->strgeo, &c->codes, &c->rank_dev,
                  &c->out_i, &c->out_j, &c->out_ed, &c->in_bytes, &c->in_offsets, &c->branges,
                  &c->band, &c->feat_x, &c->mult, &c->run_start, &c->parts, &c->yhat, &c->kband, &c->lvals,
                  &c->franges, &c->fnext, &c->fcnt, &c->ed_first};

@@ -122,6 +122,7 @@ struct PartitionArgs {
   uint64_t seed64;
   const uint64_t* table;  // nullable explicit Pi
   uint8_t rank[256];
+  uint8_t* codes = nullptr;  // nullable: also the input's rank codes, one byte per input byte (with the planes)
   // set by the launcher: 2^19 and 2^16, so that x >> 13 and x >> 16 are the
   // high words of x * mul (the mixer's shifts on the multiply pipe)
   uint32_t mul_shr13, mul_shr16;
@@ -129,7 +130,9 @@ struct PartitionArgs {
 constexpr int kPartTile = 2048;  // byte positions per CTA tile
 uint64_t partition_num_tiles(uint64_t nbytes);
 // planes (nullable): also writes the rank-code bit-planes of the tile for the
-// verifier (plane p word guard_words + g/32 holds positions g .. g+31).
+// verifier (plane p word guard_words + g/32 holds positions g .. g+31), and
+// with a.codes the rank codes themselves (a.codes[g] for position g; the
+// buffer covers whole tiles).
 int launch_anchor_flags(const PartitionArgs& a, uint32_t* bitmap, uint32_t* tile_count,
                         uint32_t* dev_flags, uint32_t* planes, uint64_t plane_words,
                         uint32_t guard_words, uint32_t* tile_first, cudaStream_t s);
@@ -232,14 +235,17 @@ struct VerifyArgs {
   const uint4* pair_geo = nullptr;     // nullable: at order position q, (oA, oB, m, n) of pair order[q], A the
                                        // longer string (n = kGeoBadIds: an id out of range); loaded with order[q]
   uint32_t* out_t = nullptr;           // nullable: indices of the pairs with result <= K, appended (order arbitrary)
-  const uint8_t* rank_table = nullptr; // device copy of the 256 rank codes (text kernels read B's bytes through it)
+  const uint8_t* rank_table = nullptr; // device copy of the 256 rank codes
+  const uint8_t* codes = nullptr;      // the input's rank codes, one byte per input byte (digit-table kernels)
   uint64_t nbytes = 0;                 // bytes of the input
   unsigned long long* out_count = nullptr;
 };
 int verify_words_for(uint32_t kmax);
 inline uint32_t plane_guard_words(uint32_t kmax) { return kmax / 64 + (uint32_t)verify_words_for(kmax) + 4; }
+// codes (nullable, nbytes + 32 bytes): also the rank code of every byte.
 int launch_build_planes(const uint8_t* bytes, uint64_t nbytes, const RankTable& rt, uint32_t bits,
-                        uint32_t* planes, uint64_t plane_words, uint32_t guard_words, cudaStream_t s);
+                        uint32_t* planes, uint64_t plane_words, uint32_t guard_words, uint8_t* codes,
+                        cudaStream_t s);
 // `next` is a device counter the persistent kernel hands pairs out from.
 // kernel: MJ_VERIFY_KERNEL_*; lanes: wavefront lanes per pair (0 = fewest that fit).
 int launch_verify(const VerifyArgs& a, uint64_t plane_words, uint32_t guard_words, uint32_t kmax,

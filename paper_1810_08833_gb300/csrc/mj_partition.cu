@@ -397,6 +397,7 @@ __global__ void __launch_bounds__(kAThreads, sizeof(HT) == 4 ? 4 : 2) anchor_fla
             }
             reinterpret_cast<uint16_t*>(planes + (uint64_t)p * plane_words + word)[(g >> 4) & 1] = (uint16_t)half;
           }
+          if (a.codes) *reinterpret_cast<uint4*>(a.codes + g) = make_uint4(symw[0], symw[1], symw[2], symw[3]);
         }
       }
     }

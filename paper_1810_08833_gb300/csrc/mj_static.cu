@@ -80,7 +80,7 @@ extern "C" int mj_verify_static(const uint8_t* d_bytes, const int64_t* d_offsets
   MJ_CUDA_TRY(cudaMemsetAsync(scratch, 0, kHeaderBytes, s));   // counter and flags start at zero
   RankTable rt;
   for (int b = 0; b < 256; ++b) rt.r[b] = (uint8_t)b;
-  MJ_TRY(launch_build_planes(d_bytes, (uint64_t)nbytes, rt, bits, planes, PW, GW, s));
+  MJ_TRY(launch_build_planes(d_bytes, (uint64_t)nbytes, rt, bits, planes, PW, GW, nullptr, s));
   VerifyArgs a;
   a.planes = planes;
   a.bits = bits;

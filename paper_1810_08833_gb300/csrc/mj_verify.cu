@@ -44,7 +44,8 @@ constexpr int kMaxBits = 8;
 
 // One 32-symbol word per thread (two 16-byte loads where aligned).
 __global__ void build_planes_kernel(const uint8_t* __restrict__ bytes, uint64_t nbytes, RankTable rt, uint32_t bits,
-                                    uint32_t* __restrict__ planes, uint64_t plane_words, uint32_t guard_words) {
+                                    uint32_t* __restrict__ planes, uint64_t plane_words, uint32_t guard_words,
+                                    uint8_t* __restrict__ codes) {
   __shared__ uint8_t s_rank[256];
   s_rank[threadIdx.x] = rt.r[threadIdx.x];
   __syncthreads();
@@ -70,12 +71,18 @@ __global__ void build_planes_kernel(const uint8_t* __restrict__ bytes, uint64_t 
         sym[q] = x;
       }
     }
+    uint32_t cw[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // the 32 rank codes, four per word
 #pragma unroll
     for (int t = 0; t < 32; ++t) {
       const int64_t c = c0 + t;
       const uint32_t r = (c >= 0 && (uint64_t)c < nbytes) ? s_rank[(sym[t >> 2] >> (8 * (t & 3))) & 255u] : 0u;
+      cw[t >> 2] |= r << (8 * (t & 3));
 #pragma unroll
       for (int p = 0; p < kMaxBits; ++p) acc[p] |= ((r >> p) & 1u) << t;
+    }
+    if (codes && c0 >= 0 && (uint64_t)c0 < nbytes) {   // codes + c0 is 32-byte aligned, the buffer nbytes + 32 long
+      *reinterpret_cast<uint4*>(codes + c0) = make_uint4(cw[0], cw[1], cw[2], cw[3]);
+      *reinterpret_cast<uint4*>(codes + c0 + 16) = make_uint4(cw[4], cw[5], cw[6], cw[7]);
     }
 #pragma unroll
     for (int p = 0; p < kMaxBits; ++p)
@@ -297,7 +304,7 @@ constexpr int kChunkFor = (W <= 2 && !kDigitTables<P>) ? 16 : 32;
 // whose rank code has digit value d" for each digit of the code: one digit of
 // 2 bits for 2 planes (4 masks), 3 + 2 bits for 5 planes (8 + 4), 3 + 2 + 2
 // bits for 7 planes (8 + 4 + 4); a column then takes its symbol's rank code
-// from B's bytes and ANDs one mask of each digit's table (one load per word
+// from the input's code bytes and ANDs one mask of each digit's table (one load per word
 // for 2 planes, one three-input logic op per word for 7), instead of an XNOR
 // per plane and word.  Tables: word (d * (W + 1) + w) * 128 + thread, the
 // digits' tables back to back.  (For 7 planes, two digits of 4 and 3 bits,
@@ -306,7 +313,7 @@ constexpr int kChunkFor = (W <= 2 && !kDigitTables<P>) ? 16 : 32;
 template <int P>
 constexpr int digit_masks() { return P == 2 ? 4 : (P == 5 ? 12 : 16); }
 template <int W, int P>
-constexpr size_t digit_smem_bytes() { return 256 + (size_t)digit_masks<P>() * (W + 1) * 128 * 4; }
+constexpr size_t digit_smem_bytes() { return (size_t)digit_masks<P>() * (W + 1) * 128 * 4; }
 
 // The masks of band word w (A's pre-shifted plane words pa) into the tables.
 template <int W, int P>
@@ -358,8 +365,7 @@ __device__ __forceinline__ void digit_lookup(const uint32_t* __restrict__ tab, u
 
 template <int W, int P>
 __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs& a, uint64_t PW, uint32_t* res,
-                                           uint32_t* __restrict__ tab, const uint8_t* __restrict__ s_rank,
-                                           uint32_t GW) {
+                                           uint32_t* __restrict__ tab, uint32_t GW) {
   constexpr bool kDigits = kDigitTables<P>;
   const int32_t j0 = st.j;
   uint32_t pa[P][W + 1];
@@ -393,13 +399,13 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
       const int tid = threadIdx.x;
 #pragma unroll
       for (int w = 0; w <= W; ++w) build_digit_tables<W, P>(pa, w, tab, tid);
-      // B's bytes of columns j0 .. j0 + 31, aligned so that column j0 + c is
-      // byte c (words beyond the input read as zero)
+      // B's rank codes of columns j0 .. j0 + 31, aligned so that column j0 + c
+      // is byte c (words beyond the input read as zero)
       const uint64_t bi = st.bpos - 32 * (uint64_t)GW;   // byte index of column j0's symbol
-      const uintptr_t at0 = (uintptr_t)(a.bytes + bi);
+      const uintptr_t at0 = (uintptr_t)(a.codes + bi);
       const uint32_t sh = 8u * (uint32_t)(at0 & 3);
       const uintptr_t wa = at0 & ~(uintptr_t)3;
-      const uintptr_t lo_end = (uintptr_t)a.bytes, hi_end = (uintptr_t)(a.bytes + a.nbytes);
+      const uintptr_t lo_end = (uintptr_t)a.codes, hi_end = (uintptr_t)(a.codes + a.nbytes);
       uint32_t raw[9];
       if (wa >= lo_end && wa + 36 <= hi_end) {   // the common case: nine aligned words inside the input
 #pragma unroll
@@ -434,7 +440,7 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
     // equality bits of column j0 + c: A's plane bits XNOR B's, over the planes
     uint32_t EqF[W + 1];
     if constexpr (kDigits) {
-      const uint32_t code = s_rank[(bsym[c >> 2] >> (8 * (c & 3))) & 255u];
+      const uint32_t code = (bsym[c >> 2] >> (8 * (c & 3))) & 255u;
       digit_lookup<W, P>(tab, code, threadIdx.x, EqF);
     } else {
 #pragma unroll
@@ -507,13 +513,8 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
 template <int W, int P>
 __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t PW, uint32_t GW,
                                                           unsigned long long* __restrict__ next) {
-  extern __shared__ __align__(16) uint32_t vsm[];   // digit tables: the rank table, then the tables
-  uint8_t* s_rank = reinterpret_cast<uint8_t*>(vsm);
-  uint32_t* tab = vsm + 64;   // the digit tables
-  if (kDigitTables<P>) {
-    for (int b = threadIdx.x; b < 256; b += blockDim.x) s_rank[b] = a.rank_table[b];
-    __syncthreads();
-  }
+  extern __shared__ __align__(16) uint32_t vsm[];   // the digit tables
+  uint32_t* tab = vsm;
   const int lane = threadIdx.x & 31;
   const uint64_t q_lo = a.range_lo ? *a.range_lo : 0;
   const uint64_t q_hi = a.range_hi ? *a.range_hi : a.m;
@@ -565,7 +566,7 @@ __global__ void __launch_bounds__(128) verify_diag_kernel(VerifyArgs a, uint64_t
     if (active) {
       uint32_t res;
       const int32_t j_before = st.j;
-      const bool done = pair_chunk<W, P>(st, a, PW, &res, tab, s_rank, GW);
+      const bool done = pair_chunk<W, P>(st, a, PW, &res, tab, GW);
       work += (uint64_t)(st.j - j_before) * W;
       if (done) {
         put_result(a, st.t, res);
@@ -1175,7 +1176,7 @@ int launch_wp(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long*
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t smem = kDigitTables<P> ? digit_smem_bytes<W, P>() : 0;
   if (kDigitTables<P>) {
-    if (!a.rank_table) return MJ_ERR_ARG;
+    if (!a.codes) return MJ_ERR_ARG;
     MJ_CUDA_TRY(cudaFuncSetAttribute(verify_diag_kernel<W, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
   }
@@ -1196,9 +1197,9 @@ int launch_wp(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long*
 
 template <int W>
 int launch_w(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long* next, cudaStream_t s) {
-  // digit tables read B's symbols through the rank codes; without them (raw
-  // byte planes) every plane is XNORed
-  if (!a.rank_table) return launch_wp<W, 8>(a, PW, GW, next, s);
+  // digit tables read B's rank codes; without them (raw byte planes) every
+  // plane is XNORed
+  if (!a.codes) return launch_wp<W, 8>(a, PW, GW, next, s);
   if (a.bits <= 2) return launch_wp<W, 2>(a, PW, GW, next, s);
   if (a.bits <= 5) return launch_wp<W, 5>(a, PW, GW, next, s);
   if (a.bits == 7) return launch_wp<W, 7>(a, PW, GW, next, s);   // text (65-128 symbols)
@@ -1208,12 +1209,13 @@ int launch_w(const VerifyArgs& a, uint64_t PW, uint32_t GW, unsigned long long* 
 }  // namespace
 
 int launch_build_planes(const uint8_t* bytes, uint64_t nbytes, const RankTable& rt, uint32_t bits,
-                        uint32_t* planes, uint64_t plane_words, uint32_t guard_words, cudaStream_t s) {
+                        uint32_t* planes, uint64_t plane_words, uint32_t guard_words, uint8_t* codes,
+                        cudaStream_t s) {
   if (bits > (uint32_t)kMaxBits) return MJ_ERR_UNSUPPORTED;
   uint64_t blocks = (plane_words + 255) / 256;
   uint64_t cap = (uint64_t)kNumSMsHint * 32;
   build_planes_kernel<<<(unsigned)(blocks > cap ? cap : blocks), 256, 0, s>>>(bytes, nbytes, rt, bits, planes,
-                                                                              plane_words, guard_words);
+                                                                              plane_words, guard_words, codes);
   MJ_KERNEL_DONE();
   return MJ_OK;
 }
