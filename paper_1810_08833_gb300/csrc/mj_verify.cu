@@ -511,7 +511,7 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
 // next pair index (warp-aggregated atomic on *next) as soon as its pair is
 // decided, so early exits do not leave lanes idle behind slow pairs.
 template <int W, int P>
-__global__ void __launch_bounds__(128, (P == 7 && W <= 3) ? 7 : 1) verify_diag_kernel(VerifyArgs a, uint64_t PW, uint32_t GW,
+__global__ void __launch_bounds__(128, (P == 7 && W <= 3) ? 7 : ((P == 5 && W <= 2) ? 8 : 1)) verify_diag_kernel(VerifyArgs a, uint64_t PW, uint32_t GW,
                                                           unsigned long long* __restrict__ next) {
   extern __shared__ __align__(16) uint32_t vsm[];   // the digit tables
   uint32_t* tab = vsm;
