@@ -48,9 +48,9 @@ RECORD_BYTES = 24            # one partition record written: sid, pos, len, stri
 # of the full-size launch) of the current kernel, keyed by (section, workload
 # number); absent (reported as null) where no capture of the current kernel
 # exists.  Text-like workload: verify_diag_kernel<3, 7> with three digit
-# tables and the per-chunk count of the top row's rises, 49.73 GB read +
-# 3.82 GB written in one launch over 645 M candidates.
-TRAFFIC_BYTES = {("verify_kernel", 5): 49.73e9 + 3.82e9}
+# tables, code bytes and the per-chunk count of the top row's rises,
+# 49.80 GB read + 3.82 GB written in one launch over 645 M candidates.
+TRAFFIC_BYTES = {("verify_kernel", 5): 49.80e9 + 3.82e9}
 # integer issue ceiling per SM and clock: the ALU pipe's 64 lanes plus the
 # FMA pipe's 64 (integer multiply-adds run there)
 ISSUE_LANES_PER_SM = 128
