@@ -297,8 +297,10 @@ constexpr int kChunkFor = (W <= 2 && !kDigitTables<P>) ? 16 : 32;
 // Advances up to kChunkFor<W, P> columns; returns true when the pair is decided.
 // The chunk's symbols are loaded at its start for every lane at once: A's
 // plane words of the rows the band covers in these columns (pre-shifted so
-// that column j0 + c needs a shift by c < 32), and B's plane bits of the
-// columns, bit-reversed so that the next column's bit is the sign bit.
+// that column j0 + c needs a shift by c < 32), and B's symbols of the
+// columns: with digit tables its rank codes, one byte per column; with the
+// XNORs (8 planes) its plane bits, bit-reversed so that the next column's
+// bit is the sign bit.
 // Equality bits by digit tables (2, 5 and 7 bit-planes).  Per chunk, every
 // thread writes to shared memory, for each of A's band words, the masks "rows
 // whose rank code has digit value d" for each digit of the code: one digit of
@@ -370,7 +372,7 @@ __device__ __forceinline__ bool pair_chunk(PairState<W, P>& st, const VerifyArgs
   const int32_t j0 = st.j;
   uint32_t pa[P][W + 1];
   uint32_t bw[P];
-  uint32_t bsym[kDigits ? 8 : 1];   // B's bytes of the chunk's columns, four per word
+  uint32_t bsym[kDigits ? 8 : 1];   // B's rank codes of the chunk's columns, four per word
   {
     const uint64_t ab = st.abit + (uint64_t)(j0 - 1);
     const uint64_t aw = ab >> 5;
