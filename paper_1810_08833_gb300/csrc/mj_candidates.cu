@@ -505,7 +505,7 @@ __device__ __forceinline__ uint64_t band_cells_of(int64_t m, int64_t n, int64_t 
 // class counts, block-major (bh[b * 256 + c]); the scan turns them into each
 // block's first position per class, so the scatter needs no global atomics.
 constexpr int kOrderThreads = 256;
-constexpr int kOrderItems = 4;
+constexpr int kOrderItems = 8;
 constexpr uint64_t kOrderChunk = (uint64_t)kOrderThreads * kOrderItems;
 constexpr int kOrderBlocksMax = kNumSMsHint * 8;
 
