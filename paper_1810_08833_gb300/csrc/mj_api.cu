@@ -172,8 +172,8 @@ struct mj_ctx {
   Buf branges;   // bucket counts [32] then ranges [64]
   // CUDA graph of the plain verification stage
   cudaGraphExec_t graph_exec = nullptr;
-  uint64_t graph_sig[17] = {};
-  uint64_t last_sig[17] = {};
+  uint64_t graph_sig[23] = {};
+  uint64_t last_sig[23] = {};
   uint64_t graph_launches = 0;
   // learned first-pass band: parameters P, Adam moments M and V, gradient G, loss
   Buf band;
@@ -762,10 +762,14 @@ int verify_ordered_graph(mj_ctx* c, const uint8_t* d_bytes, const int64_t* d_off
   if (c->tuned) {
     for (int b = 0; b < kLenBuckets; ++b) plan = plan * 1000003u + c->tuned_kernel[b] * 64u + c->tuned_lanes[b];
   }
-  const uint64_t sig[17] = {(uint64_t)d_bytes, (uint64_t)d_offsets, (uint64_t)ci, (uint64_t)cj, m, K,
+  // everything the captured launches read as a parameter: buffers, sizes, plan
+  const uint64_t sig[23] = {(uint64_t)d_bytes, (uint64_t)d_offsets, (uint64_t)ci, (uint64_t)cj, m, K,
                             (uint64_t)ed, (uint64_t)c->planes.p, c->planes_pw, c->d.bits, plan,
                             (uint64_t)c->small.p, (uint64_t)c->idx.p, (uint64_t)c->branges.p,
-                            (uint64_t)c->dev_flags.p, c->out_collect ? (uint64_t)c->out_t.p : 0, (uint64_t)c->geo.p};
+                            (uint64_t)c->dev_flags.p, c->out_collect ? (uint64_t)c->out_t.p : 0, (uint64_t)c->geo.p,
+                            c->stats.n_bytes, c->stats.n_strings, c->planes_gw,
+                            (uint64_t)c->codes.p, (uint64_t)c->strgeo.p,
+                            (uint64_t)c->rank_dev.p};
   if (c->graph_exec && memcmp(sig, c->graph_sig, sizeof(sig)) == 0) {
     MJ_CUDA_TRY(cudaGraphLaunch(c->graph_exec, s));
     mark_graph_sections(c);

@@ -79,6 +79,35 @@ def test_graph_recaptures_on_new_inputs(ctx):
         ctx.set_verify_config(0, 0, 0, 0)
 
 
+def test_graph_after_buffers_grow(ctx):
+    """Inputs verified again from the same device tensors after a larger input
+    grew the context's buffers (code bytes, bit-planes, per-string table):
+    the graph captured for them reads the old buffers, so it must be captured
+    again, and the distances stay the oracle's."""
+    import torch
+    import paper_1810_08833_gb300 as mj
+    ctx.set_verify_config(mj.MJ_VERIFY_KERNEL_AUTO, 0, 0, 1)
+    try:
+        small = _mixed_lengths(71, 60, 200)
+        large = _mixed_lengths(72, 400, 600)
+        inputs = []
+        for s, pairs in (small, large):
+            data, off = to_device(s)
+            i = torch.from_numpy(pairs[:, 0].astype(np.int32)).cuda()
+            j = torch.from_numpy(pairs[:, 1].astype(np.int32)).cuda()
+            inputs.append((data, off, i, j, oracle.ed_band_pairs(s.bytes, s.offsets, pairs, 60)))
+        stream = torch.cuda.Stream()
+        for which in (0, 1, 0):
+            data, off, i, j, want = inputs[which]
+            for _ in range(3):
+                with torch.cuda.stream(stream):
+                    got = ctx.verify(data, off, i, j, 60, stream=stream)
+                stream.synchronize()
+                assert np.array_equal(got.cpu().numpy().astype(np.int64), want), which
+    finally:
+        ctx.set_verify_config(0, 0, 0, 0)
+
+
 def test_join_with_tuned_graph_plan(ctx):
     import paper_1810_08833_gb300 as mj
     s = synth.make_config(3, n_roots=6)
